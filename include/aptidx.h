@@ -1,0 +1,236 @@
+/*
+ * aptidx.h -- C ABI of the GB300 (sm_103a) library for real-space (RSP)
+ * crystallographic signatures of atom probe data and their indexing, after
+ * Kuehbach, Kasemer, Gault, Breen, "On Open and Strong-Scaling Tools for Atom
+ * Probe Crystallography: High-Throughput Methods for Indexing Crystal
+ * Structure and Orientation" (arXiv 2009.00735).
+ *
+ * The method (Section 2.2): for every region of interest (ROI) -- a sphere of
+ * radius R around a point p_c -- project the ROI-centred atom positions onto
+ * each direction of a geodesic sphere, bin the projected distances into a
+ * 2^m-bin histogram (Eq. 1), take the histogram's Fourier amplitude spectrum,
+ * and keep, per direction, the largest amplitude inside a band of frequency
+ * bins.  The result is one spherical image (signature) per ROI, which is
+ * matched against rotated reference signatures (Section 2.4, Eq. 3) and
+ * refined to an orientation.
+ *
+ * Conventions
+ *   - Every function returns an int status: APTIDX_OK (0) or an APTIDX_E_*
+ *     code.  aptidx_last_error() gives a message for the last failure.
+ *   - Pointers tagged `mem` are host memory (APTIDX_MEM_HOST) or device
+ *     memory of the context's GPU (APTIDX_MEM_DEVICE).  The caller keeps
+ *     ownership of every pointer it passes.  Inputs are copied into
+ *     library-owned device memory before the call returns its work to the
+ *     stream; outputs are written into caller-allocated buffers.
+ *   - Work is queued on the context's CUDA stream.  Calls that return data
+ *     to host memory synchronise that stream.  Calls that write device
+ *     buffers do not: the caller orders later work on the same stream.
+ *   - Device-side failures (a bounded wait that ran out, a count overflow)
+ *     are recorded in a device status word and reported by the next
+ *     synchronising call, or by aptidx_sync().
+ *   - Layouts are row-major, C order.  Positions are FP32 nm, ROI centres
+ *     and radii FP64 nm, directions FP32 unit vectors.
+ *
+ * Arithmetic contract (what the results equal)
+ *   - Membership: atom i belongs to ROI c iff (dx*dx + dy*dy) + dz*dz <= R*R
+ *     in FP64 with dx = (double)x_i - c_x (no fused multiply-add).  Centred
+ *     coordinates are x_i - p_c rounded once to FP32.
+ *   - Bin (Eq. 1 with dR = R / (2^(m-1) - 1), Fig. 2 caption):
+ *       s = fma(u_z, x_z, fma(u_y, x_y, u_x * x_x))   (FP32, round-to-nearest)
+ *       scale = (float)((2^(m-1) - 1) / R)
+ *       b = clamp(2^(m-1) + floor(s * scale), 0, 2^m - 1)
+ *     with s * scale the exact product.  Histograms are exact integers.
+ *   - Spectrum: X(k) = sum_n h[n] exp(-2 pi i k n / 2^m), unnormalised,
+ *     rectangular window; signature S(v) = max over the ROI's band of |X(k)|.
+ */
+#ifndef APTIDX_H
+#define APTIDX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aptidx_ctx aptidx_ctx;
+
+/* status codes */
+#define APTIDX_OK              0
+#define APTIDX_E_INVALID_ARG   1   /* a pointer, size or value is out of range */
+#define APTIDX_E_CUDA          2   /* a CUDA runtime call failed */
+#define APTIDX_E_OOM           3   /* device memory allocation failed */
+#define APTIDX_E_TIMEOUT       4   /* a bounded device-side wait ran out */
+#define APTIDX_E_OVERFLOW      5   /* a ROI or bin count exceeds what the path carries */
+#define APTIDX_E_STATE         6   /* a required earlier call is missing */
+
+/* memory spaces */
+#define APTIDX_MEM_HOST        0
+#define APTIDX_MEM_DEVICE      1
+
+/* signature paths */
+#define APTIDX_PATH_PLAIN_FP32 0   /* FP32 CUDA-core DFT of the histograms */
+#define APTIDX_PATH_TC_FP16    1   /* histogram x DFT-matrix contraction on tcgen05 */
+
+/* flags of aptidx_compute_signatures */
+#define APTIDX_NORMALISE_MAX   1u  /* divide each ROI's signature by its largest value */
+
+/* limits */
+#define APTIDX_MAX_ATOMS_PER_ROI 65535   /* u16 histogram counts */
+#define APTIDX_MIN_M 8
+#define APTIDX_MAX_M 10
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to queue all work on (NULL: the legacy default stream); the
+ * caller keeps ownership of the stream.  On success *out receives the
+ * context.  Errors: INVALID_ARG (out == NULL, bad device), CUDA. */
+int aptidx_create(aptidx_ctx** out, int device, void* cuda_stream);
+
+/* Synchronise the stream and free every library-owned buffer. */
+int aptidx_destroy(aptidx_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  The
+ * string is owned by the context and valid until the next call. */
+const char* aptidx_last_error(const aptidx_ctx* ctx);
+
+/* Synchronise the context's stream and report the device status word:
+ * TIMEOUT or OVERFLOW if a kernel recorded one since the last report.
+ * Clears the word. */
+int aptidx_sync(aptidx_ctx* ctx);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int aptidx_version(void);
+
+/* ---- inputs ------------------------------------------------------------- */
+
+/* Atom positions of the reconstruction (Section 2.2: p_i).  xyz: n x 3 FP32
+ * (x, y, z) in nm; types: n atom-type ids (NULL: all type 0).  Copies the
+ * data and invalidates any previous ROI set.  Errors: INVALID_ARG (n <= 0,
+ * n >= 2^31, NULL xyz, non-finite coordinate), OOM, CUDA. */
+int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const uint8_t* types,
+                          int mem);
+
+/* Projection directions (Section 2.2: outer unit normals of the nodes of a
+ * geodesic sphere, N_v = 40962 in the paper).  u: nv x 3 FP32 unit vectors
+ * (|u| within 1e-5 of 1).  Errors: INVALID_ARG (nv <= 0, non-unit), OOM, CUDA. */
+int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem);
+
+/* Histogram resolution 2^m bins (Eq. 1; APTIDX_MIN_M <= m <= APTIDX_MAX_M)
+ * and the default signature band of frequency bins [k_lo, k_hi]
+ * (supplement, Al bicrystal: the highest amplitude in a fixed bin interval),
+ * 0 <= k_lo <= k_hi <= 2^(m-1).  flags: reserved, 0. */
+int aptidx_set_binning(aptidx_ctx* ctx, int m, int32_t k_lo, int32_t k_hi, int flags);
+
+/* The ROI list (Section 2.4: ROIs on a grid or randomly placed).
+ * centres: nroi x 3 FP64 nm; radii: nroi FP64 nm (> 0); band_lo/band_hi:
+ * per-ROI signature bands (NULL: the default band of aptidx_set_binning);
+ * type_mask: bit t selects atoms of type t (0xFFFFFFFF: all).  All arrays
+ * live in `mem`.  Requires positions, directions and binning.  Counts the
+ * ROI atoms once to size the library's gather buffers.  Errors:
+ * INVALID_ARG, STATE, OVERFLOW (a ROI holds more than
+ * APTIDX_MAX_ATOMS_PER_ROI selected atoms), OOM, CUDA. */
+int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii, int64_t nroi,
+                    const int32_t* band_lo, const int32_t* band_hi, uint32_t type_mask, int mem);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Signatures of every ROI: gather and centre the ROI atoms (FP64
+ * membership), project them on every direction, histogram them (Eq. 1),
+ * take the band of the amplitude spectrum and keep its maximum (Section
+ * 2.2).  path: APTIDX_PATH_PLAIN_FP32 or APTIDX_PATH_TC_FP16.  flags:
+ * APTIDX_NORMALISE_MAX or 0.
+ * Outputs (in `mem`; NULL to skip): S nroi x nv FP32; argk nroi x nv u16 (the
+ * lowest frequency bin attaining the maximum; not written when normalising
+ * is the only change); n_atoms nroi int32 (N_w per ROI).
+ * With mem == APTIDX_MEM_HOST the call copies the results back and
+ * synchronises.  Errors: STATE, INVALID_ARG, OVERFLOW, TIMEOUT, OOM, CUDA. */
+int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* S, uint16_t* argk,
+                              int32_t* n_atoms, int mem);
+
+/* Debug/parity: the 2^m-bin histograms of ROI `roi` for every direction, as
+ * computed by the histogram stage of `path` (same kernel code).  h: nv x 2^m
+ * u16 in `mem`. */
+int aptidx_get_histograms(aptidx_ctx* ctx, int64_t roi, int path, uint16_t* h, int mem);
+
+/* Debug/parity: the centred FP32 coordinates of ROI `roi` in gather order.
+ * xc: cap x 3 FP32 in `mem`; *n_out receives N_w (written even if cap is
+ * too small, in which case nothing is copied and OVERFLOW is returned). */
+int aptidx_get_roi_atoms(aptidx_ctx* ctx, int64_t roi, float* xc, int64_t cap, int64_t* n_out,
+                         int mem);
+
+/* ---- indexing (supplement "Indexing algorithm", Eq. 3) ---------------------- */
+
+/* Reference of crystal-structure candidate `cand` (0 <= cand < 8):
+ * node_sig: nv FP32 normalised reference signature on the current
+ * directions (its n_hat strongest nodes enter Eq. 3);
+ * img: 181 x 360 FP32 elevation-azimuth image of the same reference
+ * (row i: elevation -90 + i degrees; column j: azimuth j degrees), used by
+ * refinement; may be NULL if refinement is not used.
+ * 1 <= n_hat <= nv.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
+int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, int32_t n_hat,
+                         const float* img, int mem);
+
+/* Look-up table of candidate `cand` for test orientations quats (ng x 4
+ * FP64 unit quaternions (w, x, y, z), mapping crystal to lab): entry
+ * (g, k) = the direction index nearest to R(q_g) n_k for the k-th strongest
+ * reference node n_k.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
+int aptidx_build_lut(aptidx_ctx* ctx, int32_t cand, const double* quats, int64_t ng, int mem);
+
+/* Eq. 3 for every ROI: Delta(g) = sum_k (S[roi, lut[g, k]] - ref[n_k])^2
+ * over the candidate's look-up table; best[roi] = argmin_g (ties: lowest
+ * g), score[roi] = Delta(best).  S: nroi x nv FP32 normalised signatures in
+ * `mem`; best: nroi int32; score: nroi FP32 (NULL to skip).  Errors:
+ * INVALID_ARG, STATE, OOM, CUDA. */
+int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, int32_t* best,
+                 float* score, int mem);
+
+/* ---- orientation refinement ------------------------------------------------ */
+
+/* Loss and gradient of the misfit between measured signatures and the
+ * candidate's reference image sampled bilinearly at R^T u:
+ *   L_roi(q) = sum_v (S[roi, v] - I(alpha, beta of R(q)^T u_v))^2,
+ * leaving out directions whose crystal-frame elevation exceeds 89 degrees
+ * in magnitude.  q: nroi x 4 FP64.  loss: nroi FP32.  grad (NULL to skip):
+ * nroi x 3 FP32 dL/d(delta) for R = exp([delta]x) R(q) at delta = 0 (the
+ * backward kernel).  All in `mem`. */
+int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q, int64_t nroi,
+                       float* loss, float* grad, int mem);
+
+/* `iters` Gauss-Newton steps per ROI from q0: delta = -(J^T J + lambda I)^-1
+ * J^T r with lambda = 1e-6 tr(J^T J), R <- exp([delta]x) R, FP64
+ * renormalisation.  q_out: nroi x 4 FP64 (w >= 0); loss: nroi FP32 at q_out
+ * (NULL to skip).  All in `mem`. */
+int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, int64_t nroi,
+                  int32_t iters, double* q_out, float* loss, int mem);
+
+/* ---- capabilities and profiling ------------------------------------------- */
+
+/* 1 if `path` can run on the context's device, else 0. */
+int aptidx_path_supported(aptidx_ctx* ctx, int path);
+
+/* Phases timed when profiling is on. */
+#define APTIDX_PHASE_GATHER    0   /* ROI count, offsets, gather + centring (a1) */
+#define APTIDX_PHASE_ORDER     1   /* longest-first ROI order */
+#define APTIDX_PHASE_SIGNATURE 2   /* projection, histogram, spectrum, band max (a2-a5) */
+#define APTIDX_PHASE_NORMALISE 3
+#define APTIDX_PHASE_MATCH     4   /* Eq. 3 (a6) */
+#define APTIDX_PHASE_REFINE    5   /* Gauss-Newton (a7) */
+#define APTIDX_N_PHASES        6
+
+/* enable != 0: record CUDA events on the context's stream around every
+ * phase of the following calls and count the kernels they launch; resets
+ * the totals.  enable == 0: stop recording. */
+int aptidx_set_profiling(aptidx_ctx* ctx, int enable);
+
+/* Synchronise and return the totals since profiling was enabled:
+ * phase_ms[APTIDX_N_PHASES] summed CUDA-event milliseconds, phase_calls
+ * [APTIDX_N_PHASES] how many times each phase ran, *launches the number of
+ * library kernels launched.  Any pointer may be NULL. */
+int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APTIDX_H */

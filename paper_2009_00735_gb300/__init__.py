@@ -1,0 +1,361 @@
+"""GB300-native RSP signatures and orientation indexing for atom probe data
+(Kuehbach et al., arXiv 2009.00735) -- Python binding of libaptidx.
+
+Thin ctypes marshalling over the C ABI declared in include/aptidx.h: every
+function keeps its C name, accepts torch tensors (CUDA -> device pointer,
+CPU -> host pointer) or numpy arrays (host), and raises AptidxError on a
+non-zero status.  All computation runs in the library's CUDA kernels; there is
+no CPU fallback.  Build the library first with
+``paper_2009_00735_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = [
+    "AptidxError", "load", "Context",
+    "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
+    "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
+    "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_match", "aptidx_refine_loss", "aptidx_refine",
+    "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
+    "tc_available", "PHASES",
+    "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
+    "APTIDX_NORMALISE_MAX",
+]
+
+APTIDX_OK = 0
+APTIDX_E_INVALID_ARG = 1
+APTIDX_E_CUDA = 2
+APTIDX_E_OOM = 3
+APTIDX_E_TIMEOUT = 4
+APTIDX_E_OVERFLOW = 5
+APTIDX_E_STATE = 6
+APTIDX_MEM_HOST = 0
+APTIDX_MEM_DEVICE = 1
+APTIDX_PATH_PLAIN_FP32 = 0
+APTIDX_PATH_TC_FP16 = 1
+APTIDX_NORMALISE_MAX = 1
+
+_ERR_NAMES = {1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "OVERFLOW", 6: "STATE"}
+
+
+class AptidxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"aptidx error {code} ({_ERR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+_vp = C.c_void_p
+_i64 = C.c_int64
+_i32 = C.c_int32
+_SIGS = {
+    "aptidx_version": (C.c_int, []),
+    "aptidx_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
+    "aptidx_destroy": (C.c_int, [_vp]),
+    "aptidx_last_error": (C.c_char_p, [_vp]),
+    "aptidx_sync": (C.c_int, [_vp]),
+    "aptidx_load_positions": (C.c_int, [_vp, _vp, _i64, _vp, C.c_int]),
+    "aptidx_set_directions": (C.c_int, [_vp, _vp, _i32, C.c_int]),
+    "aptidx_set_binning": (C.c_int, [_vp, C.c_int, _i32, _i32, C.c_int]),
+    "aptidx_set_rois": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, C.c_uint32, C.c_int]),
+    "aptidx_compute_signatures": (C.c_int, [_vp, C.c_int, C.c_uint, _vp, _vp, _vp, C.c_int]),
+    "aptidx_get_histograms": (C.c_int, [_vp, _i64, C.c_int, _vp, C.c_int]),
+    "aptidx_get_roi_atoms": (C.c_int, [_vp, _i64, _vp, _i64, C.POINTER(_i64), C.c_int]),
+    "aptidx_set_reference": (C.c_int, [_vp, _i32, _vp, _i32, _vp, C.c_int]),
+    "aptidx_build_lut": (C.c_int, [_vp, _i32, _vp, _i64, C.c_int]),
+    "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
+    "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, C.c_int]),
+    "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
+    "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
+    "aptidx_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "aptidx_get_profile": (C.c_int, [_vp, _vp, _vp, _vp]),
+}
+
+APTIDX_N_PHASES = 6
+PHASES = ("gather", "order", "signature", "normalise", "match", "refine")
+
+
+def library_path() -> str:
+    return _build_mod.LIB
+
+
+def load():
+    """Load libaptidx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libaptidx.so is not built ({path}); run paper_2009_00735_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(lib, name):
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    lib = load()
+    return [n for n in _SIGS if hasattr(lib, n)]
+
+
+# ---------------------------------------------------------------------------
+# marshalling
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def _arg(x, dtype):
+    """(pointer, mem, keep-alive object) of an input array."""
+    if x is None:
+        return None, None, None
+    if _is_torch(x):
+        torch = _torch()
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+               np.uint8: torch.uint8, np.uint16: torch.uint16, np.int64: torch.int64}[dtype]
+        if x.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {x.dtype}")
+        x = x.contiguous()
+        return x.data_ptr(), (APTIDX_MEM_DEVICE if x.is_cuda else APTIDX_MEM_HOST), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, APTIDX_MEM_HOST, a
+
+
+def _out(x, dtype):
+    """(pointer, mem) of an output array; must already be contiguous."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        torch = _torch()
+        if not x.is_contiguous():
+            raise ValueError("output tensors must be contiguous")
+        return x.data_ptr(), (APTIDX_MEM_DEVICE if x.is_cuda else APTIDX_MEM_HOST)
+    if not (isinstance(x, np.ndarray) and x.flags.c_contiguous and x.dtype == dtype):
+        raise ValueError(f"output arrays must be C-contiguous {np.dtype(dtype)}")
+    return x.ctypes.data, APTIDX_MEM_HOST
+
+
+def _one_mem(*mems):
+    ms = {m for m in mems if m is not None}
+    if len(ms) > 1:
+        raise ValueError("all arrays of one call must live in the same memory space")
+    return ms.pop() if ms else APTIDX_MEM_HOST
+
+
+def _check(ctx, rc):
+    if rc != APTIDX_OK:
+        msg = load().aptidx_last_error(ctx).decode() if ctx else ""
+        raise AptidxError(rc, msg)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per C function
+# ---------------------------------------------------------------------------
+
+def aptidx_version() -> int:
+    return load().aptidx_version()
+
+
+def aptidx_create(device: int = 0, stream=None):
+    """Context on `device`; `stream` is a torch.cuda.Stream, a raw cudaStream_t
+    (int) or None for torch's current stream on that device."""
+    lib = load()
+    if stream is None:
+        torch = _torch()
+        stream = torch.cuda.current_stream(device).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = _vp()
+    rc = lib.aptidx_create(C.byref(h), int(device), _vp(int(stream)) if stream else None)
+    if rc != APTIDX_OK:
+        raise AptidxError(rc, "aptidx_create failed")
+    return h
+
+
+def aptidx_destroy(ctx):
+    _check(None, load().aptidx_destroy(ctx))
+
+
+def aptidx_last_error(ctx) -> str:
+    return load().aptidx_last_error(ctx).decode()
+
+
+def aptidx_sync(ctx):
+    _check(ctx, load().aptidx_sync(ctx))
+
+
+def aptidx_load_positions(ctx, xyz, types=None):
+    p, m, k1 = _arg(xyz, np.float32)
+    t, mt, k2 = _arg(types, np.uint8)
+    n = (k1.numel() if _is_torch(k1) else k1.size) // 3
+    _check(ctx, load().aptidx_load_positions(ctx, p, n, t, _one_mem(m, mt)))
+
+
+def aptidx_set_directions(ctx, u):
+    p, m, k = _arg(u, np.float32)
+    nv = (k.numel() if _is_torch(k) else k.size) // 3
+    _check(ctx, load().aptidx_set_directions(ctx, p, nv, m))
+
+
+def aptidx_set_binning(ctx, m: int, k_lo: int, k_hi: int, flags: int = 0):
+    _check(ctx, load().aptidx_set_binning(ctx, m, k_lo, k_hi, flags))
+
+
+def aptidx_set_rois(ctx, centres, radii, band_lo=None, band_hi=None, type_mask=0xFFFFFFFF):
+    pc, mc, kc = _arg(centres, np.float64)
+    pr, mr, kr = _arg(radii, np.float64)
+    nroi = (kr.numel() if _is_torch(kr) else kr.size)
+    if band_lo is not None and not _is_torch(band_lo):
+        band_lo = np.broadcast_to(np.asarray(band_lo, np.int32), (nroi,))
+        band_hi = np.broadcast_to(np.asarray(band_hi, np.int32), (nroi,))
+    pl, ml, kl = _arg(band_lo, np.int32)
+    ph, mh, kh = _arg(band_hi, np.int32)
+    _check(ctx, load().aptidx_set_rois(ctx, pc, pr, nroi, pl, ph, C.c_uint32(type_mask & 0xFFFFFFFF),
+                                       _one_mem(mc, mr, ml, mh)))
+
+
+def aptidx_compute_signatures(ctx, path: int, flags: int, S=None, argk=None, n_atoms=None):
+    pS, mS = _out(S, np.float32)
+    pA, mA = _out(argk, np.uint16)
+    pN, mN = _out(n_atoms, np.int32)
+    _check(ctx, load().aptidx_compute_signatures(ctx, path, flags, pS, pA, pN, _one_mem(mS, mA, mN)))
+
+
+def aptidx_get_histograms(ctx, roi: int, path: int, h):
+    p, m = _out(h, np.uint16)
+    _check(ctx, load().aptidx_get_histograms(ctx, roi, path, p, m))
+
+
+def aptidx_get_roi_atoms(ctx, roi: int, xc=None, cap: int = 0):
+    n = _i64(0)
+    if xc is None:
+        rc = load().aptidx_get_roi_atoms(ctx, roi, None, 0, C.byref(n), APTIDX_MEM_HOST)
+        if rc not in (APTIDX_OK, APTIDX_E_OVERFLOW):
+            _check(ctx, rc)
+        xc = np.empty((n.value, 3), np.float32)
+        cap = n.value
+    p, m = _out(xc, np.float32)
+    _check(ctx, load().aptidx_get_roi_atoms(ctx, roi, p, cap, C.byref(n), m))
+    return xc[: n.value]
+
+
+def aptidx_set_reference(ctx, cand: int, node_sig, n_hat: int, img=None):
+    p, m, k = _arg(node_sig, np.float32)
+    pi, mi, ki = _arg(img, np.float32)
+    _check(ctx, load().aptidx_set_reference(ctx, cand, p, n_hat, pi, _one_mem(m, mi)))
+
+
+def aptidx_build_lut(ctx, cand: int, quats):
+    p, m, k = _arg(quats, np.float64)
+    ng = (k.numel() if _is_torch(k) else k.size) // 4
+    _check(ctx, load().aptidx_build_lut(ctx, cand, p, ng, m))
+
+
+def aptidx_match(ctx, cand: int, S, best, score=None):
+    pS, mS, kS = _arg(S, np.float32)
+    pb, mb = _out(best, np.int32)
+    ps, ms = _out(score, np.float32)
+    nroi = best.shape[0]
+    _check(ctx, load().aptidx_match(ctx, cand, pS, nroi, pb, ps, _one_mem(mS, mb, ms)))
+
+
+def aptidx_refine_loss(ctx, cand: int, S, q, loss, grad=None):
+    pS, mS, kS = _arg(S, np.float32)
+    pq, mq, kq = _arg(q, np.float64)
+    pl, ml = _out(loss, np.float32)
+    pg, mg = _out(grad, np.float32)
+    nroi = loss.shape[0]
+    _check(ctx, load().aptidx_refine_loss(ctx, cand, pS, pq, nroi, pl, pg, _one_mem(mS, mq, ml, mg)))
+
+
+def aptidx_refine(ctx, cand: int, S, q0, iters: int, q_out, loss=None):
+    pS, mS, kS = _arg(S, np.float32)
+    pq, mq, kq = _arg(q0, np.float64)
+    po, mo = _out(q_out, np.float64)
+    pl, ml = _out(loss, np.float32)
+    nroi = q_out.shape[0]
+    _check(ctx, load().aptidx_refine(ctx, cand, pS, pq, nroi, iters, po, pl, _one_mem(mS, mq, mo, ml)))
+
+
+def aptidx_path_supported(ctx, path: int) -> bool:
+    return bool(load().aptidx_path_supported(ctx, path))
+
+
+def aptidx_set_profiling(ctx, enable: bool):
+    _check(ctx, load().aptidx_set_profiling(ctx, 1 if enable else 0))
+
+
+def aptidx_get_profile(ctx):
+    """{phase: (total ms, calls)} and the library kernel-launch count."""
+    ms = np.zeros(APTIDX_N_PHASES, np.float64)
+    calls = np.zeros(APTIDX_N_PHASES, np.int64)
+    n = np.zeros(1, np.int64)
+    _check(ctx, load().aptidx_get_profile(ctx, ms.ctypes.data, calls.ctypes.data, n.ctypes.data))
+    return {PHASES[i]: (float(ms[i]), int(calls[i])) for i in range(APTIDX_N_PHASES)}, int(n[0])
+
+
+def tc_available(device: int = 0) -> bool:
+    ctx = Context(device)
+    try:
+        return aptidx_path_supported(ctx.handle, APTIDX_PATH_TC_FP16)
+    finally:
+        ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# conveniences (host-side parameter arithmetic only)
+# ---------------------------------------------------------------------------
+
+def band_for_spacing(d_min: float, d_max: float, R: float, m: int):
+    """Frequency-bin band [k_lo, k_hi] holding plane spacings d_min..d_max:
+    bin k has period W / k with W = 2 (R + dR), dR = R / (2^(m-1) - 1)
+    (Fig. 2 caption)."""
+    import math
+    dR = R / ((1 << (m - 1)) - 1)
+    W = 2.0 * (R + dR)
+    return int(math.ceil(W / d_max)), int(math.floor(W / d_min))
+
+
+class Context:
+    """Owning wrapper of an aptidx context (destroyed on close/garbage collection)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.handle = aptidx_create(device, stream)
+        self.device = device
+
+    def close(self):
+        if self.handle is not None:
+            aptidx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

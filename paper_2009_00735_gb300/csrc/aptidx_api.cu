@@ -1,0 +1,678 @@
+// aptidx_api.cu -- the C ABI (include/aptidx.h): argument checks, ownership of
+// device buffers, and the order of the launches of the hot path.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace aptidx {
+
+int set_error(Ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_check(Ctx* c, cudaError_t e, const char* what) {
+    int code = (e == cudaErrorMemoryAllocation) ? APTIDX_E_OOM : APTIDX_E_CUDA;
+    return set_error(c, code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int dev_alloc(Ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(c, e == cudaErrorMemoryAllocation ? APTIDX_E_OOM : APTIDX_E_CUDA,
+                         "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    return APTIDX_OK;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+template <typename T>
+static void free_ptr(T*& p) {
+    dev_free((void*)p);
+    p = nullptr;
+}
+
+// A host view of an input array: the caller's pointer for host memory, a
+// copy for device memory.
+template <typename T>
+struct HostView {
+    const T* p = nullptr;
+    std::vector<T> own;
+    const T& operator[](size_t i) const { return p[i]; }
+    const T* data() const { return p; }
+};
+
+template <typename T>
+static int to_host(Ctx* c, const T* src, size_t count, int mem, HostView<T>& out) {
+    if (mem == APTIDX_MEM_HOST || count == 0) {
+        out.p = src;
+        return APTIDX_OK;
+    }
+    out.own.resize(count);
+    APTIDX_CUDA(c, cudaMemcpyAsync(out.own.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    out.p = out.own.data();
+    return APTIDX_OK;
+}
+
+void prof_begin(Ctx* c, int phase) {
+    if (!c->prof) return;
+    cudaEvent_t e;
+    if (!c->ev_pool.empty()) {
+        e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(e, c->stream);
+    c->ev_open[phase] = e;
+}
+
+void prof_end(Ctx* c, int phase, int kernels) {
+    c->launches += kernels;
+    if (!c->prof || !c->ev_open[phase]) return;
+    cudaEvent_t e;
+    if (!c->ev_pool.empty()) {
+        e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(e, c->stream);
+    c->ev_pending.push_back({phase, c->ev_open[phase], e});
+    c->ev_open[phase] = nullptr;
+}
+
+static int check_mem(Ctx* c, int mem) {
+    if (mem != APTIDX_MEM_HOST && mem != APTIDX_MEM_DEVICE)
+        return set_error(c, APTIDX_E_INVALID_ARG, "mem must be APTIDX_MEM_HOST or APTIDX_MEM_DEVICE");
+    return APTIDX_OK;
+}
+
+static int read_status(Ctx* c) {
+    int st = 0;
+    APTIDX_CUDA(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st) {
+        APTIDX_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+        if (st & kStatusTimeout)
+            return set_error(c, APTIDX_E_TIMEOUT, "a bounded device-side wait ran out (status 0x%x)", st);
+        if (st & kStatusOverflow)
+            return set_error(c, APTIDX_E_OVERFLOW, "a device-side count overflowed (status 0x%x)", st);
+    }
+    return APTIDX_OK;
+}
+
+static void free_rois(Ctx* c) {
+    free_ptr(c->d_centres);
+    free_ptr(c->d_radii);
+    free_ptr(c->d_scale);
+    free_ptr(c->d_band);
+    free_ptr(c->d_nw);
+    free_ptr(c->d_nw64);
+    free_ptr(c->d_off);
+    free_ptr(c->d_atoms);
+    free_ptr(c->d_order);
+    free_ptr(c->d_scan_tmp);
+    free_ptr(c->d_q);
+    free_ptr(c->d_acc);
+    c->nroi = 0;
+    c->atoms_cap = c->atoms_total = 0;
+    c->q_cap = 0;
+    c->scan_tmp_elems = 0;
+}
+
+static void free_grid(Ctx* c) {
+    free_ptr(c->d_cell_start);
+    free_ptr(c->d_cell_pos);
+    c->cell_h = 0.0;
+    c->n_cells = 0;
+}
+
+static int ensure_scan_tmp(Ctx* c, int64_t n) {
+    size_t need = scan_tmp_elems(n) + 1;
+    if (c->scan_tmp_elems >= need) return APTIDX_OK;
+    free_ptr(c->d_scan_tmp);
+    int rc = dev_alloc(c, (void**)&c->d_scan_tmp, need * sizeof(int64_t));
+    if (rc) return rc;
+    c->scan_tmp_elems = need;
+    return APTIDX_OK;
+}
+
+// Uniform cell grid with cell edge h over the positions' bounding box.
+static int build_grid(Ctx* c, double h) {
+    free_grid(c);
+    int64_t n_cells = 1;
+    for (;;) {
+        n_cells = 1;
+        for (int d = 0; d < 3; ++d) {
+            double ext = c->hi[d] - c->lo[d];
+            int dim = (int)std::max(1.0, ceil(ext / h));
+            if (dim > (1 << 20)) dim = 1 << 20;
+            c->dims[d] = dim;
+            n_cells *= dim;
+        }
+        if (n_cells <= (int64_t)1 << 24) break;
+        h *= 1.25;
+    }
+    c->cell_h = h;
+    c->n_cells = n_cells;
+    int rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_cell_start, (n_cells + 1) * sizeof(int64_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_cell_pos, c->n_atoms * sizeof(float4)))) return rc;
+    if ((rc = ensure_scan_tmp(c, n_cells))) return rc;
+    int32_t *cell_of = nullptr, *cursor = nullptr, *idx = nullptr;
+    int64_t* counts = nullptr;
+    rc = dev_alloc(c, (void**)&cell_of, c->n_atoms * sizeof(int32_t));
+    if (!rc) rc = dev_alloc(c, (void**)&cursor, n_cells * sizeof(int32_t));
+    if (!rc) rc = dev_alloc(c, (void**)&counts, n_cells * sizeof(int64_t));
+    if (!rc) rc = dev_alloc(c, (void**)&idx, c->n_atoms * sizeof(int32_t));
+    if (!rc) {
+        cudaError_t e = launch_cell_build(c, cell_of, cursor, counts, idx);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_check(c, e, "cell grid build");
+    }
+    dev_free(cell_of);
+    dev_free(cursor);
+    dev_free(counts);
+    dev_free(idx);
+    if (rc) free_grid(c);
+    return rc;
+}
+
+// gather count + offsets + fill (step a1), queued on the stream
+static int run_gather(Ctx* c) {
+    cudaError_t e = launch_gather_count(c);
+    if (e == cudaSuccess) e = launch_gather_fill(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "ROI gather");
+    return APTIDX_OK;
+}
+
+}  // namespace aptidx
+
+using namespace aptidx;
+
+#define CTX_OR_FAIL(ctx)                                   \
+    if (!(ctx)) return APTIDX_E_INVALID_ARG;               \
+    Ctx* c = &(ctx)->c;                                    \
+    c->err.clear();                                        \
+    {                                                      \
+        cudaError_t _e = cudaSetDevice(c->device);         \
+        if (_e != cudaSuccess) return cuda_check(c, _e, "cudaSetDevice"); \
+    }
+
+extern "C" {
+
+int aptidx_version(void) { return 100; }
+
+int aptidx_create(aptidx_ctx** out, int device, void* cuda_stream) {
+    if (!out) return APTIDX_E_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return APTIDX_E_INVALID_ARG;
+    }
+    aptidx_ctx* h = new aptidx_ctx();
+    Ctx* c = &h->c;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    int rc = APTIDX_OK;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) rc = APTIDX_E_CUDA;
+    if (!rc) rc = dev_alloc(c, (void**)&c->d_status, sizeof(int) * 4);
+    if (!rc) rc = dev_alloc(c, (void**)&c->d_counter, sizeof(int32_t) * 4);
+    if (!rc) rc = dev_alloc(c, (void**)&c->d_sort_hist, sizeof(int32_t) * 65537);
+    if (!rc && cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, c->stream) != cudaSuccess) rc = APTIDX_E_CUDA;
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = APTIDX_E_CUDA;
+    if (rc) {
+        aptidx_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return APTIDX_OK;
+}
+
+int aptidx_destroy(aptidx_ctx* ctx) {
+    if (!ctx) return APTIDX_E_INVALID_ARG;
+    Ctx* c = &ctx->c;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_rois(c);
+    free_grid(c);
+    free_ptr(c->d_S);
+    free_ptr(c->d_argk);
+    free_ptr(c->d_pos);
+    free_ptr(c->d_types);
+    free_ptr(c->d_dirs);
+    free_ptr(c->d_tw);
+    dev_free(c->d_twb);
+    c->d_twb = nullptr;
+    free_ptr(c->d_status);
+    free_ptr(c->d_counter);
+    free_ptr(c->d_sort_hist);
+    for (auto& pr : c->ev_pending) {
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (int i = 0; i < APTIDX_N_PHASES; ++i)
+        if (c->ev_open[i]) cudaEventDestroy(c->ev_open[i]);
+    for (int i = 0; i < kMaxCandidates; ++i) {
+        Reference& r = c->ref[i];
+        free_ptr(r.d_node_sig);
+        free_ptr(r.d_top);
+        free_ptr(r.d_top_val);
+        free_ptr(r.d_img);
+        free_ptr(r.d_lut);
+    }
+    delete ctx;
+    return APTIDX_OK;
+}
+
+const char* aptidx_last_error(const aptidx_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->c.err.c_str();
+}
+
+int aptidx_sync(aptidx_ctx* ctx) {
+    CTX_OR_FAIL(ctx);
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const uint8_t* types, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (!xyz || n <= 0 || n >= ((int64_t)1 << 31))
+        return set_error(c, APTIDX_E_INVALID_ARG, "positions: need 0 < n < 2^31 and a non-NULL pointer");
+    HostView<float> hx;
+    if ((rc = to_host(c, xyz, (size_t)n * 3, mem, hx))) return rc;
+    for (size_t i = 0; i < (size_t)n * 3; ++i)
+        if (!isfinite(hx[i])) return set_error(c, APTIDX_E_INVALID_ARG, "positions: non-finite coordinate at %zu", i / 3);
+    free_rois(c);
+    free_grid(c);
+    free_ptr(c->d_pos);
+    free_ptr(c->d_types);
+    c->n_atoms = 0;
+    if ((rc = dev_alloc(c, (void**)&c->d_pos, (size_t)n * 3 * sizeof(float)))) return rc;
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_pos, xyz, (size_t)n * 3 * sizeof(float),
+                                   mem == APTIDX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    if (types) {
+        if ((rc = dev_alloc(c, (void**)&c->d_types, (size_t)n))) return rc;
+        APTIDX_CUDA(c, cudaMemcpyAsync(c->d_types, types, (size_t)n,
+                                       mem == APTIDX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                       c->stream));
+    }
+    float* mm = nullptr;
+    if ((rc = dev_alloc(c, (void**)&mm, 12 * sizeof(float)))) return rc;
+    cudaError_t e = launch_bbox(c->d_pos, n, mm, c->stream);
+    float hmm[6];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(mm);
+    if (e != cudaSuccess) return cuda_check(c, e, "bounding box");
+    for (int d = 0; d < 3; ++d) {
+        c->lo[d] = hmm[d];
+        c->hi[d] = hmm[3 + d];
+    }
+    c->n_atoms = n;
+    return APTIDX_OK;
+}
+
+int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (!u || nv <= 0) return set_error(c, APTIDX_E_INVALID_ARG, "directions: need nv > 0");
+    HostView<float> hu;
+    if ((rc = to_host(c, u, (size_t)nv * 3, mem, hu))) return rc;
+    const int32_t nv_pad = (nv + kTileDirs - 1) / kTileDirs * kTileDirs;
+    std::vector<float4> d4((size_t)nv_pad, make_float4(1.f, 0.f, 0.f, 0.f));
+    for (int32_t v = 0; v < nv; ++v) {
+        float x = hu[3 * v], y = hu[3 * v + 1], z = hu[3 * v + 2];
+        double n2 = (double)x * x + (double)y * y + (double)z * z;
+        if (!(fabs(sqrt(n2) - 1.0) <= 1e-5))
+            return set_error(c, APTIDX_E_INVALID_ARG, "directions: |u[%d]| = %g is not 1", v, sqrt(n2));
+        d4[v] = make_float4(x, y, z, 0.f);
+    }
+    free_ptr(c->d_dirs);
+    c->nv = c->nv_pad = 0;
+    if ((rc = dev_alloc(c, (void**)&c->d_dirs, (size_t)nv_pad * sizeof(float4)))) return rc;
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_dirs, d4.data(), (size_t)nv_pad * sizeof(float4), cudaMemcpyHostToDevice,
+                                   c->stream));
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->nv = nv;
+    c->nv_pad = nv_pad;
+    for (int i = 0; i < kMaxCandidates; ++i) c->ref[i].nv_at_set = -1;   // references refer to old nodes
+    return APTIDX_OK;
+}
+
+int aptidx_set_binning(aptidx_ctx* ctx, int m, int32_t k_lo, int32_t k_hi, int flags) {
+    CTX_OR_FAIL(ctx);
+    if (m < APTIDX_MIN_M || m > APTIDX_MAX_M)
+        return set_error(c, APTIDX_E_INVALID_ARG, "m = %d outside [%d, %d]", m, APTIDX_MIN_M, APTIDX_MAX_M);
+    if (k_lo < 0 || k_hi < k_lo || k_hi > (1 << (m - 1)))
+        return set_error(c, APTIDX_E_INVALID_ARG, "band [%d, %d] outside [0, 2^(m-1)]", k_lo, k_hi);
+    if (flags != 0) return set_error(c, APTIDX_E_INVALID_ARG, "flags must be 0");
+    if (c->tw_m != m) {
+        free_ptr(c->d_tw);
+        c->tw_m = 0;
+        int rc = dev_alloc(c, (void**)&c->d_tw, sizeof(float2) << m);
+        if (rc) return rc;
+        cudaError_t e = launch_twiddles(c->d_tw, m, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "twiddles");
+        c->tw_m = m;
+    }
+    if (c->m != m && c->nroi > 0) free_rois(c);   // per-ROI scales depend on m
+    c->m = m;
+    c->k_lo = k_lo;
+    c->k_hi = k_hi;
+    c->binning_set = true;
+    return APTIDX_OK;
+}
+
+int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii, int64_t nroi,
+                    const int32_t* band_lo, const int32_t* band_hi, uint32_t type_mask, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (c->n_atoms <= 0) return set_error(c, APTIDX_E_STATE, "set_rois: load positions first");
+    if (c->nv <= 0) return set_error(c, APTIDX_E_STATE, "set_rois: set directions first");
+    if (!c->binning_set) return set_error(c, APTIDX_E_STATE, "set_rois: set binning first");
+    if (!centres || !radii || nroi <= 0 || nroi >= ((int64_t)1 << 30))
+        return set_error(c, APTIDX_E_INVALID_ARG, "set_rois: need 0 < nroi < 2^30 and centres, radii");
+    if ((band_lo == nullptr) != (band_hi == nullptr))
+        return set_error(c, APTIDX_E_INVALID_ARG, "set_rois: band_lo and band_hi must both be given or both NULL");
+    HostView<double> hc, hr;
+    HostView<int32_t> hlo, hhi;
+    if ((rc = to_host(c, centres, (size_t)nroi * 3, mem, hc))) return rc;
+    if ((rc = to_host(c, radii, (size_t)nroi, mem, hr))) return rc;
+    if (band_lo) {
+        if ((rc = to_host(c, band_lo, (size_t)nroi, mem, hlo))) return rc;
+        if ((rc = to_host(c, band_hi, (size_t)nroi, mem, hhi))) return rc;
+    }
+    const int half = 1 << (c->m - 1);
+    std::vector<float> scale((size_t)nroi);
+    std::vector<int32_t> band((size_t)nroi * 2);
+    int32_t bmin = 1 << 30, bmax = -1;
+    double rmax = 0.0;
+    for (int64_t r = 0; r < nroi; ++r) {
+        for (int d = 0; d < 3; ++d)
+            if (!isfinite(hc[3 * r + d])) return set_error(c, APTIDX_E_INVALID_ARG, "centre %lld not finite", (long long)r);
+        const double R = hr[r];
+        if (!(R > 0.0) || !isfinite(R)) return set_error(c, APTIDX_E_INVALID_ARG, "radius %lld must be > 0", (long long)r);
+        scale[r] = (float)((double)(half - 1) / R);
+        int32_t lo = band_lo ? hlo[r] : c->k_lo, hi = band_lo ? hhi[r] : c->k_hi;
+        if (lo < 0 || hi < lo || hi > half)
+            return set_error(c, APTIDX_E_INVALID_ARG, "band of ROI %lld [%d, %d] outside [0, %d]", (long long)r, lo, hi, half);
+        band[2 * r] = lo;
+        band[2 * r + 1] = hi;
+        bmin = std::min(bmin, lo);
+        bmax = std::max(bmax, hi);
+        rmax = std::max(rmax, R);
+    }
+    free_rois(c);
+    if ((rc = dev_alloc(c, (void**)&c->d_centres, (size_t)nroi * 3 * sizeof(double)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_radii, (size_t)nroi * sizeof(double)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_scale, (size_t)nroi * sizeof(float)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_band, (size_t)nroi * 2 * sizeof(int32_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_nw, (size_t)nroi * sizeof(int32_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_nw64, (size_t)nroi * sizeof(int64_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_off, (size_t)(nroi + 1) * sizeof(int64_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_order, (size_t)nroi * sizeof(int32_t)))) return rc;
+    c->scan_tmp_elems = 0;
+    if ((rc = ensure_scan_tmp(c, std::max<int64_t>(nroi, c->n_cells)))) return rc;
+    cudaStream_t s = c->stream;
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_centres, hc.data(), (size_t)nroi * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_radii, hr.data(), (size_t)nroi * sizeof(double), cudaMemcpyHostToDevice, s));
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_scale, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_band, band.data(), band.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    c->nroi = nroi;
+    c->band_min = bmin;
+    c->band_max = bmax;
+    c->type_mask = type_mask;
+    c->r_max = rmax;
+    // cell grid sized for the largest ROI (edge ~ R_max / 2, at least 0.25 nm)
+    const double want_h = std::max(rmax / 2.0, 0.25);
+    if (c->cell_h <= 0.0 || c->cell_h < 0.7 * want_h || c->cell_h > 1.5 * want_h) {
+        if ((rc = build_grid(c, want_h))) {
+            free_rois(c);
+            return rc;
+        }
+        if ((rc = ensure_scan_tmp(c, std::max<int64_t>(nroi, c->n_cells)))) return rc;
+    }
+    // count the ROI atoms once to size the gather buffer
+    APTIDX_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    cudaError_t e = launch_gather_count(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "ROI count");
+    std::vector<int32_t> hnw((size_t)nroi);
+    APTIDX_CUDA(c, cudaMemcpyAsync(hnw.data(), c->d_nw, (size_t)nroi * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    APTIDX_CUDA(c, cudaStreamSynchronize(s));
+    int64_t total = 0;
+    int32_t nwmax = 0;
+    for (int64_t r = 0; r < nroi; ++r) {
+        total += hnw[r];
+        nwmax = std::max(nwmax, hnw[r]);
+    }
+    if (nwmax > APTIDX_MAX_ATOMS_PER_ROI) {
+        APTIDX_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+        free_rois(c);
+        return set_error(c, APTIDX_E_OVERFLOW, "a ROI holds %d selected atoms (limit %d)", nwmax,
+                         APTIDX_MAX_ATOMS_PER_ROI);
+    }
+    c->nw_max = nwmax;
+    c->atoms_total = total;
+    c->atoms_cap = std::max<int64_t>(total, 1);
+    if ((rc = dev_alloc(c, (void**)&c->d_atoms, (size_t)c->atoms_cap * sizeof(float4)))) return rc;
+    return read_status(c);
+}
+
+int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* S, uint16_t* argk,
+                              int32_t* n_atoms, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "compute_signatures: set ROIs first");
+    if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
+        return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
+    if (flags & ~APTIDX_NORMALISE_MAX) return set_error(c, APTIDX_E_INVALID_ARG, "unknown flags 0x%x", flags);
+    const int64_t nS = c->nroi * (int64_t)c->nv;
+    float* dS = S;
+    uint16_t* dA = argk;
+    if (mem == APTIDX_MEM_HOST || !S) {
+        if (c->S_cap < nS) {
+            free_ptr(c->d_S);
+            free_ptr(c->d_argk);
+            c->S_cap = 0;
+            if ((rc = dev_alloc(c, (void**)&c->d_S, (size_t)nS * sizeof(float)))) return rc;
+            if ((rc = dev_alloc(c, (void**)&c->d_argk, (size_t)nS * sizeof(uint16_t)))) return rc;
+            c->S_cap = nS;
+        }
+        dS = c->d_S;
+        dA = argk ? c->d_argk : nullptr;
+    }
+    if (path == APTIDX_PATH_TC_FP16 && (rc = prepare_tc(c))) return rc;
+    prof_begin(c, APTIDX_PHASE_GATHER);
+    if ((rc = run_gather(c))) return rc;
+    prof_end(c, APTIDX_PHASE_GATHER, 6);
+    prof_begin(c, APTIDX_PHASE_ORDER);
+    cudaError_t e = launch_roi_order(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "ROI order");
+    prof_end(c, APTIDX_PHASE_ORDER, 3);
+    prof_begin(c, APTIDX_PHASE_SIGNATURE);
+    if (path == APTIDX_PATH_PLAIN_FP32) {
+        e = launch_signatures_plain(c, dS, dA, nullptr, -1);
+    } else {
+        e = launch_signatures_tc(c, dS, dA, nullptr, -1);
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "signature kernel");
+    prof_end(c, APTIDX_PHASE_SIGNATURE, 1);
+    if (flags & APTIDX_NORMALISE_MAX) {
+        prof_begin(c, APTIDX_PHASE_NORMALISE);
+        e = launch_normalise(c, dS);
+        if (e != cudaSuccess) return cuda_check(c, e, "normalise");
+        prof_end(c, APTIDX_PHASE_NORMALISE, 1);
+    }
+    if (mem == APTIDX_MEM_HOST) {
+        if (S) APTIDX_CUDA(c, cudaMemcpyAsync(S, dS, (size_t)nS * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        if (argk)
+            APTIDX_CUDA(c, cudaMemcpyAsync(argk, dA, (size_t)nS * sizeof(uint16_t), cudaMemcpyDeviceToHost, c->stream));
+        if (n_atoms)
+            APTIDX_CUDA(c, cudaMemcpyAsync(n_atoms, c->d_nw, (size_t)c->nroi * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                           c->stream));
+        return read_status(c);
+    }
+    if (n_atoms)
+        APTIDX_CUDA(c, cudaMemcpyAsync(n_atoms, c->d_nw, (size_t)c->nroi * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                       c->stream));
+    return APTIDX_OK;
+}
+
+int aptidx_path_supported(aptidx_ctx* ctx, int path) {
+    if (!ctx) return 0;
+    if (path == APTIDX_PATH_PLAIN_FP32) return 1;
+    if (path == APTIDX_PATH_TC_FP16) return tc_supported(&ctx->c) ? 1 : 0;
+    return 0;
+}
+
+int aptidx_set_profiling(aptidx_ctx* ctx, int enable) {
+    CTX_OR_FAIL(ctx);
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& pr : c->ev_pending) {
+        c->ev_pool.push_back(pr.a);
+        c->ev_pool.push_back(pr.b);
+    }
+    c->ev_pending.clear();
+    for (int i = 0; i < APTIDX_N_PHASES; ++i) {
+        if (c->ev_open[i]) c->ev_pool.push_back(c->ev_open[i]);
+        c->ev_open[i] = nullptr;
+        c->prof_ms[i] = 0.0;
+        c->prof_calls[i] = 0;
+    }
+    c->launches = 0;
+    c->prof = enable != 0;
+    return APTIDX_OK;
+}
+
+int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, int64_t* launches) {
+    CTX_OR_FAIL(ctx);
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& pr : c->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess) {
+            c->prof_ms[pr.phase] += ms;
+            c->prof_calls[pr.phase] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        c->ev_pool.push_back(pr.a);
+        c->ev_pool.push_back(pr.b);
+    }
+    c->ev_pending.clear();
+    for (int i = 0; i < APTIDX_N_PHASES; ++i) {
+        if (phase_ms) phase_ms[i] = c->prof_ms[i];
+        if (phase_calls) phase_calls[i] = c->prof_calls[i];
+    }
+    if (launches) *launches = c->launches;
+    return APTIDX_OK;
+}
+
+int aptidx_get_histograms(aptidx_ctx* ctx, int64_t roi, int path, uint16_t* h, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "get_histograms: set ROIs first");
+    if (roi < 0 || roi >= c->nroi || !h) return set_error(c, APTIDX_E_INVALID_ARG, "get_histograms: bad roi or NULL h");
+    if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
+        return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
+    const size_t n = (size_t)c->nv << c->m;
+    uint16_t* dh = h;
+    if (mem == APTIDX_MEM_HOST && (rc = dev_alloc(c, (void**)&dh, n * sizeof(uint16_t)))) return rc;
+    // scratch signature row for the single ROI
+    float* row = nullptr;
+    if ((rc = dev_alloc(c, (void**)&row, (size_t)c->nv * sizeof(float)))) {
+        if (mem == APTIDX_MEM_HOST) dev_free(dh);
+        return rc;
+    }
+    rc = run_gather(c);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        if (path == APTIDX_PATH_PLAIN_FP32) {
+            e = launch_signatures_plain(c, row, nullptr, dh, roi);
+        } else {
+            rc = prepare_tc(c);
+            if (!rc) e = launch_signatures_tc(c, row, nullptr, dh, roi);
+        }
+        if (!rc && e != cudaSuccess) rc = cuda_check(c, e, "histogram export");
+    }
+    if (!rc && mem == APTIDX_MEM_HOST) {
+        e = cudaMemcpyAsync(h, dh, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) rc = cuda_check(c, e, "copy histograms");
+    }
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (!rc && e2 != cudaSuccess) rc = cuda_check(c, e2, "sync");
+    dev_free(row);
+    if (mem == APTIDX_MEM_HOST) dev_free(dh);
+    if (rc) return rc;
+    return read_status(c);
+}
+
+int aptidx_get_roi_atoms(aptidx_ctx* ctx, int64_t roi, float* xc, int64_t cap, int64_t* n_out, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "get_roi_atoms: set ROIs first");
+    if (roi < 0 || roi >= c->nroi || !n_out) return set_error(c, APTIDX_E_INVALID_ARG, "get_roi_atoms: bad arguments");
+    if ((rc = run_gather(c))) return rc;
+    int64_t off[2];
+    APTIDX_CUDA(c, cudaMemcpyAsync(off, c->d_off + roi, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int64_t n = off[1] - off[0];
+    *n_out = n;
+    if (n > cap || (n > 0 && !xc)) return set_error(c, APTIDX_E_OVERFLOW, "get_roi_atoms: %lld atoms exceed cap %lld", (long long)n, (long long)cap);
+    std::vector<float4> tmp((size_t)n);
+    if (n > 0) {
+        APTIDX_CUDA(c, cudaMemcpyAsync(tmp.data(), c->d_atoms + off[0], (size_t)n * sizeof(float4), cudaMemcpyDeviceToHost,
+                                       c->stream));
+        APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    std::vector<float> packed((size_t)n * 3);
+    for (int64_t i = 0; i < n; ++i) {
+        packed[3 * i] = tmp[i].x;
+        packed[3 * i + 1] = tmp[i].y;
+        packed[3 * i + 2] = tmp[i].z;
+    }
+    if (n > 0) {
+        APTIDX_CUDA(c, cudaMemcpyAsync(xc, packed.data(), packed.size() * sizeof(float),
+                                       mem == APTIDX_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice,
+                                       c->stream));
+        APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return read_status(c);
+}
+
+}  // extern "C"

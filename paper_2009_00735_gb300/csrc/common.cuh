@@ -1,0 +1,132 @@
+// common.cuh -- device helpers shared by the aptidx kernels: the binning
+// contract of Eq. 1, bounded mbarrier waits, bulk (TMA) copies.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace aptidx {
+
+template <typename T>
+__host__ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <typename T>
+__host__ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+// -----------------------------------------------------------------------------
+// Eq. 1, the bin of a projected atom.  With dR = R / (2^(m-1) - 1) (Fig. 2
+// caption) Eq. 1 is b = floor(2^(m-1) + s (2^(m-1) - 1) / R).  The library
+// evaluates s in FP32 with a fixed fma order and takes the floor of the exact
+// product s * scale: one fma rounding toward -inf onto the integer grid of
+// [2^23, 2^24), whose bit pattern is 0x4B000000 + integer part.
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ float project_f32(float ux, float uy, float uz, float4 a) {
+    return __fmaf_rn(uz, a.z, __fmaf_rn(uy, a.y, __fmul_rn(ux, a.x)));
+}
+
+// magic = 2^23 + 2^(m-1) as float
+__host__ __device__ __forceinline__ float bin_magic(int m) {
+    return 8388608.0f + (float)(1 << (m - 1));
+}
+
+__device__ __forceinline__ int bin_of(float s, float scale, float magic, int nb_minus_1) {
+    int b = __float_as_int(__fmaf_rd(s, scale, magic)) - 0x4B000000;
+    return min(max(b, 0), nb_minus_1);
+}
+
+// exact small non-negative integer (< 2^23) to float with one integer op and
+// one FP32 add (no conversion-pipe instruction)
+__device__ __forceinline__ float u23_to_float(uint32_t c) {
+    return __int_as_float(0x4B000000 | c) - 8388608.0f;
+}
+
+// -----------------------------------------------------------------------------
+// status word
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ void raise_status(int* status, int bit) {
+    atomicOr(status, bit);
+}
+
+// -----------------------------------------------------------------------------
+// shared-memory addresses, mbarriers and bulk copies (inline PTX)
+// -----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, at most `limit` polls.  Returns
+// false (and raises the timeout status bit) if the phase never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status,
+                                                  uint32_t limit = (1u << 22)) {
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    raise_status(status, kStatusTimeout);
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted in bytes on
+// `bar`.  dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Stage `n` float4 atoms from global into shared memory with one bulk copy
+// issued by thread 0, then make them visible to the whole CTA.  `phase` is
+// the barrier's parity bit, toggled per use.  Returns false on a timeout
+// (every thread of the CTA returns the same value).
+__device__ __forceinline__ bool stage_atoms(float4* dst, const float4* src, int n, uint64_t* bar,
+                                            uint32_t& phase, int* status, int* flag_smem) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (n > 0) {
+            fence_proxy_async_smem();   // earlier generic reads of dst before the async write
+            mbar_arrive_expect_tx(bar, (uint32_t)n * 16u);
+            bulk_g2s(dst, src, (uint32_t)n * 16u, bar);
+            ok = mbar_wait_bounded(bar, phase, status) ? 1 : 0;
+            if (!ok) mbar_wait_bounded(bar, phase, status, 1u << 20);   // let an in-flight copy land
+            phase ^= 1u;
+        }
+        *flag_smem = ok;
+    }
+    __syncthreads();
+    int ok = *flag_smem;
+    if (threadIdx.x != 0 && n > 0) phase ^= 1u;
+    __syncthreads();   // flag_smem is rewritten by the next call
+    return ok != 0;
+}
+
+}  // namespace aptidx

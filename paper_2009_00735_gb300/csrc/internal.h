@@ -1,0 +1,170 @@
+// internal.h -- context and launch prototypes of the aptidx library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "aptidx.h"
+
+namespace aptidx {
+
+constexpr int kMaxCandidates = 8;
+constexpr int kImgRows = 181;   // elevation -90..90 deg, 1 deg
+constexpr int kImgCols = 360;   // azimuth 0..359 deg, 1 deg
+constexpr int kTileDirs = 64;   // directions per signature work item
+
+// device status word bits
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusOverflow = 2;
+
+struct Reference {
+    float* d_node_sig = nullptr;   // [nv] normalised reference signature
+    int32_t* d_top = nullptr;      // [n_hat] strongest nodes, strongest first
+    float* d_top_val = nullptr;    // [n_hat] their values
+    int32_t n_hat = 0;
+    float* d_img = nullptr;        // [181 x 360] or null
+    int32_t* d_lut = nullptr;      // [ng x n_hat]
+    int64_t ng = 0;
+    int32_t nv_at_set = 0;
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+
+    // positions
+    int64_t n_atoms = 0;
+    float* d_pos = nullptr;        // [n x 3]
+    uint8_t* d_types = nullptr;    // [n] or null
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+
+    // uniform cell grid over the positions
+    double cell_h = 0.0;
+    int dims[3] = {0, 0, 0};
+    int64_t n_cells = 0;
+    int64_t* d_cell_start = nullptr;   // [n_cells + 1]
+    float4* d_cell_pos = nullptr;      // [n] positions in cell order, w = type (as float)
+
+    // directions (padded to a multiple of kTileDirs with (1, 0, 0))
+    int32_t nv = 0, nv_pad = 0;
+    float4* d_dirs = nullptr;
+
+    // binning
+    int m = 0;
+    int32_t k_lo = 0, k_hi = 0;
+    bool binning_set = false;
+    float2* d_tw = nullptr;            // [2^m] (cos, sin)(2 pi j / 2^m), FP32
+    int tw_m = 0;
+    // tensor-core twiddle operand (B): [n_cols] hi/lo FP16 in canonical layout
+    void* d_twb = nullptr;
+    size_t twb_bytes = 0;
+    int twb_key[3] = {-1, -1, -1};     // (m, band_min, n_cols)
+
+    // ROIs
+    int64_t nroi = 0;
+    double* d_centres = nullptr;       // [nroi x 3]
+    double* d_radii = nullptr;         // [nroi]
+    float* d_scale = nullptr;          // [nroi] (float)((2^(m-1)-1)/R)
+    int32_t* d_band = nullptr;         // [nroi x 2] (k_lo, k_hi)
+    int32_t band_min = 0, band_max = 0;
+    uint32_t type_mask = 0xFFFFFFFFu;
+    double r_max = 0.0;
+
+    // gather output (CSR)
+    int32_t* d_nw = nullptr;           // [nroi]
+    int64_t* d_nw64 = nullptr;         // [nroi] widened counts (scan input)
+    int64_t* d_off = nullptr;          // [nroi + 1]
+    float4* d_atoms = nullptr;         // [total] centred FP32 (x, y, z, 0)
+    int64_t atoms_cap = 0;
+    int64_t atoms_total = 0;
+    int32_t nw_max = 0;
+
+    // scheduling scratch
+    int32_t* d_order = nullptr;        // [nroi] ROI order (largest first)
+    int32_t* d_counter = nullptr;      // [4] work counters
+    int32_t* d_sort_hist = nullptr;    // [65536 + 1]
+    int64_t* d_scan_tmp = nullptr;     // scan block sums
+    size_t scan_tmp_elems = 0;
+
+    // library-owned outputs used when the caller passes host buffers
+    float* d_S = nullptr;
+    uint16_t* d_argk = nullptr;
+    int64_t S_cap = 0;
+
+    // status word
+    int* d_status = nullptr;
+
+    Reference ref[kMaxCandidates];
+
+    // refinement scratch
+    double* d_q = nullptr;
+    double* d_acc = nullptr;           // [nroi x 16] FP64 accumulators
+    int64_t q_cap = 0;
+
+    // profiling (CUDA events on the stream around phases)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct EvPair { int phase; cudaEvent_t a, b; };
+    std::vector<EvPair> ev_pending;
+    cudaEvent_t ev_open[APTIDX_N_PHASES] = {};
+    double prof_ms[APTIDX_N_PHASES] = {};
+    int64_t prof_calls[APTIDX_N_PHASES] = {};
+    int64_t launches = 0;
+};
+
+// profiling helpers (no-ops unless profiling is enabled)
+void prof_begin(Ctx* c, int phase);
+void prof_end(Ctx* c, int phase, int kernels);
+
+// error helpers ---------------------------------------------------------------
+int set_error(Ctx* c, int code, const char* fmt, ...);
+int cuda_check(Ctx* c, cudaError_t e, const char* what);
+#define APTIDX_CUDA(ctx, call)                                    \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return ::aptidx::cuda_check(ctx, _e, #call); \
+    } while (0)
+
+int dev_alloc(Ctx* c, void** p, size_t bytes);
+void dev_free(void* p);
+
+// launches (all async on c->stream) -----------------------------------------
+cudaError_t launch_bbox(const float* pos, int64_t n, float* d_minmax, cudaStream_t s);
+cudaError_t launch_cell_build(Ctx* c, int32_t* d_cell_of, int32_t* d_cursor, int64_t* d_counts,
+                              int32_t* d_idx);
+cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
+size_t scan_tmp_elems(int64_t n);
+cudaError_t launch_gather_count(Ctx* c);
+cudaError_t launch_gather_fill(Ctx* c);
+cudaError_t launch_roi_order(Ctx* c);
+cudaError_t launch_twiddles(float2* tw, int m, cudaStream_t s);
+
+// signature kernels
+cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out,
+                                    int64_t hist_roi);
+cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out,
+                                 int64_t hist_roi);
+int prepare_tc(Ctx* c);
+bool tc_supported(Ctx* c);
+cudaError_t launch_normalise(Ctx* c, float* S);
+
+// indexing / refinement
+cudaError_t launch_top_nodes(Ctx* c, Reference* r);
+cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng);
+cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best,
+                         float* score);
+cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q, int64_t nroi,
+                               float* loss, float* grad, double* acc);
+cudaError_t launch_refine_update(Ctx* c, double* q, const double* acc, int64_t nroi);
+cudaError_t launch_refine_finish(Ctx* c, double* q, int64_t nroi);
+
+}  // namespace aptidx
+
+struct aptidx_ctx {
+    aptidx::Ctx c;
+};

@@ -1,0 +1,332 @@
+// signature_plain.cu -- steps (a2)-(a5) on CUDA cores, FP32: projection (Eq. 1
+// dot product), binning into 2^m-bin histograms, the band of the DFT
+// amplitude spectrum (Section 2.2), and the per-direction band maximum (the
+// signature value, supplement "Al bicrystal").
+//
+// Work item = (ROI, group of 64-direction tiles).  A persistent grid claims
+// items from a global counter, ROIs in longest-first order.  Per item the
+// ROI's centred atoms are copied into shared memory once (bulk copy on the
+// TMA engine).  Per tile every warp walks a strided subset of the atoms; lane
+// l owns directions 2l and 2l+1 and adds 1 to 16-bit halves of the word
+// H[b * 32 + l].  A lane's words sit in bank l whatever the bin, so the
+// shared-memory atomics of one warp instruction never conflict.
+// The band spectrum X(k) = sum_n h[n] e^{-2 pi i k n / 2^m} is then
+// accumulated in FP32 against a (cos, sin) table; the twiddle index is
+// uniform across a warp, so table reads are broadcasts.
+#include "common.cuh"
+
+namespace aptidx {
+
+namespace {
+
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kDirs = kTileDirs;        // 64 directions per tile
+constexpr int kWords = kDirs / 2;       // u32 words per bin
+constexpr int kKpw = 4;                 // frequencies per warp unit
+constexpr int kPartBytes = kWarps * kKpw * kDirs * 8;
+
+struct SigParams {
+    const float4* atoms;
+    const int64_t* off;
+    const int32_t* nw;
+    const int32_t* order;
+    const float4* dirs;
+    int32_t nv;
+    int32_t tiles_per_roi;
+    int32_t tiles_per_item;
+    int32_t items_per_roi;
+    int64_t n_items;
+    const float* scale;
+    const int32_t* band;
+    int m;
+    const float2* tw;
+    float* S;
+    uint16_t* argk;
+    uint16_t* hist_out;
+    int64_t single_roi;
+    int32_t* counter;
+    int* status;
+    int atom_cap;
+};
+
+__device__ __forceinline__ void process_atom(uint32_t* H, int lane, float4 a, float4 d0, float4 d1, float scale,
+                                             float magic, int nbm1) {
+    const float s0 = project_f32(d0.x, d0.y, d0.z, a);
+    const float s1 = project_f32(d1.x, d1.y, d1.z, a);
+    const int b0 = bin_of(s0, scale, magic, nbm1);
+    const int b1 = bin_of(s1, scale, magic, nbm1);
+    atomicAdd(&H[b0 * kWords + lane], 1u);
+    atomicAdd(&H[b1 * kWords + lane], 0x10000u);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int NB = 1 << p.m;
+    const int nbm1 = NB - 1;
+    uint32_t* H = reinterpret_cast<uint32_t*>(smem);
+    float2* TW = reinterpret_cast<float2*>(smem + (size_t)NB * kWords * 4);
+    float4* A = reinterpret_cast<float4*>(smem + (size_t)NB * kWords * 4 + (size_t)NB * 8);
+    float2* PART = reinterpret_cast<float2*>(A + p.atom_cap);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(PART) + kPartBytes);
+    int* flag = reinterpret_cast<int*>(bar + 1);
+    int64_t* item_s = reinterpret_cast<int64_t*>(bar + 2);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < NB; j += kThreads) TW[j] = p.tw[j];
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const float magic = bin_magic(p.m);
+
+    for (;;) {
+        if (tid == 0) *item_s = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int64_t item = *item_s;
+        __syncthreads();
+        if (item >= p.n_items) break;
+        const int64_t roi_rank = item / p.items_per_roi;
+        const int grp = (int)(item % p.items_per_roi);
+        const int64_t roi = p.single_roi >= 0 ? p.single_roi : (int64_t)p.order[roi_rank];
+        const int nw = p.nw[roi];
+        const int64_t abase = p.off[roi];
+        const float scale = p.scale[roi];
+        const int klo = p.band[2 * roi], khi = p.band[2 * roi + 1];
+        const int t0 = grp * p.tiles_per_item;
+        const int t1 = min(t0 + p.tiles_per_item, p.tiles_per_roi);
+        const bool one_chunk = nw <= p.atom_cap;
+        if (one_chunk && !stage_atoms(A, p.atoms + abase, nw, bar, phase, p.status, flag)) return;
+
+        for (int tile = t0; tile < t1; ++tile) {
+            uint4* H4 = reinterpret_cast<uint4*>(H);
+            for (int i = tid; i < NB * kWords / 4; i += kThreads) H4[i] = make_uint4(0, 0, 0, 0);
+            const float4 d0 = p.dirs[(int64_t)tile * kDirs + 2 * lane];
+            const float4 d1 = p.dirs[(int64_t)tile * kDirs + 2 * lane + 1];
+            __syncthreads();
+            for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
+                const int cn = min(p.atom_cap, nw - c0);
+                if (!one_chunk && !stage_atoms(A, p.atoms + abase + c0, cn, bar, phase, p.status, flag)) return;
+                int j = warp;
+                for (; j + 3 * kWarps < cn; j += 4 * kWarps) {
+                    const float4 a0 = A[j], a1 = A[j + kWarps], a2 = A[j + 2 * kWarps], a3 = A[j + 3 * kWarps];
+                    process_atom(H, lane, a0, d0, d1, scale, magic, nbm1);
+                    process_atom(H, lane, a1, d0, d1, scale, magic, nbm1);
+                    process_atom(H, lane, a2, d0, d1, scale, magic, nbm1);
+                    process_atom(H, lane, a3, d0, d1, scale, magic, nbm1);
+                }
+                for (; j < cn; j += kWarps) process_atom(H, lane, A[j], d0, d1, scale, magic, nbm1);
+                if (!one_chunk) __syncthreads();
+            }
+            __syncthreads();
+
+            if (p.hist_out) {
+                for (int i = tid; i < NB * kWords; i += kThreads) {
+                    const int b = i / kWords, l = i % kWords;
+                    const uint32_t w = H[i];
+                    const int64_t v0 = (int64_t)tile * kDirs + 2 * l;
+                    if (v0 < p.nv) p.hist_out[v0 * NB + b] = (uint16_t)(w & 0xFFFFu);
+                    if (v0 + 1 < p.nv) p.hist_out[(v0 + 1) * NB + b] = (uint16_t)(w >> 16);
+                }
+            }
+
+            // ---- band spectrum (FP32) and band maximum ----
+            const int K = khi - klo + 1;
+            const int G = (K + kKpw - 1) / kKpw;   // frequency groups of kKpw
+            const int64_t out_base = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv + (int64_t)tile * kDirs;
+            if (G <= kWarps) {
+                int nsplit = 1;
+                while (G * nsplit * 2 <= kWarps && nsplit * 2 <= NB / 32) nsplit *= 2;
+                const int span = NB / nsplit;
+                const int units = G * nsplit;
+                if (warp < units) {
+                    const int g = warp / nsplit, sp = warp % nsplit;
+                    const int k0 = klo + g * kKpw;
+                    float re[kKpw][2], im[kKpw][2];
+                    unsigned idx[kKpw];
+                    const int n0 = sp * span;
+#pragma unroll
+                    for (int q = 0; q < kKpw; ++q) {
+                        re[q][0] = re[q][1] = im[q][0] = im[q][1] = 0.f;
+                        idx[q] = (unsigned)((k0 + q) * n0) & (unsigned)nbm1;
+                    }
+                    for (int n = n0; n < n0 + span; ++n) {
+                        const uint32_t w = H[n * kWords + lane];
+                        const float f0 = u23_to_float(w & 0xFFFFu), f1 = u23_to_float(w >> 16);
+#pragma unroll
+                        for (int q = 0; q < kKpw; ++q) {
+                            const float2 t = TW[idx[q]];
+                            re[q][0] = fmaf(f0, t.x, re[q][0]);
+                            im[q][0] = fmaf(f0, t.y, im[q][0]);
+                            re[q][1] = fmaf(f1, t.x, re[q][1]);
+                            im[q][1] = fmaf(f1, t.y, im[q][1]);
+                            idx[q] = (idx[q] + (unsigned)(k0 + q)) & (unsigned)nbm1;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kKpw; ++q) {
+                        PART[((size_t)warp * kKpw + q) * kDirs + 2 * lane] = make_float2(re[q][0], im[q][0]);
+                        PART[((size_t)warp * kKpw + q) * kDirs + 2 * lane + 1] = make_float2(re[q][1], im[q][1]);
+                    }
+                }
+                __syncthreads();
+                if (tid < kDirs) {
+                    const int64_t v = (int64_t)tile * kDirs + tid;
+                    float best = -1.f;
+                    int bk = klo;
+                    for (int kk = 0; kk < K; ++kk) {
+                        const int g = kk / kKpw, q = kk % kKpw;
+                        float sr = 0.f, si = 0.f;
+                        for (int sp = 0; sp < nsplit; ++sp) {
+                            const float2 t = PART[((size_t)(g * nsplit + sp) * kKpw + q) * kDirs + tid];
+                            sr += t.x;
+                            si += t.y;
+                        }
+                        const float a = sqrtf(sr * sr + si * si);
+                        if (a > best) {
+                            best = a;
+                            bk = klo + kk;
+                        }
+                    }
+                    if (v < p.nv) {
+                        p.S[out_base + tid] = best;
+                        if (p.argk) p.argk[out_base + tid] = (uint16_t)bk;
+                    }
+                }
+            } else {
+                float b0 = -1.f, b1 = -1.f;
+                int bk0 = klo, bk1 = klo;
+                for (int g = warp; g < G; g += kWarps) {
+                    const int k0 = klo + g * kKpw;
+                    float re[kKpw][2], im[kKpw][2];
+                    unsigned idx[kKpw];
+#pragma unroll
+                    for (int q = 0; q < kKpw; ++q) {
+                        re[q][0] = re[q][1] = im[q][0] = im[q][1] = 0.f;
+                        idx[q] = 0;
+                    }
+                    for (int n = 0; n < NB; ++n) {
+                        const uint32_t w = H[n * kWords + lane];
+                        const float f0 = u23_to_float(w & 0xFFFFu), f1 = u23_to_float(w >> 16);
+#pragma unroll
+                        for (int q = 0; q < kKpw; ++q) {
+                            const float2 t = TW[idx[q]];
+                            re[q][0] = fmaf(f0, t.x, re[q][0]);
+                            im[q][0] = fmaf(f0, t.y, im[q][0]);
+                            re[q][1] = fmaf(f1, t.x, re[q][1]);
+                            im[q][1] = fmaf(f1, t.y, im[q][1]);
+                            idx[q] = (idx[q] + (unsigned)(k0 + q)) & (unsigned)nbm1;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kKpw; ++q) {
+                        if (k0 + q > khi) break;
+                        const float a0 = sqrtf(re[q][0] * re[q][0] + im[q][0] * im[q][0]);
+                        const float a1 = sqrtf(re[q][1] * re[q][1] + im[q][1] * im[q][1]);
+                        if (a0 > b0) { b0 = a0; bk0 = k0 + q; }
+                        if (a1 > b1) { b1 = a1; bk1 = k0 + q; }
+                    }
+                }
+                PART[(size_t)warp * kDirs + 2 * lane] = make_float2(b0, __int_as_float(bk0));
+                PART[(size_t)warp * kDirs + 2 * lane + 1] = make_float2(b1, __int_as_float(bk1));
+                __syncthreads();
+                if (tid < kDirs) {
+                    const int64_t v = (int64_t)tile * kDirs + tid;
+                    float best = -1.f;
+                    int bk = klo;
+                    for (int w = 0; w < kWarps; ++w) {
+                        const float2 t = PART[(size_t)w * kDirs + tid];
+                        const int k = __float_as_int(t.y);
+                        if (t.x > best || (t.x == best && k < bk)) {
+                            best = t.x;
+                            bk = k;
+                        }
+                    }
+                    if (v < p.nv) {
+                        p.S[out_base + tid] = best;
+                        if (p.argk) p.argk[out_base + tid] = (uint16_t)bk;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// per-ROI normalisation (supplement "Indexing algorithm", step 1): S / max_v S
+__global__ void __launch_bounds__(256) k_normalise(float* S, int32_t nv) {
+    __shared__ float red[8];
+    float* row = S + (int64_t)blockIdx.x * nv;
+    float mx = 0.f;
+    for (int v = threadIdx.x; v < nv; v += 256) mx = fmaxf(mx, row[v]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+    const float inv = mx > 0.f ? 1.0f / mx : 0.f;
+    for (int v = threadIdx.x; v < nv; v += 256) row[v] = mx > 0.f ? row[v] * inv : 0.f;
+}
+
+}  // namespace
+
+cudaError_t launch_normalise(Ctx* c, float* S) {
+    if (c->nroi <= 0) return cudaSuccess;
+    k_normalise<<<(unsigned)c->nroi, 256, 0, c->stream>>>(S, c->nv);
+    return cudaGetLastError();
+}
+
+size_t plain_smem_bytes(int m, int atom_cap) {
+    const size_t NB = (size_t)1 << m;
+    return NB * kWords * 4 + NB * 8 + (size_t)atom_cap * 16 + kPartBytes + 64;
+}
+
+cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out, int64_t hist_roi) {
+    static int max_optin = -1;
+    if (max_optin < 0) {
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    }
+    const size_t base = plain_smem_bytes(c->m, 0);
+    int cap = (int)(((size_t)max_optin - base) / 16);
+    cap = min(cap, 4096) & ~15;
+    if (cap < 256) return cudaErrorInvalidConfiguration;
+    const size_t smem = plain_smem_bytes(c->m, cap);
+    cudaError_t e = cudaFuncSetAttribute(k_sig_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+
+    SigParams p;
+    p.atoms = c->d_atoms;
+    p.off = c->d_off;
+    p.nw = c->d_nw;
+    p.order = c->d_order;
+    p.dirs = c->d_dirs;
+    p.nv = c->nv;
+    p.tiles_per_roi = c->nv_pad / kDirs;
+    p.tiles_per_item = min(16, p.tiles_per_roi);
+    p.items_per_roi = (p.tiles_per_roi + p.tiles_per_item - 1) / p.tiles_per_item;
+    const int64_t nroi_eff = hist_out ? 1 : c->nroi;
+    p.n_items = nroi_eff * p.items_per_roi;
+    p.scale = c->d_scale;
+    p.band = c->d_band;
+    p.m = c->m;
+    p.tw = c->d_tw;
+    p.S = S;
+    p.argk = argk;
+    p.hist_out = hist_out;
+    p.single_roi = hist_out ? hist_roi : -1;
+    p.counter = c->d_counter;
+    p.status = c->d_status;
+    p.atom_cap = cap;
+    if ((e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);
+    per_sm = max(per_sm, 1);
+    int64_t grid = tmin<int64_t>((int64_t)c->sm_count * per_sm, p.n_items);
+    if (grid < 1) return cudaSuccess;
+    k_sig_plain<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace aptidx
