@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-rois", type=int, default=0, help="oracle sample size (0: sized for ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rois", type=int, default=0,
+                    help="use only the first N ROIs (a smaller case for profiling; 0: all 8192)")
     return ap.parse_args()
 
 
@@ -191,6 +193,10 @@ def run_gb300(args):
     B.build()
     # weak scaling: every rank processes its own replica batch (own seed)
     w = synth.single_crystal_bcc(seed=synth.SEED_BASE + 2 + rank)
+    if args.rois > 0:
+        w.centres = np.ascontiguousarray(w.centres[: args.rois])
+        w.radii = np.ascontiguousarray(w.radii[: args.rois])
+        w.name += f"-first{args.rois}"
     R = float(w.radii[0])
     band = apt.band_for_spacing(*w.d_spacing, R, w.m)
     nroi, nv = w.centres.shape[0], w.dirs.shape[0]

@@ -393,28 +393,26 @@ __global__ void k_order_hist(const int32_t* __restrict__ nw, int64_t n, int32_t*
     if (i < n) atomicAdd(&hist[65535 - min(nw[i], 65535)], 1);
 }
 
-__global__ void k_order_scan(int32_t* hist) {
-    // single block, 1024 threads, 64 entries each
-    __shared__ int32_t part[1024];
-    int t = threadIdx.x;
-    int32_t loc[64];
+__global__ void __launch_bounds__(256) k_order_scan(int32_t* hist) {
+    // single block of 256 threads, 256 consecutive entries each
+    __shared__ int32_t part[256];
+    const int t = threadIdx.x;
+    int32_t* h = hist + t * 256;
     int32_t s = 0;
-    for (int i = 0; i < 64; ++i) {
-        loc[i] = hist[t * 64 + i];
-        s += loc[i];
-    }
+    for (int i = 0; i < 256; ++i) s += h[i];
     part[t] = s;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
+    for (int off = 1; off < 256; off <<= 1) {
         int32_t v = t >= off ? part[t - off] : 0;
         __syncthreads();
         part[t] += v;
         __syncthreads();
     }
     int32_t ex = part[t] - s;
-    for (int i = 0; i < 64; ++i) {
-        hist[t * 64 + i] = ex;
-        ex += loc[i];
+    for (int i = 0; i < 256; ++i) {
+        int32_t x = h[i];
+        h[i] = ex;
+        ex += x;
     }
 }
 
@@ -432,7 +430,7 @@ cudaError_t launch_roi_order(Ctx* c) {
     if (e != cudaSuccess) return e;
     unsigned b = (unsigned)((c->nroi + 255) / 256);
     k_order_hist<<<b, 256, 0, s>>>(c->d_nw, c->nroi, c->d_sort_hist);
-    k_order_scan<<<1, 1024, 0, s>>>(c->d_sort_hist);
+    k_order_scan<<<1, 256, 0, s>>>(c->d_sort_hist);
     k_order_scatter<<<b, 256, 0, s>>>(c->d_nw, c->nroi, c->d_sort_hist, c->d_order);
     return cudaGetLastError();
 }
