@@ -452,6 +452,7 @@ int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii,
     APTIDX_CUDA(c, cudaMemcpyAsync(c->d_scale, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     APTIDX_CUDA(c, cudaMemcpyAsync(c->d_band, band.data(), band.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     c->nroi = nroi;
+    c->h_band = band;
     c->band_min = bmin;
     c->band_max = bmax;
     c->type_mask = type_mask;
@@ -525,7 +526,7 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
     prof_end(c, APTIDX_PHASE_ORDER, 3);
     prof_begin(c, APTIDX_PHASE_SIGNATURE);
     if (path == APTIDX_PATH_PLAIN_FP32) {
-        e = launch_signatures_plain(c, dS, dA, nullptr, -1);
+        e = launch_signatures_plain(c, dS, dA, nullptr, -1, 0);
     } else {
         e = launch_signatures_tc(c, dS, dA, nullptr, -1);
     }
@@ -622,7 +623,7 @@ int aptidx_get_histograms(aptidx_ctx* ctx, int64_t roi, int path, uint16_t* h, i
     cudaError_t e = cudaSuccess;
     if (!rc) {
         if (path == APTIDX_PATH_PLAIN_FP32) {
-            e = launch_signatures_plain(c, row, nullptr, dh, roi);
+            e = launch_signatures_plain(c, row, nullptr, dh, roi, 0);
         } else {
             rc = prepare_tc(c);
             if (!rc) e = launch_signatures_tc(c, row, nullptr, dh, roi);

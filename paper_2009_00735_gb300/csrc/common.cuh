@@ -41,6 +41,54 @@ __device__ __forceinline__ float u23_to_float(uint32_t c) {
     return __int_as_float(0x4B000000 | c) - 8388608.0f;
 }
 
+// One atom into the histograms of a 64-direction tile: lane l owns
+// directions 2l (low 16 bits) and 2l + 1 (high 16 bits) of the word
+// H[b * 32 + l].  The word of a lane lies in bank l for every bin b, so the
+// 32 atomics of one warp instruction never share a bank.
+__device__ __forceinline__ void hist_add_atom(uint32_t* H, int lane, float4 a, float4 d0, float4 d1,
+                                              float scale, float magic, int nbm1) {
+    const float s0 = project_f32(d0.x, d0.y, d0.z, a);
+    const float s1 = project_f32(d1.x, d1.y, d1.z, a);
+    const int b0 = bin_of(s0, scale, magic, nbm1);
+    const int b1 = bin_of(s1, scale, magic, nbm1);
+    atomicAdd(&H[b0 * 32 + lane], 1u);
+    atomicAdd(&H[b1 * 32 + lane], 0x10000u);
+}
+
+// Histograms of one 64-direction tile over `cn` staged atoms; warp w takes
+// atoms w, w + W, w + 2W, ...
+template <int W>
+__device__ __forceinline__ void hist_tile(uint32_t* H, const float4* A, int cn, int warp, int lane, float4 d0,
+                                          float4 d1, float scale, float magic, int nbm1) {
+    int j = warp;
+    for (; j + 3 * W < cn; j += 4 * W) {
+        const float4 a0 = A[j], a1 = A[j + W], a2 = A[j + 2 * W], a3 = A[j + 3 * W];
+        hist_add_atom(H, lane, a0, d0, d1, scale, magic, nbm1);
+        hist_add_atom(H, lane, a1, d0, d1, scale, magic, nbm1);
+        hist_add_atom(H, lane, a2, d0, d1, scale, magic, nbm1);
+        hist_add_atom(H, lane, a3, d0, d1, scale, magic, nbm1);
+    }
+    for (; j < cn; j += W) hist_add_atom(H, lane, A[j], d0, d1, scale, magic, nbm1);
+}
+
+// Debug export of a tile's histograms: h_out[v * 2^m + b] for v < nv.
+__device__ __forceinline__ void hist_export(const uint32_t* H, int NB, int tile, int nv, uint16_t* h_out, int tid,
+                                            int nthreads) {
+    for (int i = tid; i < NB * 32; i += nthreads) {
+        const int b = i >> 5, l = i & 31;
+        const uint32_t w = H[i];
+        const int64_t v0 = (int64_t)tile * 64 + 2 * l;
+        if (v0 < nv) h_out[v0 * NB + b] = (uint16_t)(w & 0xFFFFu);
+        if (v0 + 1 < nv) h_out[(v0 + 1) * NB + b] = (uint16_t)(w >> 16);
+    }
+}
+
+// ROI rank ranges of a signature launch (ranks index the longest-first order)
+constexpr int kRanksAll = 0;       // [0, nroi)
+constexpr int kRanksBig = 1;       // [0, n_big): ROIs above 2048 atoms
+constexpr int kRanksSmall = 2;     // [n_big, nroi)
+constexpr int kTcMaxAtoms = 2048;  // fp16 carries every count <= 2048 exactly
+
 // -----------------------------------------------------------------------------
 // status word
 // -----------------------------------------------------------------------------

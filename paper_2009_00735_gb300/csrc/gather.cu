@@ -388,9 +388,12 @@ cudaError_t launch_gather_fill(Ctx* c) {
 // ROI order for the persistent kernels: largest N_w first (longest processing
 // time first), by a counting sort on 65535 - N_w.
 // -----------------------------------------------------------------------------
-__global__ void k_order_hist(const int32_t* __restrict__ nw, int64_t n, int32_t* hist) {
+__global__ void k_order_hist(const int32_t* __restrict__ nw, int64_t n, int32_t* hist, int32_t* n_big) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&hist[65535 - min(nw[i], 65535)], 1);
+    if (i < n) {
+        atomicAdd(&hist[65535 - min(nw[i], 65535)], 1);
+        if (nw[i] > kTcMaxAtoms) atomicAdd(n_big, 1);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_order_scan(int32_t* hist) {
@@ -428,8 +431,9 @@ cudaError_t launch_roi_order(Ctx* c) {
     cudaStream_t s = c->stream;
     cudaError_t e = cudaMemsetAsync(c->d_sort_hist, 0, sizeof(int32_t) * 65536, s);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_counter + 1, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
     unsigned b = (unsigned)((c->nroi + 255) / 256);
-    k_order_hist<<<b, 256, 0, s>>>(c->d_nw, c->nroi, c->d_sort_hist);
+    k_order_hist<<<b, 256, 0, s>>>(c->d_nw, c->nroi, c->d_sort_hist, c->d_counter + 1);
     k_order_scan<<<1, 256, 0, s>>>(c->d_sort_hist);
     k_order_scatter<<<b, 256, 0, s>>>(c->d_nw, c->nroi, c->d_sort_hist, c->d_order);
     return cudaGetLastError();

@@ -63,7 +63,10 @@ struct Ctx {
     // tensor-core twiddle operand (B): [n_cols] hi/lo FP16 in canonical layout
     void* d_twb = nullptr;
     size_t twb_bytes = 0;
-    int twb_key[3] = {-1, -1, -1};     // (m, band_min, n_cols)
+    int twb_key[3] = {-1, -1, -1};     // (m, band_min, groups)
+    int tc_gb = 0;                     // frequency groups per B batch
+    int tc_ng = 0;                     // groups in the global B operand
+    uint32_t tc_tmem_cols = 0;
 
     // ROIs
     int64_t nroi = 0;
@@ -72,6 +75,7 @@ struct Ctx {
     float* d_scale = nullptr;          // [nroi] (float)((2^(m-1)-1)/R)
     int32_t* d_band = nullptr;         // [nroi x 2] (k_lo, k_hi)
     int32_t band_min = 0, band_max = 0;
+    std::vector<int32_t> h_band;       // host copy of (k_lo, k_hi) per ROI
     uint32_t type_mask = 0xFFFFFFFFu;
     double r_max = 0.0;
 
@@ -146,7 +150,7 @@ cudaError_t launch_twiddles(float2* tw, int m, cudaStream_t s);
 
 // signature kernels
 cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out,
-                                    int64_t hist_roi);
+                                    int64_t hist_roi, int rank_mode);
 cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out,
                                  int64_t hist_roi);
 int prepare_tc(Ctx* c);

@@ -48,17 +48,10 @@ struct SigParams {
     int32_t* counter;
     int* status;
     int atom_cap;
+    const int32_t* n_big;
+    int rank_mode;
+    int64_t nroi;
 };
-
-__device__ __forceinline__ void process_atom(uint32_t* H, int lane, float4 a, float4 d0, float4 d1, float scale,
-                                             float magic, int nbm1) {
-    const float s0 = project_f32(d0.x, d0.y, d0.z, a);
-    const float s1 = project_f32(d1.x, d1.y, d1.z, a);
-    const int b0 = bin_of(s0, scale, magic, nbm1);
-    const int b1 = bin_of(s1, scale, magic, nbm1);
-    atomicAdd(&H[b0 * kWords + lane], 1u);
-    atomicAdd(&H[b1 * kWords + lane], 0x10000u);
-}
 
 __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -81,14 +74,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
     __syncthreads();
     uint32_t phase = 0;
     const float magic = bin_magic(p.m);
+    int64_t rank_lo = 0, n_items = p.n_items;
+    if (p.single_roi < 0 && p.rank_mode != kRanksAll) {
+        const int64_t nb = *p.n_big;
+        rank_lo = p.rank_mode == kRanksBig ? 0 : nb;
+        const int64_t rank_hi = p.rank_mode == kRanksBig ? nb : p.nroi;
+        n_items = (rank_hi - rank_lo) * p.items_per_roi;
+    }
 
     for (;;) {
         if (tid == 0) *item_s = atomicAdd(p.counter, 1);
         __syncthreads();
         const int64_t item = *item_s;
         __syncthreads();
-        if (item >= p.n_items) break;
-        const int64_t roi_rank = item / p.items_per_roi;
+        if (item >= n_items) break;
+        const int64_t roi_rank = rank_lo + item / p.items_per_roi;
         const int grp = (int)(item % p.items_per_roi);
         const int64_t roi = p.single_roi >= 0 ? p.single_roi : (int64_t)p.order[roi_rank];
         const int nw = p.nw[roi];
@@ -109,28 +109,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
             for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
                 const int cn = min(p.atom_cap, nw - c0);
                 if (!one_chunk && !stage_atoms(A, p.atoms + abase + c0, cn, bar, phase, p.status, flag)) return;
-                int j = warp;
-                for (; j + 3 * kWarps < cn; j += 4 * kWarps) {
-                    const float4 a0 = A[j], a1 = A[j + kWarps], a2 = A[j + 2 * kWarps], a3 = A[j + 3 * kWarps];
-                    process_atom(H, lane, a0, d0, d1, scale, magic, nbm1);
-                    process_atom(H, lane, a1, d0, d1, scale, magic, nbm1);
-                    process_atom(H, lane, a2, d0, d1, scale, magic, nbm1);
-                    process_atom(H, lane, a3, d0, d1, scale, magic, nbm1);
-                }
-                for (; j < cn; j += kWarps) process_atom(H, lane, A[j], d0, d1, scale, magic, nbm1);
+                hist_tile<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
                 if (!one_chunk) __syncthreads();
             }
             __syncthreads();
 
-            if (p.hist_out) {
-                for (int i = tid; i < NB * kWords; i += kThreads) {
-                    const int b = i / kWords, l = i % kWords;
-                    const uint32_t w = H[i];
-                    const int64_t v0 = (int64_t)tile * kDirs + 2 * l;
-                    if (v0 < p.nv) p.hist_out[v0 * NB + b] = (uint16_t)(w & 0xFFFFu);
-                    if (v0 + 1 < p.nv) p.hist_out[(v0 + 1) * NB + b] = (uint16_t)(w >> 16);
-                }
-            }
+            if (p.hist_out) hist_export(H, NB, tile, p.nv, p.hist_out, tid, kThreads);
 
             // ---- band spectrum (FP32) and band maximum ----
             const int K = khi - klo + 1;
@@ -283,7 +267,8 @@ size_t plain_smem_bytes(int m, int atom_cap) {
     return NB * kWords * 4 + NB * 8 + (size_t)atom_cap * 16 + kPartBytes + 64;
 }
 
-cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out, int64_t hist_roi) {
+cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out, int64_t hist_roi,
+                                    int rank_mode) {
     static int max_optin = -1;
     if (max_optin < 0) {
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -319,11 +304,15 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     p.counter = c->d_counter;
     p.status = c->d_status;
     p.atom_cap = cap;
+    p.n_big = c->d_counter + 1;
+    p.rank_mode = hist_out ? kRanksAll : rank_mode;
+    p.nroi = c->nroi;
     if ((e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);
     per_sm = max(per_sm, 1);
     int64_t grid = tmin<int64_t>((int64_t)c->sm_count * per_sm, p.n_items);
+    if (rank_mode == kRanksBig && !hist_out) grid = tmin<int64_t>(grid, (int64_t)c->sm_count);
     if (grid < 1) return cudaSuccess;
     k_sig_plain<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
     return cudaGetLastError();

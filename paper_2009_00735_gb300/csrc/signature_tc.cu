@@ -1,16 +1,451 @@
-// signature_tc.cu -- placeholder until the tcgen05 path lands.
+// signature_tc.cu -- steps (a2)-(a5) with the band spectrum on the tcgen05
+// tensor cores: X = H x T, H the [64 directions x 2^m bins] histogram tile and
+// T the [2^m bins x band columns] DFT matrix (cos and sin of 2 pi k n / 2^m),
+// accumulated in FP32 in tensor memory (Section 2.2: the Fourier amplitude
+// spectrum of every SDM; the paper notes that the SDMs of a ROI share one
+// bin count, which permits batching their transforms).
+//
+// Per 64-direction tile of a ROI:
+//   1. histograms by shared-memory atomics (bank-private columns, as in the
+//      FP32 path); counts c <= 2048, so the u16 bit pattern of c is the fp16
+//      value c * 2^-24 exactly (fp16 is linear through its subnormal range up
+//      to 0x0800) and the histogram is the A operand as it stands;
+//   2. an in-place permutation of 16-byte chunks gives the MN-major 128-byte
+//      swizzled layout (chunk c of bin row k moves to c ^ (k & 7));
+//   3. one thread issues 2^m / 16 tcgen05.mma (M = 64, K = 16, N = 16 per
+//      group of 4 frequencies: 8 hi columns, then 8 lo columns, where
+//      T = T_hi + T_lo with both parts fp16) into FP32 accumulators in TMEM;
+//   4. four warps read the accumulators (tcgen05.ld), add hi and lo parts,
+//      scale by 2^24 and keep the band maximum of |X(k)|.
+// ROIs with more than 2048 atoms (where a bin could exceed fp16's exact
+// range) run on the FP32 kernel in the same call.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace aptidx {
 
-bool tc_supported(Ctx*) { return false; }
+namespace {
 
-int prepare_tc(Ctx* c) {
-    return set_error(c, APTIDX_E_INVALID_ARG, "tensor-core path not built yet");
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kDirs = kTileDirs;     // M = 64
+constexpr int kBtBytes = 64 * 1024;  // shared-memory budget of the B operand
+
+struct TcParams {
+    const float4* atoms;
+    const int64_t* off;
+    const int32_t* nw;
+    const int32_t* order;
+    const int32_t* n_big;
+    const float4* dirs;
+    int32_t nv;
+    int32_t tiles_per_roi;
+    int32_t tiles_per_item;
+    int32_t items_per_roi;
+    int64_t nroi;
+    const float* scale;
+    const int32_t* band;
+    int m;
+    int32_t kbase;          // frequency of column group 0
+    const uint8_t* twb;     // global B: [hi|lo][group][k-block] x 1 KB
+    int32_t ng_total;
+    int32_t gb;             // groups per shared-memory batch
+    uint32_t tmem_cols;
+    float* S;
+    uint16_t* argk;
+    uint16_t* hist_out;
+    int64_t single_roi;
+    int32_t* counter;
+    int* status;
+    int atom_cap;
+};
+
+// ---- tcgen05 / descriptor helpers -------------------------------------------
+
+// shared-memory matrix descriptor, 128-byte swizzle
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version
+    d |= (uint64_t)2 << 61;   // 128-byte swizzle
+    return d;
 }
 
-cudaError_t launch_signatures_tc(Ctx*, float*, uint16_t*, uint16_t*, int64_t) {
-    return cudaErrorNotSupported;
+// instruction descriptor: D f32, A f16 MN-major, B f16 K-major, M = 64
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+    return (1u << 4) | (1u << 15) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kDirs >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- the kernel ----------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    const int NB = 1 << p.m;
+    const int nbm1 = NB - 1;
+    const int KB = NB / 64;   // 1 KB K-blocks per 8-row column group
+    uint32_t* H = reinterpret_cast<uint32_t*>(smem);
+    unsigned char* BT = smem + (size_t)NB * 128;
+    float4* A = reinterpret_cast<float4*>(BT + kBtBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(A + p.atom_cap);   // atoms, B, mma
+    int* flag = reinterpret_cast<int*>(bars + 3);
+    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 4);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 5);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_s)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_s;
+    const uint32_t h_addr = smem_u32(H);
+    const uint32_t bt_addr = smem_u32(BT);
+
+    uint32_t ph_atoms = 0, ph_b = 0, ph_mma = 0;
+    int cur_g0 = -1, cur_nb = -1;
+    const float magic = bin_magic(p.m);
+
+    int64_t rank_lo = 0, n_items;
+    if (p.single_roi >= 0) {
+        n_items = p.items_per_roi;
+    } else {
+        rank_lo = *p.n_big;
+        n_items = (p.nroi - rank_lo) * p.items_per_roi;
+    }
+    bool failed = false;
+
+    for (;;) {
+        if (tid == 0) *item_s = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int64_t item = *item_s;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int64_t roi = p.single_roi >= 0 ? p.single_roi : (int64_t)p.order[rank_lo + item / p.items_per_roi];
+        const int grp = (int)(item % p.items_per_roi);
+        const int nw = p.nw[roi];
+        const int64_t abase = p.off[roi];
+        const float scale = p.scale[roi];
+        const int klo = p.band[2 * roi], khi = p.band[2 * roi + 1];
+        const int fg0 = (klo - p.kbase) >> 2, fg1 = (khi - p.kbase) >> 2;
+        const int ng = fg1 - fg0 + 1;
+        const int nbatch = (ng + p.gb - 1) / p.gb;
+        const int t0 = grp * p.tiles_per_item;
+        const int t1 = min(t0 + p.tiles_per_item, p.tiles_per_roi);
+        const bool one_chunk = nw <= p.atom_cap;
+        if (one_chunk && !stage_atoms(A, p.atoms + abase, nw, &bars[0], ph_atoms, p.status, flag)) {
+            failed = true;
+            break;
+        }
+
+        for (int tile = t0; tile < t1 && !failed; ++tile) {
+            // ---- 1. histograms ----
+            uint4* H4 = reinterpret_cast<uint4*>(H);
+            for (int i = tid; i < NB * 8; i += kThreads) H4[i] = make_uint4(0, 0, 0, 0);
+            const float4 d0 = p.dirs[(int64_t)tile * kDirs + 2 * lane];
+            const float4 d1 = p.dirs[(int64_t)tile * kDirs + 2 * lane + 1];
+            __syncthreads();
+            for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
+                const int cn = min(p.atom_cap, nw - c0);
+                if (!one_chunk && !stage_atoms(A, p.atoms + abase + c0, cn, &bars[0], ph_atoms, p.status, flag)) {
+                    failed = true;
+                    break;
+                }
+                hist_tile<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
+                if (!one_chunk) __syncthreads();
+            }
+            if (failed) break;
+            __syncthreads();
+            if (p.hist_out) hist_export(H, NB, tile, p.nv, p.hist_out, tid, kThreads);
+
+            // ---- 2. 128-byte swizzle of every bin row, in place ----
+            for (int u = tid; u < NB * 4; u += kThreads) {
+                const int k = u >> 2, j = u & 3, s = k & 7;
+                if (s == 0) continue;
+                const int hb = s >= 4 ? 4 : (s >= 2 ? 2 : 1);
+                const int lowmask = hb - 1;
+                const int c0 = ((j & ~lowmask) << 1) | (j & lowmask);
+                const int c1 = c0 ^ s;
+                uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
+                const uint4 x0 = row[c0], x1 = row[c1];
+                row[c0] = x1;
+                row[c1] = x0;
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+
+            // ---- 3. tensor-core contraction (one issuing thread) ----
+            if (tid == 0) {
+                tc_fence_after();
+                int ok = 1;
+                for (int b = 0; b < nbatch && ok; ++b) {
+                    const int g0 = fg0 + b * p.gb;
+                    const int nb = min(p.gb, fg1 + 1 - g0);
+                    if (g0 != cur_g0 || nb != cur_nb) {
+                        const uint32_t part = (uint32_t)nb * KB * 1024u;
+                        mbar_arrive_expect_tx(&bars[1], 2 * part);
+                        bulk_g2s(BT, p.twb + (size_t)g0 * KB * 1024, part, &bars[1]);
+                        bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + g0) * KB * 1024, part, &bars[1]);
+                        ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                        if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                        ph_b ^= 1u;
+                        cur_g0 = ok ? g0 : -1;
+                        cur_nb = nb;
+                        if (!ok) break;
+                        tc_fence_after();
+                    }
+                    const int n = 16 * nb;
+                    const uint32_t idesc = idesc_f16(n);
+                    const uint32_t dcol = tmem + (uint32_t)(b * 16 * p.gb);
+                    const uint32_t sbo_b = (uint32_t)KB * 1024u;
+                    for (int kk = 0; kk < NB / 16; ++kk) {
+                        const uint64_t ad = sdesc_sw128(h_addr + (uint32_t)kk * 2048u, 1024u, 1024u);
+                        const uint64_t bd = sdesc_sw128(bt_addr + (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u,
+                                                        16u, sbo_b);
+                        mma_f16(dcol, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&bars[2]);
+                    ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
+                    if (!ok) mbar_wait_bounded(&bars[2], ph_mma, p.status, 1u << 20);
+                    ph_mma ^= 1u;
+                }
+                *flag = ok;
+            }
+            __syncthreads();
+            if (!*flag) {
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+
+            // ---- 4. epilogue: |X(k)| and the band maximum ----
+            if (warp < 4) {
+                float best = -1.f;
+                int bk = klo;
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+                for (int b = 0; b < nbatch; ++b) {
+                    const int g0 = fg0 + b * p.gb;
+                    const int nb = min(p.gb, fg1 + 1 - g0);
+                    const uint32_t dcol = lane_base + (uint32_t)(b * 16 * p.gb);
+                    for (int j = 0; j < nb; ++j) {
+                        float hi[8], lo[8];
+                        tmem_ld8(dcol + (uint32_t)(8 * j), hi);
+                        tmem_ld8(dcol + (uint32_t)(8 * nb + 8 * j), lo);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int f = p.kbase + 4 * (g0 + j) + q;
+                            const float re = hi[2 * q] + lo[2 * q];
+                            const float im = hi[2 * q + 1] + lo[2 * q + 1];
+                            const float a = sqrtf(re * re + im * im) * 16777216.0f;
+                            if (f >= klo && f <= khi && a > best) {
+                                best = a;
+                                bk = f;
+                            }
+                        }
+                    }
+                }
+                if (lane < 16) {
+                    const int mrow = warp * 16 + lane;
+                    const int64_t v = (int64_t)tile * kDirs + mrow;
+                    if (v < p.nv) {
+                        const int64_t o = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv + v;
+                        p.S[o] = best;
+                        if (p.argk) p.argk[o] = (uint16_t)bk;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (failed) break;
+    }
+    // teardown: every thread arrives here; warp 0 frees the tensor memory
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+    }
+}
+
+// ---- the global B operand: DFT matrix columns, fp16 hi + lo, K-major SW128 ----
+
+__global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng) {
+    const int NB = 1 << m;
+    const int KB = NB / 64;
+    const int64_t total = (int64_t)2 * ng * NB * 8;   // [hi|lo] x groups x bins x 8 rows
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i & 7);
+        const int64_t t = i >> 3;
+        const int k = (int)(t % NB);
+        const int64_t t2 = t / NB;
+        const int g = (int)(t2 % ng);
+        const int part = (int)(t2 / ng);   // 0 hi, 1 lo
+        const int f = kbase + 4 * g + (r >> 1);
+        const int jn = (int)(((int64_t)f * k) % NB);
+        double sn, cs;
+        sincospi(2.0 * (double)jn / (double)NB, &sn, &cs);
+        const double v = (r & 1) ? sn : cs;
+        const __half hi = __double2half(v);
+        const __half lo = __double2half(v - (double)__half2float(hi));
+        const int kb = k >> 6, kin = k & 63;
+        const size_t off = ((size_t)(part * ng + g) * KB + kb) * 1024 + (size_t)r * 128 + (size_t)(((kin >> 3) ^ r) << 4) +
+                           (size_t)(kin & 7) * 2;
+        *reinterpret_cast<__half*>(twb + off) = part ? lo : hi;
+    }
+}
+
+}  // namespace
+
+bool tc_supported(Ctx* c) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+    return major == 10 && minor == 3;
+}
+
+static size_t tc_smem_bytes(int m, int atom_cap) {
+    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + (size_t)atom_cap * 16 + 64;
+}
+
+// Build the B operand for the current ROI bands and pick the TMEM size.
+int prepare_tc(Ctx* c) {
+    if (!tc_supported(c)) return set_error(c, APTIDX_E_INVALID_ARG, "tensor-core path needs an sm_103 device");
+    const int NB = 1 << c->m;
+    const int KB = NB / 64;
+    const int kbase = c->band_min;
+    const int ng = (c->band_max - kbase) / 4 + 1;
+    const int gb = kBtBytes / (2 * KB * 1024);
+    int ng_roi_max = 1;
+    for (int64_t r = 0; r < c->nroi; ++r) {
+        const int g0 = (c->h_band[2 * r] - kbase) >> 2, g1 = (c->h_band[2 * r + 1] - kbase) >> 2;
+        ng_roi_max = std::max(ng_roi_max, g1 - g0 + 1);
+    }
+    const int nbatch = (ng_roi_max + gb - 1) / gb;
+    const uint32_t need = (uint32_t)(nbatch * 16 * gb);
+    uint32_t cols = 32;
+    while (cols < need) cols <<= 1;
+    if (cols > 512)
+        return set_error(c, APTIDX_E_INVALID_ARG,
+                         "tensor-core path: a ROI band spans %d frequency groups; at most %d fit in tensor memory",
+                         ng_roi_max, 512 / (16 * gb) * gb);
+    if (c->twb_key[0] != c->m || c->twb_key[1] != kbase || c->twb_key[2] != ng) {
+        dev_free(c->d_twb);
+        c->d_twb = nullptr;
+        c->twb_key[0] = c->twb_key[1] = c->twb_key[2] = -1;
+        const size_t bytes = (size_t)2 * ng * KB * 1024;
+        int rc = dev_alloc(c, &c->d_twb, bytes);
+        if (rc) return rc;
+        k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)2 * ng * NB * 8 + 255) / 256, 4096), 256, 0, c->stream>>>(
+            (uint8_t*)c->d_twb, c->m, kbase, ng);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_check(c, e, "twiddle operand");
+        c->launches += 1;
+        c->twb_key[0] = c->m;
+        c->twb_key[1] = kbase;
+        c->twb_key[2] = ng;
+    }
+    c->tc_gb = gb;
+    c->tc_ng = ng;
+    c->tc_tmem_cols = cols;
+    return APTIDX_OK;
+}
+
+cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out, int64_t hist_roi) {
+    cudaError_t e;
+    // ROIs above 2048 atoms: FP32 kernel (no-op when there are none)
+    if (!hist_out) {
+        if ((e = launch_signatures_plain(c, S, argk, nullptr, -1, kRanksBig)) != cudaSuccess) return e;
+    }
+    static int max_optin = -1;
+    if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    const size_t base = tc_smem_bytes(c->m, 0);
+    int cap = (int)(((size_t)max_optin - base) / 16);
+    cap = std::min(cap, kTcMaxAtoms) & ~15;
+    if (cap < 256) return cudaErrorInvalidConfiguration;
+    const size_t smem = tc_smem_bytes(c->m, cap);
+    if ((e = cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    TcParams p;
+    p.atoms = c->d_atoms;
+    p.off = c->d_off;
+    p.nw = c->d_nw;
+    p.order = c->d_order;
+    p.n_big = c->d_counter + 1;
+    p.dirs = c->d_dirs;
+    p.nv = c->nv;
+    p.tiles_per_roi = c->nv_pad / kDirs;
+    p.tiles_per_item = std::min(16, p.tiles_per_roi);
+    p.items_per_roi = (p.tiles_per_roi + p.tiles_per_item - 1) / p.tiles_per_item;
+    p.nroi = c->nroi;
+    p.scale = c->d_scale;
+    p.band = c->d_band;
+    p.m = c->m;
+    p.kbase = c->band_min;
+    p.twb = (const uint8_t*)c->d_twb;
+    p.ng_total = c->tc_ng;
+    p.gb = c->tc_gb;
+    p.tmem_cols = c->tc_tmem_cols;
+    p.S = S;
+    p.argk = argk;
+    p.hist_out = hist_out;
+    p.single_roi = hist_out ? hist_roi : -1;
+    p.counter = c->d_counter + 2;
+    p.status = c->d_status;
+    p.atom_cap = cap;
+    if ((e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_tc, kThreads, smem);
+    per_sm = std::max(1, std::min(per_sm, (int)(512 / p.tmem_cols)));
+    const int64_t items = (hist_out ? 1 : c->nroi) * (int64_t)p.items_per_roi;
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, items);
+    if (grid < 1) return cudaSuccess;
+    k_sig_tc<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
+    c->launches += hist_out ? 0 : 1;   // the FP32 launch above is counted by the caller's phase count
+    return cudaGetLastError();
 }
 
 }  // namespace aptidx
