@@ -31,6 +31,7 @@ constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDirs = kTileDirs;     // M = 64
 constexpr int kBtBytes = 64 * 1024;  // shared-memory budget of the B operand
+constexpr int kIssuers = 4;          // warps issuing MMAs, one TMEM partial accumulator each
 
 struct TcParams {
     const float4* atoms;
@@ -109,27 +110,29 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // ---- the kernel ----------------------------------------------------------------
 
 __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                           ~static_cast<uintptr_t>(1023));
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzled operands; offset arithmetic on the
+    // shared array keeps the pointers in the shared address space
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int NB = 1 << p.m;
     const int nbm1 = NB - 1;
     const int KB = NB / 64;   // 1 KB K-blocks per 8-row column group
     uint32_t* H = reinterpret_cast<uint32_t*>(smem);
     unsigned char* BT = smem + (size_t)NB * 128;
     float4* A = reinterpret_cast<float4*>(BT + kBtBytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(A + p.atom_cap);   // atoms, B, mma
-    int* flag = reinterpret_cast<int*>(bars + 3);
-    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 4);
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 5);
+    // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per issuer
+    uint64_t* bars = reinterpret_cast<uint64_t*>(A + p.atom_cap);
+    int* flag = reinterpret_cast<int*>(bars + 2 + kIssuers);
+    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 3 + kIssuers);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 4 + kIssuers);
+    int* iss_ok = reinterpret_cast<int*>(bars + 5 + kIssuers);   // [kIssuers]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int i = 0; i < 2 + kIssuers; ++i) mbar_init(&bars[i], 1);
         fence_barrier_init();
     }
+    for (int i = tid; i < NB * 8; i += kThreads) reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_s)),
                      "r"(p.tmem_cols)
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     const uint32_t h_addr = smem_u32(H);
     const uint32_t bt_addr = smem_u32(BT);
 
-    uint32_t ph_atoms = 0, ph_b = 0, ph_mma = 0;
+    uint32_t ph_atoms = 0, ph_b = 0, ph_mma = 0;   // ph_mma: this warp's issuer barrier
     int cur_g0 = -1, cur_nb = -1;
     const float magic = bin_magic(p.m);
 
@@ -180,12 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         }
 
         for (int tile = t0; tile < t1 && !failed; ++tile) {
-            // ---- 1. histograms ----
-            uint4* H4 = reinterpret_cast<uint4*>(H);
-            for (int i = tid; i < NB * 8; i += kThreads) H4[i] = make_uint4(0, 0, 0, 0);
+            // ---- 1. histograms (H is zero here) ----
             const float4 d0 = p.dirs[(int64_t)tile * kDirs + 2 * lane];
             const float4 d1 = p.dirs[(int64_t)tile * kDirs + 2 * lane + 1];
-            __syncthreads();
             for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
                 const int cn = min(p.atom_cap, nw - c0);
                 if (!one_chunk && !stage_atoms(A, p.atoms + abase + c0, cn, &bars[0], ph_atoms, p.status, flag)) {
@@ -197,89 +197,157 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
             }
             if (failed) break;
             __syncthreads();
-            if (p.hist_out) hist_export(H, NB, tile, p.nv, p.hist_out, tid, kThreads);
-
-            // ---- 2. 128-byte swizzle of every bin row, in place ----
-            for (int u = tid; u < NB * 4; u += kThreads) {
-                const int k = u >> 2, j = u & 3, s = k & 7;
-                if (s == 0) continue;
-                const int hb = s >= 4 ? 4 : (s >= 2 ? 2 : 1);
-                const int lowmask = hb - 1;
-                const int c0 = ((j & ~lowmask) << 1) | (j & lowmask);
-                const int c1 = c0 ^ s;
-                uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
-                const uint4 x0 = row[c0], x1 = row[c1];
-                row[c0] = x1;
-                row[c1] = x0;
+            if (p.hist_out) {
+                hist_export(H, NB, tile, p.nv, p.hist_out, tid, kThreads);
+                __syncthreads();   // every row is read before the permutation moves it
             }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncthreads();
 
-            // ---- 3. tensor-core contraction (one issuing thread) ----
+            // ---- 2 + 3. swizzle and contraction, pipelined over four K chunks.
+            // Warps kIssuers.. bring the bin rows of chunk q into the MN-major
+            // 128-byte swizzled layout in place (a warp holds four rows, 512
+            // contiguous bytes, one 16-byte chunk per lane, and writes chunk c
+            // of row k to chunk c ^ (k & 7)); then lane 0 of each of warps
+            // 0 .. n_iss-1 issues its share of the K steps of chunk q into its
+            // own partial accumulator while the others permute chunk q + 1.
+            // A single tcgen05.mma costs an issuing warp ~75 cycles whatever
+            // its N; four issuers overlap that cost.
+            const int n_iss = nbatch == 1 ? kIssuers : 1;
+            const int rows_q = NB / 4;
+            const int kk_q = NB / 64;   // K steps of 16 bins per chunk
+            const uint32_t sbo_b = (uint32_t)KB * 1024u;
+            const uint32_t cols_b = (uint32_t)(16 * p.gb);   // TMEM columns per accumulator
+            const bool issuer = lane == 0 && warp < n_iss;
+            int ok = 1;
             if (tid == 0) {
-                tc_fence_after();
-                int ok = 1;
-                for (int b = 0; b < nbatch && ok; ++b) {
-                    const int g0 = fg0 + b * p.gb;
-                    const int nb = min(p.gb, fg1 + 1 - g0);
-                    if (g0 != cur_g0 || nb != cur_nb) {
-                        const uint32_t part = (uint32_t)nb * KB * 1024u;
-                        mbar_arrive_expect_tx(&bars[1], 2 * part);
-                        bulk_g2s(BT, p.twb + (size_t)g0 * KB * 1024, part, &bars[1]);
-                        bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + g0) * KB * 1024, part, &bars[1]);
-                        ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
-                        if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
-                        ph_b ^= 1u;
-                        cur_g0 = ok ? g0 : -1;
-                        cur_nb = nb;
-                        if (!ok) break;
-                        tc_fence_after();
-                    }
-                    const int n = 16 * nb;
-                    const uint32_t idesc = idesc_f16(n);
-                    const uint32_t dcol = tmem + (uint32_t)(b * 16 * p.gb);
-                    const uint32_t sbo_b = (uint32_t)KB * 1024u;
-                    for (int kk = 0; kk < NB / 16; ++kk) {
-                        const uint64_t ad = sdesc_sw128(h_addr + (uint32_t)kk * 2048u, 1024u, 1024u);
-                        const uint64_t bd = sdesc_sw128(bt_addr + (uint32_t)(kk >> 2) * 1024u + (uint32_t)(kk & 3) * 32u,
-                                                        16u, sbo_b);
-                        mma_f16(dcol, ad, bd, idesc, kk > 0 ? 1u : 0u);
-                    }
-                    mma_commit(&bars[2]);
-                    ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
-                    if (!ok) mbar_wait_bounded(&bars[2], ph_mma, p.status, 1u << 20);
-                    ph_mma ^= 1u;
+                // B operand of batch 0 (kept across tiles while the ROI band allows)
+                const int nb0 = min(p.gb, fg1 + 1 - fg0);
+                if (fg0 != cur_g0 || nb0 != cur_nb) {
+                    const uint32_t part = (uint32_t)nb0 * KB * 1024u;
+                    mbar_arrive_expect_tx(&bars[1], 2 * part);
+                    bulk_g2s(BT, p.twb + (size_t)fg0 * KB * 1024, part, &bars[1]);
+                    bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + fg0) * KB * 1024, part, &bars[1]);
+                    ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                    if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                    ph_b ^= 1u;
+                    cur_g0 = ok ? fg0 : -1;
+                    cur_nb = nb0;
                 }
                 *flag = ok;
             }
+            for (int q = 0; q < 4; ++q) {
+                if (warp >= kIssuers) {
+                    for (int r0 = q * rows_q + (warp - kIssuers) * 4; r0 < (q + 1) * rows_q;
+                         r0 += (kWarps - kIssuers) * 4) {
+                        const int k = r0 + (lane >> 3), c = lane & 7;
+                        uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
+                        const uint4 x = row[c];
+                        __syncwarp();
+                        row[c ^ (k & 7)] = x;
+                    }
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (q == 0) ok = *flag;
+                if (issuer && ok) {
+                    tc_fence_after();
+                    const int nb0 = min(p.gb, fg1 + 1 - fg0);
+                    const uint32_t idesc = idesc_f16(16 * nb0);
+                    const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
+                    const uint64_t a0 = sdesc_sw128(h_addr, 1024u, 1024u);
+                    const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
+                    // descriptors advance by constant steps: A by 2 KB per K
+                    // step, B by 32 bytes inside a 128-byte row and 1 KB per
+                    // 64-bin block (the address field counts 16-byte units)
+                    for (int kk = q * kk_q + warp; kk < (q + 1) * kk_q; kk += n_iss) {
+                        const uint64_t ad = a0 + (uint64_t)(kk * 128);
+                        const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+                        mma_f16(dcol, ad, bd, idesc, kk >= n_iss ? 1u : 0u);
+                    }
+                    if (q == 3 && tid == 0 && nbatch > 1) {
+                        // wide band: further batches, each reloading the B buffer
+                        for (int b = 1; b < nbatch && ok; ++b) {
+                            mma_commit(&bars[2]);
+                            ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
+                            ph_mma ^= 1u;
+                            if (!ok) break;
+                            const int g0 = fg0 + b * p.gb;
+                            const int nb = min(p.gb, fg1 + 1 - g0);
+                            const uint32_t part = (uint32_t)nb * KB * 1024u;
+                            mbar_arrive_expect_tx(&bars[1], 2 * part);
+                            bulk_g2s(BT, p.twb + (size_t)g0 * KB * 1024, part, &bars[1]);
+                            bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + g0) * KB * 1024, part, &bars[1]);
+                            ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                            if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                            ph_b ^= 1u;
+                            cur_g0 = ok ? g0 : -1;
+                            cur_nb = nb;
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint32_t idb = idesc_f16(16 * nb);
+                            const uint32_t dcb = tmem + (uint32_t)b * cols_b;
+                            for (int kk = 0; kk < NB / 16; ++kk) {
+                                const uint64_t ad = a0 + (uint64_t)(kk * 128);
+                                const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+                                mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : 0u);
+                            }
+                        }
+                    }
+                }
+            }
+            if (issuer) {
+                int mine = ok;
+                if (mine) {
+                    mma_commit(&bars[2 + warp]);
+                    mine = mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status) ? 1 : 0;
+                    if (!mine) mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status, 1u << 20);
+                    ph_mma ^= 1u;
+                }
+                iss_ok[warp] = mine;
+            }
             __syncthreads();
-            if (!*flag) {
-                failed = true;
-                break;
+            {
+                int all = 1;
+                for (int i = 0; i < n_iss; ++i) all &= iss_ok[i];
+                if (!all) {
+                    failed = true;
+                    break;
+                }
             }
             tc_fence_after();
 
-            // ---- 4. epilogue: |X(k)| and the band maximum ----
-            if (warp < 4) {
+            // ---- 4. epilogue: |X(k)| and the band maximum (warps 0-3, one per
+            // TMEM lane quadrant); the other warps zero H for the next tile ----
+            if (warp >= 4) {
+                for (int i = tid - 128; i < NB * 8; i += kThreads - 128)
+                    reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+            } else {
                 float best = -1.f;
                 int bk = klo;
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+                const int n_iss = nbatch == 1 ? kIssuers : 1;
+                const uint32_t cols_b = (uint32_t)(16 * p.gb);
                 for (int b = 0; b < nbatch; ++b) {
                     const int g0 = fg0 + b * p.gb;
                     const int nb = min(p.gb, fg1 + 1 - g0);
-                    const uint32_t dcol = lane_base + (uint32_t)(b * 16 * p.gb);
                     for (int j = 0; j < nb; ++j) {
-                        float hi[8], lo[8];
-                        tmem_ld8(dcol + (uint32_t)(8 * j), hi);
-                        tmem_ld8(dcol + (uint32_t)(8 * nb + 8 * j), lo);
-                        tmem_wait_ld();
+                        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+                        for (int i = 0; i < n_iss; ++i) {
+                            const uint32_t dcol = lane_base + (uint32_t)(b + i) * cols_b;
+                            float hi[8], lo[8];
+                            tmem_ld8(dcol + (uint32_t)(8 * j), hi);
+                            tmem_ld8(dcol + (uint32_t)(8 * nb + 8 * j), lo);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                re[q] += hi[2 * q] + lo[2 * q];
+                                im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                            }
+                        }
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int f = p.kbase + 4 * (g0 + j) + q;
-                            const float re = hi[2 * q] + lo[2 * q];
-                            const float im = hi[2 * q + 1] + lo[2 * q + 1];
-                            const float a = sqrtf(re * re + im * im) * 16777216.0f;
+                            const float a = sqrtf(re[q] * re[q] + im[q] * im[q]) * 16777216.0f;
                             if (f >= klo && f <= khi && a > best) {
                                 best = a;
                                 bk = f;
@@ -302,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         }
         if (failed) break;
     }
-    // teardown: every thread arrives here; warp 0 frees the tensor memory
+    // teardown: warp 0 frees the tensor memory
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -348,7 +416,7 @@ bool tc_supported(Ctx* c) {
 }
 
 static size_t tc_smem_bytes(int m, int atom_cap) {
-    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + (size_t)atom_cap * 16 + 64;
+    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + (size_t)atom_cap * 16 + 256;
 }
 
 // Build the B operand for the current ROI bands and pick the TMEM size.
@@ -365,7 +433,8 @@ int prepare_tc(Ctx* c) {
         ng_roi_max = std::max(ng_roi_max, g1 - g0 + 1);
     }
     const int nbatch = (ng_roi_max + gb - 1) / gb;
-    const uint32_t need = (uint32_t)(nbatch * 16 * gb);
+    // accumulators: kIssuers partials for single-batch bands, one per batch otherwise
+    const uint32_t need = (uint32_t)(std::max(nbatch, kIssuers) * 16 * gb);
     uint32_t cols = 32;
     while (cols < need) cols <<= 1;
     if (cols > 512)
