@@ -229,6 +229,52 @@ int aptidx_set_profiling(aptidx_ctx* ctx, int enable);
  * library kernels launched.  Any pointer may be NULL. */
 int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, int64_t* launches);
 
+/* ---- no-allocation variant ------------------------------------------------ */
+
+/* The paper has no counterpart of this call; it serves callers that cannot
+ * allocate device memory: code that runs while a CUDA graph is being
+ * captured, a host framework that owns every device allocation through its
+ * own pool, or a plugin that may not call cudaMalloc from its callback.
+ * It computes the FP32 signatures of aptidx_compute_signatures
+ * (APTIDX_PATH_PLAIN_FP32, no normalisation) for ROIs whose atoms the caller
+ * has already gathered and centred, and needs no context.
+ *
+ *   xc4     device, 16-byte aligned: centred atom coordinates as rows of four
+ *           floats (x, y, z, unused); ROI r owns rows [off[r], off[r+1])
+ *   off     device, nroi + 1 int64 row offsets
+ *   radii   device, nroi FP64 ROI radii (> 0)
+ *   u       device, nv x 3 FP32 unit directions (|u| within 1e-5 of 1)
+ *   m, k_lo, k_hi: 2^m bins and the signature band, as in aptidx_set_binning
+ *   S       device output, nroi x nv FP32
+ *   status  device int or NULL: the kernels OR APTIDX_STATUS_* bits into it
+ *           (a ROI above APTIDX_MAX_ATOMS_PER_ROI atoms, whose row of S is
+ *           then zero; a direction that is not a unit vector; a bounded wait
+ *           that ran out); the caller clears it
+ *   cuda_stream  the stream to queue on (NULL: the legacy default stream)
+ *
+ * Work is queued on the stream and the call returns without waiting.  It
+ * allocates nothing: what the call derives from its inputs lives in one
+ * library-owned scratch array of APTIDX_NOALLOC_SCRATCH_BYTES (2.5 MiB) that
+ * every GPU loading the library holds until the process exits.  Hence
+ * nroi <= APTIDX_NOALLOC_MAX_ROIS and nv <= APTIDX_NOALLOC_MAX_DIRS; larger
+ * sizes, m outside [APTIDX_MIN_M, APTIDX_MAX_M], a bad band or a misaligned
+ * xc4 return APTIDX_E_INVALID_ARG before any work is queued.  Every call
+ * shares the scratch array, which keeps the last call's contents: calls
+ * whose work overlaps on the GPU (other streams, other threads) race, so
+ * order them on one stream.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.
+ * Returns APTIDX_OK, APTIDX_E_INVALID_ARG or APTIDX_E_CUDA. */
+#define APTIDX_NOALLOC_MAX_ROIS 65536
+#define APTIDX_NOALLOC_MAX_DIRS 65536
+#define APTIDX_NOALLOC_SCRATCH_BYTES (2621440)
+#define APTIDX_STATUS_TIMEOUT  1
+#define APTIDX_STATUS_OVERFLOW 2
+#define APTIDX_STATUS_INVALID  4
+int aptidx_signatures_noalloc(const float* xc4, const int64_t* off, const double* radii, int64_t nroi,
+                              const float* u, int32_t nv, int m, int32_t k_lo, int32_t k_hi, float* S,
+                              int* status, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

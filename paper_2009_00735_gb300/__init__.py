@@ -24,7 +24,7 @@ __all__ = [
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
     "aptidx_set_reference", "aptidx_build_lut", "aptidx_match", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
-    "tc_available", "PHASES",
+    "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
     "APTIDX_NORMALISE_MAX",
 ]
@@ -76,6 +76,7 @@ _SIGS = {
     "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
     "aptidx_set_profiling": (C.c_int, [_vp, C.c_int]),
     "aptidx_get_profile": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "aptidx_signatures_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, C.c_int, _i32, _i32, _vp, _vp, _vp]),
 }
 
 APTIDX_N_PHASES = 6
@@ -312,6 +313,29 @@ def aptidx_get_profile(ctx):
     n = np.zeros(1, np.int64)
     _check(ctx, load().aptidx_get_profile(ctx, ms.ctypes.data, calls.ctypes.data, n.ctypes.data))
     return {PHASES[i]: (float(ms[i]), int(calls[i])) for i in range(APTIDX_N_PHASES)}, int(n[0])
+
+
+def aptidx_signatures_noalloc(xc4, off, radii, u, m: int, k_lo: int, k_hi: int, S, status=None, stream=None):
+    """The no-allocation call: every array is a CUDA tensor the caller owns
+    (xc4 float32 [N, 4], off int64 [nroi + 1], radii float64 [nroi], u float32
+    [nv, 3], S float32 [nroi, nv], status int32 [1] or None).  Queued on
+    `stream` (default: torch's current stream); returns without waiting."""
+    torch = _torch()
+    for t in (xc4, off, radii, u, S) + ((status,) if status is not None else ()):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("aptidx_signatures_noalloc takes contiguous CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream(S.device).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    nroi = radii.numel()
+    nv = u.numel() // 3
+    rc = load().aptidx_signatures_noalloc(xc4.data_ptr(), off.data_ptr(), radii.data_ptr(), nroi, u.data_ptr(), nv,
+                                          m, k_lo, k_hi, S.data_ptr(),
+                                          status.data_ptr() if status is not None else None,
+                                          _vp(int(stream)) if stream else None)
+    if rc != APTIDX_OK:
+        raise AptidxError(rc, "aptidx_signatures_noalloc: invalid sizes (limits in include/aptidx.h) or CUDA error")
 
 
 def tc_available(device: int = 0) -> bool:

@@ -19,6 +19,7 @@ constexpr int kTileDirs = 64;   // directions per signature work item
 // device status word bits
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusOverflow = 2;
+constexpr int kStatusInvalid = 4;
 
 struct Reference {
     float* d_node_sig = nullptr;   // [nv] normalised reference signature
@@ -156,6 +157,7 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
 int prepare_tc(Ctx* c);
 bool tc_supported(Ctx* c);
 cudaError_t launch_normalise(Ctx* c, float* S);
+size_t plain_smem_bytes(int m, int atom_cap);
 
 // indexing / refinement
 cudaError_t launch_top_nodes(Ctx* c, Reference* r);

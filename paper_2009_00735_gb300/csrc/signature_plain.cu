@@ -13,6 +13,8 @@
 // The band spectrum X(k) = sum_n h[n] e^{-2 pi i k n / 2^m} is then
 // accumulated in FP32 against a (cos, sin) table; the twiddle index is
 // uniform across a warp, so table reads are broadcasts.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace aptidx {
@@ -318,4 +320,166 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     return cudaGetLastError();
 }
 
+// -----------------------------------------------------------------------------
+// No-allocation variant (aptidx_signatures_noalloc).  Everything a call derives
+// from its inputs -- padded directions, per-ROI scale, band, atom count and
+// order, the twiddle table, the work counter -- lives in one fixed scratch
+// array in device memory, so the call allocates nothing.  Every GPU that loads
+// the library holds the array until the process exits; all calls share it.
+// -----------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNaMaxRoi = APTIDX_NOALLOC_MAX_ROIS;
+constexpr int64_t kNaMaxDirs = APTIDX_NOALLOC_MAX_DIRS;
+// byte offsets inside the scratch array
+constexpr size_t kNaDirs = 0;                                        // float4 [kNaMaxDirs]
+constexpr size_t kNaTw = kNaDirs + 16 * (size_t)kNaMaxDirs;          // float2 [1024]
+constexpr size_t kNaScale = kNaTw + 8 * 1024;                        // float  [kNaMaxRoi]
+constexpr size_t kNaBand = kNaScale + 4 * (size_t)kNaMaxRoi;         // int32  [2 kNaMaxRoi]
+constexpr size_t kNaNw = kNaBand + 8 * (size_t)kNaMaxRoi;            // int32  [kNaMaxRoi]
+constexpr size_t kNaOrder = kNaNw + 4 * (size_t)kNaMaxRoi;           // int32  [kNaMaxRoi]
+constexpr size_t kNaCounter = kNaOrder + 4 * (size_t)kNaMaxRoi;      // int32  [4]
+constexpr size_t kNaStatus = kNaCounter + 16;                        // int    [1]
+constexpr size_t kNaEnd = kNaStatus + 16;
+static_assert(kNaEnd <= APTIDX_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[APTIDX_NOALLOC_SCRATCH_BYTES];
+
+// Per-call set-up: counts, scales, bands and identity order per ROI; padded
+// float4 directions; the twiddle table.  Flags ROIs above 65535 atoms
+// (overflow) and directions that are not unit vectors (invalid input).
+__global__ void k_noalloc_setup(unsigned char* scr, const int64_t* __restrict__ off, const double* __restrict__ radii,
+                                int64_t nroi, const float* __restrict__ u, int32_t nv, int32_t nv_pad, int m,
+                                int32_t k_lo, int32_t k_hi, int* status) {
+    float4* dirs = reinterpret_cast<float4*>(scr + kNaDirs);
+    float2* tw = reinterpret_cast<float2*>(scr + kNaTw);
+    float* scale = reinterpret_cast<float*>(scr + kNaScale);
+    int32_t* band = reinterpret_cast<int32_t*>(scr + kNaBand);
+    int32_t* nw = reinterpret_cast<int32_t*>(scr + kNaNw);
+    int32_t* order = reinterpret_cast<int32_t*>(scr + kNaOrder);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int half = 1 << (m - 1);
+    for (int64_t r = t0; r < nroi; r += stride) {
+        int64_t n = off[r + 1] - off[r];
+        if (n < 0 || n > APTIDX_MAX_ATOMS_PER_ROI) {
+            atomicOr(status, kStatusOverflow);
+            n = 0;
+        }
+        nw[r] = (int32_t)n;
+        scale[r] = __double2float_rn((double)(half - 1) / radii[r]);
+        band[2 * r] = k_lo;
+        band[2 * r + 1] = k_hi;
+        order[r] = (int32_t)r;
+    }
+    for (int64_t v = t0; v < nv_pad; v += stride) {
+        float4 d = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (v < nv) {
+            d = make_float4(u[3 * v], u[3 * v + 1], u[3 * v + 2], 0.f);
+            const double n2 = (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z;
+            if (!(fabs(sqrt(n2) - 1.0) <= 1e-5)) atomicOr(status, kStatusInvalid);
+        }
+        dirs[v] = d;
+    }
+    for (int64_t j = t0; j < (int64_t)(1 << m); j += stride) {
+        double sn, cs;
+        sincospi(2.0 * (double)j / (double)(1 << m), &sn, &cs);
+        tw[j] = make_float2((float)cs, (float)sn);
+    }
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+}  // namespace
+
 }  // namespace aptidx
+
+extern "C" int aptidx_signatures_noalloc(const float* xc4, const int64_t* off, const double* radii, int64_t nroi,
+                                         const float* u, int32_t nv, int m, int32_t k_lo, int32_t k_hi, float* S,
+                                         int* status, void* cuda_stream) {
+    using namespace aptidx;
+    if (nroi < 0 || nroi > kNaMaxRoi || nv <= 0 || nv > kNaMaxDirs) return APTIDX_E_INVALID_ARG;
+    if (m < APTIDX_MIN_M || m > APTIDX_MAX_M) return APTIDX_E_INVALID_ARG;
+    if (k_lo < 0 || k_hi < k_lo || k_hi > (1 << (m - 1))) return APTIDX_E_INVALID_ARG;
+    if (nroi == 0) return APTIDX_OK;
+    if (!xc4 || !off || !radii || !u || !S) return APTIDX_E_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(xc4) & 15u) != 0) return APTIDX_E_INVALID_ARG;   // bulk copies need 16-byte rows
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return APTIDX_E_CUDA;
+    }
+    void* scr = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side
+        // name of the array is not a device address
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return APTIDX_E_CUDA;
+            }
+            g_noalloc_ptr[dev] = ptr;
+        }
+        scr = g_noalloc_ptr[dev];
+    }
+    unsigned char* base = static_cast<unsigned char*>(scr);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int* st = status ? status : reinterpret_cast<int*>(base + kNaStatus);
+    int32_t* counter = reinterpret_cast<int32_t*>(base + kNaCounter);
+    const int32_t nv_pad = (nv + kTileDirs - 1) / kTileDirs * kTileDirs;
+    int sm_count = 0, max_optin = 0;
+    if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return APTIDX_E_CUDA;
+    }
+    // the work counter must start at zero; the rest is rewritten by the set-up kernel
+    if (cudaMemsetAsync(counter, 0, 16, s) != cudaSuccess) return APTIDX_E_CUDA;
+    const int64_t work = std::max<int64_t>(nroi, (int64_t)nv_pad);
+    k_noalloc_setup<<<(unsigned)std::min<int64_t>((work + 255) / 256, 1024), 256, 0, s>>>(base, off, radii, nroi, u, nv,
+                                                                                       nv_pad, m, k_lo, k_hi, st);
+    if (cudaGetLastError() != cudaSuccess) return APTIDX_E_CUDA;
+    const size_t smem_base = plain_smem_bytes(m, 0);
+    int cap = (int)(((size_t)max_optin - smem_base) / 16);
+    cap = std::min(cap, 4096) & ~15;
+    if (cap < 256) return APTIDX_E_CUDA;
+    const size_t smem = plain_smem_bytes(m, cap);
+    if (cudaFuncSetAttribute(k_sig_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return APTIDX_E_CUDA;
+    }
+    SigParams p;
+    p.atoms = reinterpret_cast<const float4*>(xc4);
+    p.off = off;
+    p.nw = reinterpret_cast<const int32_t*>(base + kNaNw);
+    p.order = reinterpret_cast<const int32_t*>(base + kNaOrder);
+    p.dirs = reinterpret_cast<const float4*>(base + kNaDirs);
+    p.nv = nv;
+    p.tiles_per_roi = nv_pad / kDirs;
+    p.tiles_per_item = std::min(16, p.tiles_per_roi);
+    p.items_per_roi = (p.tiles_per_roi + p.tiles_per_item - 1) / p.tiles_per_item;
+    p.n_items = nroi * p.items_per_roi;
+    p.scale = reinterpret_cast<const float*>(base + kNaScale);
+    p.band = reinterpret_cast<const int32_t*>(base + kNaBand);
+    p.m = m;
+    p.tw = reinterpret_cast<const float2*>(base + kNaTw);
+    p.S = S;
+    p.argk = nullptr;
+    p.hist_out = nullptr;
+    p.single_roi = -1;
+    p.counter = counter;
+    p.status = st;
+    p.atom_cap = cap;
+    p.n_big = counter + 1;
+    p.rank_mode = kRanksAll;
+    p.nroi = nroi;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>((int64_t)sm_count * per_sm, p.n_items);
+    k_sig_plain<<<(unsigned)grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError() == cudaSuccess ? APTIDX_OK : APTIDX_E_CUDA;
+}
