@@ -177,6 +177,10 @@ int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, i
  * reference node n_k.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
 int aptidx_build_lut(aptidx_ctx* ctx, int32_t cand, const double* quats, int64_t ng, int mem);
 
+/* Debug/parity: the look-up table of candidate `cand`, lut[g * n_hat + k]
+ * (ng x n_hat int32 in `mem`); *n_hat_out receives n_hat (may be NULL). */
+int aptidx_get_lut(aptidx_ctx* ctx, int32_t cand, int32_t* lut, int32_t* n_hat_out, int mem);
+
 /* Eq. 3 for every ROI: Delta(g) = sum_k (S[roi, lut[g, k]] - ref[n_k])^2
  * over the candidate's look-up table; best[roi] = argmin_g (ties: lowest
  * g), score[roi] = Delta(best).  S: nroi x nv FP32 normalised signatures in
@@ -189,13 +193,17 @@ int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, in
 
 /* Loss and gradient of the misfit between measured signatures and the
  * candidate's reference image sampled bilinearly at R^T u:
- *   L_roi(q) = sum_v (S[roi, v] - I(alpha, beta of R(q)^T u_v))^2,
+ *   L_roi = sum_v (S[roi, v] - I(alpha, beta of R^T u_v))^2,
  * leaving out directions whose crystal-frame elevation exceeds 89 degrees
- * in magnitude.  q: nroi x 4 FP64.  loss: nroi FP32.  grad (NULL to skip):
- * nroi x 3 FP32 dL/d(delta) for R = exp([delta]x) R(q) at delta = 0 (the
- * backward kernel).  All in `mem`. */
-int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q, int64_t nroi,
-                       float* loss, float* grad, int mem);
+ * in magnitude.  The rotation is R = exp([omega]x) R(q0) (q0: nroi x 4 FP64
+ * unit quaternions; omega: nroi x 3 FP64 axis-angle vectors, or NULL for
+ * omega = 0).  loss: nroi FP32 (the forward kernel).  grad (NULL to skip):
+ * nroi x 3 FP32 dL/domega (the backward kernel; with omega = NULL this is
+ * the derivative with respect to a lab-frame rotation exp([delta]x) R(q0) at
+ * delta = 0).  All arrays in `mem`.  Errors: STATE (no reference image),
+ * INVALID_ARG, OOM, CUDA. */
+int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const double* omega,
+                       int64_t nroi, float* loss, float* grad, int mem);
 
 /* `iters` Gauss-Newton steps per ROI from q0: delta = -(J^T J + lambda I)^-1
  * J^T r with lambda = 1e-6 tr(J^T J), R <- exp([delta]x) R, FP64

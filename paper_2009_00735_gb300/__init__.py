@@ -22,7 +22,7 @@ __all__ = [
     "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
-    "aptidx_set_reference", "aptidx_build_lut", "aptidx_match", "aptidx_refine_loss", "aptidx_refine",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
@@ -70,8 +70,9 @@ _SIGS = {
     "aptidx_get_roi_atoms": (C.c_int, [_vp, _i64, _vp, _i64, C.POINTER(_i64), C.c_int]),
     "aptidx_set_reference": (C.c_int, [_vp, _i32, _vp, _i32, _vp, C.c_int]),
     "aptidx_build_lut": (C.c_int, [_vp, _i32, _vp, _i64, C.c_int]),
+    "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
-    "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, C.c_int]),
+    "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
     "aptidx_set_profiling": (C.c_int, [_vp, C.c_int]),
@@ -272,6 +273,17 @@ def aptidx_build_lut(ctx, cand: int, quats):
     _check(ctx, load().aptidx_build_lut(ctx, cand, p, ng, m))
 
 
+def aptidx_get_lut(ctx, cand: int, ng: int = None):
+    """The candidate's look-up table as int32 [ng, n_hat] (host)."""
+    nh = np.zeros(1, np.int32)
+    _check(ctx, load().aptidx_get_lut(ctx, cand, None, nh.ctypes.data, APTIDX_MEM_HOST))
+    if ng is None:
+        raise ValueError("pass ng (the number of test orientations of the table)")
+    out = np.empty((ng, int(nh[0])), np.int32)
+    _check(ctx, load().aptidx_get_lut(ctx, cand, out.ctypes.data, None, APTIDX_MEM_HOST))
+    return out
+
+
 def aptidx_match(ctx, cand: int, S, best, score=None):
     pS, mS, kS = _arg(S, np.float32)
     pb, mb = _out(best, np.int32)
@@ -280,13 +292,14 @@ def aptidx_match(ctx, cand: int, S, best, score=None):
     _check(ctx, load().aptidx_match(ctx, cand, pS, nroi, pb, ps, _one_mem(mS, mb, ms)))
 
 
-def aptidx_refine_loss(ctx, cand: int, S, q, loss, grad=None):
+def aptidx_refine_loss(ctx, cand: int, S, q0, loss, grad=None, omega=None):
     pS, mS, kS = _arg(S, np.float32)
-    pq, mq, kq = _arg(q, np.float64)
+    pq, mq, kq = _arg(q0, np.float64)
+    pw, mw, kw = _arg(omega, np.float64)
     pl, ml = _out(loss, np.float32)
     pg, mg = _out(grad, np.float32)
     nroi = loss.shape[0]
-    _check(ctx, load().aptidx_refine_loss(ctx, cand, pS, pq, nroi, pl, pg, _one_mem(mS, mq, ml, mg)))
+    _check(ctx, load().aptidx_refine_loss(ctx, cand, pS, pq, pw, nroi, pl, pg, _one_mem(mS, mq, mw, ml, mg)))
 
 
 def aptidx_refine(ctx, cand: int, S, q0, iters: int, q_out, loss=None):

@@ -134,11 +134,8 @@ static void free_rois(Ctx* c) {
     free_ptr(c->d_atoms);
     free_ptr(c->d_order);
     free_ptr(c->d_scan_tmp);
-    free_ptr(c->d_q);
-    free_ptr(c->d_acc);
     c->nroi = 0;
     c->atoms_cap = c->atoms_total = 0;
-    c->q_cap = 0;
     c->scan_tmp_elems = 0;
 }
 
@@ -674,6 +671,238 @@ int aptidx_get_roi_atoms(aptidx_ctx* ctx, int64_t roi, float* xc, int64_t cap, i
         APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     return read_status(c);
+}
+
+}  // extern "C"
+
+// ---- indexing (a6) and refinement (a7) --------------------------------------
+
+namespace {
+
+// device buffer freed at scope exit
+struct DevTmp {
+    void* p = nullptr;
+    ~DevTmp() { dev_free(p); }
+};
+
+// Device view of an input array: the pointer itself (device) or a temporary
+// device copy (host).
+template <typename T>
+int dev_view(Ctx* c, const T* src, size_t count, int mem, DevTmp& tmp, const T** out) {
+    if (mem == APTIDX_MEM_DEVICE || count == 0) {
+        *out = src;
+        return APTIDX_OK;
+    }
+    int rc = dev_alloc(c, &tmp.p, count * sizeof(T));
+    if (rc) return rc;
+    APTIDX_CUDA(c, cudaMemcpyAsync(tmp.p, src, count * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    *out = static_cast<const T*>(tmp.p);
+    return APTIDX_OK;
+}
+
+// Device destination of an output: the pointer itself (device) or a
+// temporary to copy back after the launch (host).
+template <typename T>
+int dev_out(Ctx* c, T* dst, size_t count, int mem, DevTmp& tmp, T** out) {
+    if (!dst || mem == APTIDX_MEM_DEVICE) {
+        *out = dst;
+        return APTIDX_OK;
+    }
+    int rc = dev_alloc(c, &tmp.p, count * sizeof(T));
+    if (rc) return rc;
+    *out = static_cast<T*>(tmp.p);
+    return APTIDX_OK;
+}
+
+template <typename T>
+int copy_back(Ctx* c, T* dst, const T* dsrc, size_t count, int mem) {
+    if (!dst || mem == APTIDX_MEM_DEVICE) return APTIDX_OK;
+    APTIDX_CUDA(c, cudaMemcpyAsync(dst, dsrc, count * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    return APTIDX_OK;
+}
+
+int check_ref(Ctx* c, int32_t cand, bool need_lut, bool need_img) {
+    if (cand < 0 || cand >= kMaxCandidates) return set_error(c, APTIDX_E_INVALID_ARG, "candidate %d outside [0, %d)", cand, kMaxCandidates);
+    const Reference& r = c->ref[cand];
+    if (!r.d_node_sig || r.nv_at_set != c->nv)
+        return set_error(c, APTIDX_E_STATE, "candidate %d: set the reference for the current directions first", cand);
+    if (need_lut && (!r.d_lut || r.ng <= 0)) return set_error(c, APTIDX_E_STATE, "candidate %d: build the look-up table first", cand);
+    if (need_img && !r.d_img) return set_error(c, APTIDX_E_STATE, "candidate %d: no reference image", cand);
+    return APTIDX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, int32_t n_hat, const float* img, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (cand < 0 || cand >= kMaxCandidates) return set_error(c, APTIDX_E_INVALID_ARG, "candidate %d outside [0, %d)", cand, kMaxCandidates);
+    if (c->nv <= 0) return set_error(c, APTIDX_E_STATE, "set_reference: set directions first");
+    if (!node_sig || n_hat < 1 || n_hat > c->nv)
+        return set_error(c, APTIDX_E_INVALID_ARG, "set_reference: need node_sig and 1 <= n_hat <= nv");
+    HostView<float> hs;
+    if ((rc = to_host(c, node_sig, (size_t)c->nv, mem, hs))) return rc;
+    for (int32_t v = 0; v < c->nv; ++v)
+        if (!isfinite(hs[v])) return set_error(c, APTIDX_E_INVALID_ARG, "set_reference: node value %d not finite", v);
+    Reference& r = c->ref[cand];
+    free_ptr(r.d_node_sig);
+    free_ptr(r.d_top);
+    free_ptr(r.d_top_val);
+    free_ptr(r.d_lut);
+    free_ptr(r.d_img);
+    r.ng = 0;
+    r.nv_at_set = -1;
+    if ((rc = dev_alloc(c, (void**)&r.d_node_sig, (size_t)c->nv * sizeof(float)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&r.d_top, (size_t)n_hat * sizeof(int32_t)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&r.d_top_val, (size_t)n_hat * sizeof(float)))) return rc;
+    APTIDX_CUDA(c, cudaMemcpyAsync(r.d_node_sig, hs.data(), (size_t)c->nv * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    if (img) {
+        HostView<float> hi;
+        const size_t ni = (size_t)kImgRows * kImgCols;
+        if ((rc = to_host(c, img, ni, mem, hi))) return rc;
+        for (size_t i = 0; i < ni; ++i)
+            if (!isfinite(hi[i])) return set_error(c, APTIDX_E_INVALID_ARG, "set_reference: image value %zu not finite", i);
+        if ((rc = dev_alloc(c, (void**)&r.d_img, ni * sizeof(float)))) return rc;
+        APTIDX_CUDA(c, cudaMemcpyAsync(r.d_img, hi.data(), ni * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    }
+    r.n_hat = n_hat;
+    cudaError_t e = launch_top_nodes(c, &r);
+    if (e != cudaSuccess) return cuda_check(c, e, "strongest reference nodes");
+    c->launches += 1;
+    r.nv_at_set = c->nv;
+    return APTIDX_OK;
+}
+
+int aptidx_build_lut(aptidx_ctx* ctx, int32_t cand, const double* quats, int64_t ng, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if ((rc = check_ref(c, cand, false, false))) return rc;
+    if (!quats || ng <= 0 || ng > ((int64_t)1 << 31) / std::max(1, c->ref[cand].n_hat))
+        return set_error(c, APTIDX_E_INVALID_ARG, "build_lut: need quats and 0 < ng * n_hat < 2^31");
+    HostView<double> hq;
+    if ((rc = to_host(c, quats, (size_t)ng * 4, mem, hq))) return rc;
+    for (int64_t g = 0; g < ng; ++g) {
+        const double n = sqrt(hq[4 * g] * hq[4 * g] + hq[4 * g + 1] * hq[4 * g + 1] + hq[4 * g + 2] * hq[4 * g + 2] +
+                              hq[4 * g + 3] * hq[4 * g + 3]);
+        if (!(fabs(n - 1.0) <= 1e-6)) return set_error(c, APTIDX_E_INVALID_ARG, "build_lut: quaternion %lld not unit", (long long)g);
+    }
+    Reference& r = c->ref[cand];
+    free_ptr(r.d_lut);
+    r.ng = 0;
+    DevTmp tq;
+    if ((rc = dev_alloc(c, &tq.p, (size_t)ng * 4 * sizeof(double)))) return rc;
+    APTIDX_CUDA(c, cudaMemcpyAsync(tq.p, hq.data(), (size_t)ng * 4 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = dev_alloc(c, (void**)&r.d_lut, (size_t)ng * r.n_hat * sizeof(int32_t)))) return rc;
+    cudaError_t e = launch_build_lut(c, &r, static_cast<const double*>(tq.p), ng);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "look-up table");
+    c->launches += 1;
+    r.ng = ng;
+    return APTIDX_OK;
+}
+
+int aptidx_get_lut(aptidx_ctx* ctx, int32_t cand, int32_t* lut, int32_t* n_hat_out, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if ((rc = check_ref(c, cand, true, false))) return rc;
+    Reference& r = c->ref[cand];
+    if (n_hat_out) *n_hat_out = r.n_hat;
+    if (!lut) return APTIDX_OK;
+    DevTmp t;
+    int32_t* d;
+    const size_t n = (size_t)r.ng * r.n_hat;
+    if ((rc = dev_out(c, lut, n, mem, t, &d))) return rc;
+    cudaError_t e = launch_lut_export(c, &r, d);
+    if (e != cudaSuccess) return cuda_check(c, e, "look-up table export");
+    if ((rc = copy_back(c, lut, d, n, mem))) return rc;
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    return APTIDX_OK;
+}
+
+int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, int32_t* best, float* score, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if ((rc = check_ref(c, cand, true, false))) return rc;
+    if (!S || !best || nroi <= 0) return set_error(c, APTIDX_E_INVALID_ARG, "match: need S, best and nroi > 0");
+    Reference& r = c->ref[cand];
+    static int max_optin = -1;
+    if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (((size_t)c->nv + r.n_hat) * sizeof(float) > (size_t)max_optin)
+        return set_error(c, APTIDX_E_INVALID_ARG, "match: %d directions do not fit one shared-memory signature row", c->nv);
+    DevTmp tS, tb, ts;
+    const float* dS;
+    int32_t* db;
+    float* ds;
+    if ((rc = dev_view(c, S, (size_t)nroi * c->nv, mem, tS, &dS))) return rc;
+    if ((rc = dev_out(c, best, (size_t)nroi, mem, tb, &db))) return rc;
+    if ((rc = dev_out(c, score, (size_t)nroi, mem, ts, &ds))) return rc;
+    prof_begin(c, APTIDX_PHASE_MATCH);
+    cudaError_t e = launch_match(c, &r, dS, nroi, db, ds);
+    if (e != cudaSuccess) return cuda_check(c, e, "match");
+    prof_end(c, APTIDX_PHASE_MATCH, 1);
+    if ((rc = copy_back(c, best, db, (size_t)nroi, mem))) return rc;
+    if ((rc = copy_back(c, score, ds, (size_t)nroi, mem))) return rc;
+    if (mem == APTIDX_MEM_HOST) return read_status(c);
+    return APTIDX_OK;
+}
+
+int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const double* omega,
+                       int64_t nroi, float* loss, float* grad, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if ((rc = check_ref(c, cand, false, true))) return rc;
+    if (!S || !q0 || !loss || nroi <= 0) return set_error(c, APTIDX_E_INVALID_ARG, "refine_loss: need S, q0, loss, nroi > 0");
+    DevTmp tS, tq, tw, tl, tg;
+    const float* dS;
+    const double *dq, *dw = nullptr;
+    float *dl, *dg;
+    if ((rc = dev_view(c, S, (size_t)nroi * c->nv, mem, tS, &dS))) return rc;
+    if ((rc = dev_view(c, q0, (size_t)nroi * 4, mem, tq, &dq))) return rc;
+    if (omega && (rc = dev_view(c, omega, (size_t)nroi * 3, mem, tw, &dw))) return rc;
+    if ((rc = dev_out(c, loss, (size_t)nroi, mem, tl, &dl))) return rc;
+    if ((rc = dev_out(c, grad, (size_t)nroi * 3, mem, tg, &dg))) return rc;
+    prof_begin(c, APTIDX_PHASE_REFINE);
+    cudaError_t e = launch_refine_eval(c, &c->ref[cand], dS, dq, dw, nroi, dl, dg);
+    if (e != cudaSuccess) return cuda_check(c, e, "refine loss");
+    prof_end(c, APTIDX_PHASE_REFINE, 1);
+    if ((rc = copy_back(c, loss, dl, (size_t)nroi, mem))) return rc;
+    if ((rc = copy_back(c, grad, dg, (size_t)nroi * 3, mem))) return rc;
+    if (mem == APTIDX_MEM_HOST) return read_status(c);
+    return APTIDX_OK;
+}
+
+int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, int64_t nroi, int32_t iters,
+                  double* q_out, float* loss, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if ((rc = check_ref(c, cand, false, true))) return rc;
+    if (!S || !q0 || !q_out || nroi <= 0 || iters < 0 || iters > 1000)
+        return set_error(c, APTIDX_E_INVALID_ARG, "refine: need S, q0, q_out, nroi > 0, 0 <= iters <= 1000");
+    DevTmp tS, tq, to, tl;
+    const float* dS;
+    const double* dq;
+    double* dqo;
+    float* dl;
+    if ((rc = dev_view(c, S, (size_t)nroi * c->nv, mem, tS, &dS))) return rc;
+    if ((rc = dev_view(c, q0, (size_t)nroi * 4, mem, tq, &dq))) return rc;
+    if ((rc = dev_out(c, q_out, (size_t)nroi * 4, mem, to, &dqo))) return rc;
+    if ((rc = dev_out(c, loss, (size_t)nroi, mem, tl, &dl))) return rc;
+    prof_begin(c, APTIDX_PHASE_REFINE);
+    cudaError_t e = launch_refine_gn(c, &c->ref[cand], dS, dq, nroi, iters, dqo, dl);
+    if (e != cudaSuccess) return cuda_check(c, e, "refine");
+    prof_end(c, APTIDX_PHASE_REFINE, 1);
+    if ((rc = copy_back(c, q_out, dqo, (size_t)nroi * 4, mem))) return rc;
+    if ((rc = copy_back(c, loss, dl, (size_t)nroi, mem))) return rc;
+    if (mem == APTIDX_MEM_HOST) return read_status(c);
+    return APTIDX_OK;
 }
 
 }  // extern "C"

@@ -1,30 +1,560 @@
-// indexing.cu -- steps (a6) look-up-table matching (Eq. 3) and (a7)
-// Gauss-Newton orientation refinement.  Entry points are wired; kernels land next.
+// indexing.cu -- step (a6): the look-up table and Eq. 3 matching, and step
+// (a7): Gauss-Newton orientation refinement on a bilinear elevation-azimuth
+// reference image, with forward and backward kernels for automatic
+// differentiation.
+//
+// Supplement "Indexing algorithm": the reference signature of a candidate is
+// normalised, its n_hat strongest nodes are kept, every test orientation g
+// rotates them, and the look-up table holds the measured-image node nearest
+// to each rotated reference node; Eq. 3 scores g by the sum of squared
+// differences of the image values there.  Rotations map crystal to lab.
+#include <math.h>
+
 #include "common.cuh"
 
-using namespace aptidx;
+namespace aptidx {
 
-extern "C" {
+namespace {
 
-int aptidx_set_reference(aptidx_ctx* ctx, int32_t, const float*, int32_t, const float*, int) {
-    if (!ctx) return APTIDX_E_INVALID_ARG;
-    return set_error(&ctx->c, APTIDX_E_INVALID_ARG, "set_reference: not built yet");
-}
-int aptidx_build_lut(aptidx_ctx* ctx, int32_t, const double*, int64_t, int) {
-    if (!ctx) return APTIDX_E_INVALID_ARG;
-    return set_error(&ctx->c, APTIDX_E_INVALID_ARG, "build_lut: not built yet");
-}
-int aptidx_match(aptidx_ctx* ctx, int32_t, const float*, int64_t, int32_t*, float*, int) {
-    if (!ctx) return APTIDX_E_INVALID_ARG;
-    return set_error(&ctx->c, APTIDX_E_INVALID_ARG, "match: not built yet");
-}
-int aptidx_refine_loss(aptidx_ctx* ctx, int32_t, const float*, const double*, int64_t, float*, float*, int) {
-    if (!ctx) return APTIDX_E_INVALID_ARG;
-    return set_error(&ctx->c, APTIDX_E_INVALID_ARG, "refine_loss: not built yet");
-}
-int aptidx_refine(aptidx_ctx* ctx, int32_t, const float*, const double*, int64_t, int32_t, double*, float*, int) {
-    if (!ctx) return APTIDX_E_INVALID_ARG;
-    return set_error(&ctx->c, APTIDX_E_INVALID_ARG, "refine: not built yet");
+// ---- rotations (FP64, fixed operation order, no contraction) ----------------
+
+struct M3 {
+    double a[9];
+};
+
+__device__ __forceinline__ M3 quat_to_matrix(double w, double x, double y, double z) {
+    const double xx = __dmul_rn(x, x), yy = __dmul_rn(y, y), zz = __dmul_rn(z, z);
+    const double xy = __dmul_rn(x, y), xz = __dmul_rn(x, z), yz = __dmul_rn(y, z);
+    const double wx = __dmul_rn(w, x), wy = __dmul_rn(w, y), wz = __dmul_rn(w, z);
+    M3 m;
+    m.a[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(yy, zz)));
+    m.a[1] = __dmul_rn(2.0, __dsub_rn(xy, wz));
+    m.a[2] = __dmul_rn(2.0, __dadd_rn(xz, wy));
+    m.a[3] = __dmul_rn(2.0, __dadd_rn(xy, wz));
+    m.a[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, zz)));
+    m.a[5] = __dmul_rn(2.0, __dsub_rn(yz, wx));
+    m.a[6] = __dmul_rn(2.0, __dsub_rn(xz, wy));
+    m.a[7] = __dmul_rn(2.0, __dadd_rn(yz, wx));
+    m.a[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, yy)));
+    return m;
 }
 
-}  // extern "C"
+__device__ __forceinline__ void quat_mul(const double* a, const double* b, double* o) {
+    const double r0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    const double r1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    const double r2 = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    const double r3 = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    o[0] = r0;
+    o[1] = r1;
+    o[2] = r2;
+    o[3] = r3;
+}
+
+__device__ __forceinline__ void exp_quat(const double* d, double* q) {
+    const double th = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (th < 1e-300) {
+        q[0] = 1.0;
+        q[1] = q[2] = q[3] = 0.0;
+        return;
+    }
+    const double s = sin(0.5 * th) / th;
+    q[0] = cos(0.5 * th);
+    q[1] = s * d[0];
+    q[2] = s * d[1];
+    q[3] = s * d[2];
+}
+
+// ---- strongest reference nodes (bitonic sort of packed keys, one block) -----
+
+__device__ __forceinline__ uint32_t ordered_f32(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// key = (descending value, ascending index); padding sorts last
+__global__ void __launch_bounds__(1024) k_top_nodes(const float* __restrict__ sig, int32_t nv, int32_t npow2,
+                                                    uint64_t* keys, int32_t n_hat, int32_t* top, float* top_val) {
+    for (int i = threadIdx.x; i < npow2; i += blockDim.x)
+        keys[i] = i < nv ? ((uint64_t)(~ordered_f32(sig[i])) << 32) | (uint32_t)i : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint64_t a = keys[i], b = keys[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n_hat; i += blockDim.x) {
+        const int32_t idx = (int32_t)(keys[i] & 0xFFFFFFFFu);
+        top[i] = idx;
+        top_val[i] = sig[idx];
+    }
+}
+
+// ---- look-up table ---------------------------------------------------------------
+
+constexpr int kLutThreads = 256;
+constexpr int kLutPer = 4;                       // queries per thread
+constexpr int kLutTile = 2048;                   // nodes per shared-memory tile
+
+// lut_t[k * ng + g] = argmax_p u_p . r with r = (float)(R(q_g) n_top[k]) (FP64
+// products summed left to right), the dot product by the FP32 contract
+// fma(u_z, r_z, fma(u_y, r_y, u_x r_x)); ties resolve to the lowest index.
+__global__ void __launch_bounds__(kLutThreads) k_build_lut(const float4* __restrict__ dirs, int32_t nv,
+                                                           const int32_t* __restrict__ top, int32_t n_hat,
+                                                           const double* __restrict__ quats, int64_t ng,
+                                                           int32_t* lut_t) {
+    __shared__ float4 tile[kLutTile];
+    const int64_t nq = ng * n_hat;
+    const int64_t q0 = (int64_t)blockIdx.x * kLutThreads * kLutPer;
+    float rx[kLutPer], ry[kLutPer], rz[kLutPer], best[kLutPer];
+    int32_t bi[kLutPer];
+    int64_t qi[kLutPer];
+#pragma unroll
+    for (int j = 0; j < kLutPer; ++j) {
+        const int64_t q = q0 + (int64_t)j * kLutThreads + threadIdx.x;
+        qi[j] = q;
+        best[j] = -INFINITY;
+        bi[j] = 0;
+        rx[j] = ry[j] = rz[j] = 0.f;
+        if (q < nq) {
+            const int64_t g = q / n_hat;
+            const int k = (int)(q % n_hat);
+            const M3 R = quat_to_matrix(quats[4 * g], quats[4 * g + 1], quats[4 * g + 2], quats[4 * g + 3]);
+            const float4 n = dirs[top[k]];
+            const double nx = n.x, ny = n.y, nz = n.z;
+            rx[j] = __double2float_rn(__dadd_rn(__dadd_rn(__dmul_rn(R.a[0], nx), __dmul_rn(R.a[1], ny)), __dmul_rn(R.a[2], nz)));
+            ry[j] = __double2float_rn(__dadd_rn(__dadd_rn(__dmul_rn(R.a[3], nx), __dmul_rn(R.a[4], ny)), __dmul_rn(R.a[5], nz)));
+            rz[j] = __double2float_rn(__dadd_rn(__dadd_rn(__dmul_rn(R.a[6], nx), __dmul_rn(R.a[7], ny)), __dmul_rn(R.a[8], nz)));
+        }
+    }
+    for (int p0 = 0; p0 < nv; p0 += kLutTile) {
+        const int cnt = min(kLutTile, nv - p0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kLutThreads) tile[i] = dirs[p0 + i];
+        __syncthreads();
+        for (int i = 0; i < cnt; ++i) {
+            const float4 u = tile[i];
+#pragma unroll
+            for (int j = 0; j < kLutPer; ++j) {
+                const float d = __fmaf_rn(u.z, rz[j], __fmaf_rn(u.y, ry[j], __fmul_rn(u.x, rx[j])));
+                if (d > best[j]) {
+                    best[j] = d;
+                    bi[j] = p0 + i;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kLutPer; ++j) {
+        const int64_t q = qi[j];
+        if (q < nq) {
+            const int64_t g = q / n_hat;
+            const int k = (int)(q % n_hat);
+            lut_t[(int64_t)k * ng + g] = bi[j];
+        }
+    }
+}
+
+// ---- Eq. 3 -----------------------------------------------------------------------
+
+constexpr int kMatchThreads = 512;
+
+// One CTA per ROI (persistent): the ROI's signature row in shared memory,
+// Delta(g) = sum_k (S[lut[k, g]] - ref[k])^2 accumulated in FP32 in k order,
+// argmin with ties to the lowest g.
+__global__ void __launch_bounds__(kMatchThreads) k_match(const float* __restrict__ S, int64_t nroi, int32_t nv,
+                                                         const int32_t* __restrict__ lut_t, int64_t ng,
+                                                         const float* __restrict__ top_val, int32_t n_hat,
+                                                         int32_t* best, float* score) {
+    extern __shared__ float sm[];
+    float* row = sm;                     // nv
+    float* ref = sm + nv;                // n_hat
+    __shared__ float red_v[kMatchThreads / 32];
+    __shared__ int32_t red_g[kMatchThreads / 32];
+    for (int i = threadIdx.x; i < n_hat; i += kMatchThreads) ref[i] = top_val[i];
+    for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
+        __syncthreads();
+        const float* src = S + r * (int64_t)nv;
+        for (int i = threadIdx.x; i < nv; i += kMatchThreads) row[i] = src[i];
+        __syncthreads();
+        float bv = INFINITY;
+        int32_t bg = 0x7FFFFFFF;
+        for (int64_t g = threadIdx.x; g < ng; g += kMatchThreads) {
+            float acc = 0.f;
+            const int32_t* lp = lut_t + g;
+            for (int k = 0; k < n_hat; ++k) {
+                const float d = row[lp[(int64_t)k * ng]] - ref[k];
+                acc = fmaf(d, d, acc);
+            }
+            if (acc < bv) {
+                bv = acc;
+                bg = (int32_t)g;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int32_t og = __shfl_xor_sync(0xffffffffu, bg, o);
+            if (ov < bv || (ov == bv && og < bg)) {
+                bv = ov;
+                bg = og;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red_v[threadIdx.x >> 5] = bv;
+            red_g[threadIdx.x >> 5] = bg;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kMatchThreads / 32; ++w)
+                if (red_v[w] < bv || (red_v[w] == bv && red_g[w] < bg)) {
+                    bv = red_v[w];
+                    bg = red_g[w];
+                }
+            best[r] = bg;
+            if (score) score[r] = bv;
+        }
+    }
+}
+
+// ---- refinement ----------------------------------------------------------------------
+
+constexpr int kRefThreads = 256;
+constexpr float kPoleDeg = 89.0f;
+constexpr float kRad2Deg = 57.295779513082320876f;
+
+struct DirTerm {
+    bool ok;
+    float r;       // residual S - I
+    float J[3];    // d r / d delta
+};
+
+// residual and its derivative with respect to the lab-frame perturbation delta
+// of R = exp([delta]x) R(q) for one direction: c = R^T u, (alpha, beta) of c,
+// bilinear sample of the image, r = s - I, J = -(R grad_c I) x u.
+__device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy, float uz, float s,
+                                            const float* __restrict__ img, bool want_j) {
+    DirTerm t;
+    const float cx = Rf[0] * ux + Rf[3] * uy + Rf[6] * uz;
+    const float cy = Rf[1] * ux + Rf[4] * uy + Rf[7] * uz;
+    const float cz = Rf[2] * ux + Rf[5] * uy + Rf[8] * uz;
+    const float rho2 = cx * cx + cy * cy;
+    const float rho = sqrtf(rho2);
+    const float alpha = atan2f(cz, rho) * kRad2Deg;
+    t.ok = fabsf(alpha) <= kPoleDeg;
+    if (!t.ok) return t;
+    float beta = atan2f(cy, cx) * kRad2Deg;
+    if (beta < 0.f) beta += 360.f;
+    const float fi = alpha + 90.f;
+    int i0 = (int)floorf(fi);
+    i0 = min(max(i0, 0), kImgRows - 2);
+    const float fj0 = floorf(beta);
+    const float ti = fi - (float)i0;
+    const float tj = beta - fj0;
+    int j0 = (int)fj0;
+    j0 = j0 >= kImgCols ? j0 - kImgCols : j0;
+    j0 = min(max(j0, 0), kImgCols - 1);
+    const int j1 = j0 + 1 == kImgCols ? 0 : j0 + 1;
+    const float I00 = __ldg(img + i0 * kImgCols + j0), I01 = __ldg(img + i0 * kImgCols + j1);
+    const float I10 = __ldg(img + (i0 + 1) * kImgCols + j0), I11 = __ldg(img + (i0 + 1) * kImgCols + j1);
+    const float v = (1.f - ti) * ((1.f - tj) * I00 + tj * I01) + ti * ((1.f - tj) * I10 + tj * I11);
+    t.r = s - v;
+    if (want_j) {
+        const float dfi = (1.f - tj) * (I10 - I00) + tj * (I11 - I01);
+        const float dfj = (1.f - ti) * (I01 - I00) + ti * (I11 - I10);
+        const float n2 = rho2 + cz * cz;
+        const float da0 = -cz * cx / (rho * n2), da1 = -cz * cy / (rho * n2), da2 = rho / n2;
+        const float db0 = -cy / rho2, db1 = cx / rho2;
+        const float g0 = kRad2Deg * (dfi * da0 + dfj * db0);
+        const float g1 = kRad2Deg * (dfi * da1 + dfj * db1);
+        const float g2 = kRad2Deg * (dfi * da2);
+        const float ax = Rf[0] * g0 + Rf[1] * g1 + Rf[2] * g2;
+        const float ay = Rf[3] * g0 + Rf[4] * g1 + Rf[5] * g2;
+        const float az = Rf[6] * g0 + Rf[7] * g1 + Rf[8] * g2;
+        t.J[0] = -(ay * uz - az * uy);
+        t.J[1] = -(az * ux - ax * uz);
+        t.J[2] = -(ax * uy - ay * ux);
+    }
+    return t;
+}
+
+// block sum of n FP32 partials per thread into FP64 totals (thread 0 holds them)
+template <int N>
+__device__ __forceinline__ void block_sum(float* v, double* out, double* scratch /* [N * 8] */) {
+    double d[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        d[i] = (double)v[i];
+        for (int o = 16; o > 0; o >>= 1) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+    }
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) scratch[i * (kRefThreads / 32) + w] = d[i];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < kRefThreads / 32; ++k) s += scratch[i * (kRefThreads / 32) + k];
+            out[i] = s;
+        }
+}
+
+// Current rotation of ROI r: q = exp(omega) (x) q0 when omega is given.
+__device__ __forceinline__ void roi_quat(const double* q0, const double* omega, int64_t r, double* q) {
+    const double* a = q0 + 4 * r;
+    if (omega) {
+        double e[4];
+        exp_quat(omega + 3 * r, e);
+        quat_mul(e, a, q);
+    } else {
+        q[0] = a[0];
+        q[1] = a[1];
+        q[2] = a[2];
+        q[3] = a[3];
+    }
+    const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int i = 0; i < 4; ++i) q[i] /= n;
+}
+
+__device__ __forceinline__ void matrix_f32(const double* q, float* Rf) {
+    const M3 R = quat_to_matrix(q[0], q[1], q[2], q[3]);
+    for (int i = 0; i < 9; ++i) Rf[i] = (float)R.a[i];
+}
+
+// Forward (loss) and backward (gradient) of L = sum_v (S_v - I(R^T u_v))^2.
+// With omega, the gradient is with respect to omega (rotation exp([omega]x)
+// R(q0)): dL/domega = J_l(omega)^T dL/ddelta, J_l the left Jacobian of SO(3).
+template <bool kGrad>
+__global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __restrict__ S, const float4* __restrict__ dirs,
+                                                             int32_t nv, const float* __restrict__ img,
+                                                             const double* __restrict__ q0, const double* __restrict__ omega,
+                                                             int64_t nroi, float* loss, float* grad) {
+    __shared__ double scratch[4 * (kRefThreads / 32)];
+    __shared__ double tot[4];
+    __shared__ float Rs[9];
+    for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
+        if (threadIdx.x == 0) {
+            double q[4];
+            roi_quat(q0, omega, r, q);
+            matrix_f32(q, Rs);
+        }
+        __syncthreads();
+        float Rf[9];
+        for (int i = 0; i < 9; ++i) Rf[i] = Rs[i];
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* srow = S + r * (int64_t)nv;
+        for (int v = threadIdx.x; v < nv; v += kRefThreads) {
+            const float4 u = dirs[v];
+            const DirTerm t = dir_term(Rf, u.x, u.y, u.z, srow[v], img, kGrad);
+            if (!t.ok) continue;
+            acc[0] = fmaf(t.r, t.r, acc[0]);
+            if (kGrad) {
+                acc[1] = fmaf(2.f * t.r, t.J[0], acc[1]);
+                acc[2] = fmaf(2.f * t.r, t.J[1], acc[2]);
+                acc[3] = fmaf(2.f * t.r, t.J[2], acc[3]);
+            }
+        }
+        block_sum<4>(acc, tot, scratch);
+        if (threadIdx.x == 0) {
+            if (loss) loss[r] = (float)tot[0];
+            if (kGrad && grad) {
+                double g[3] = {tot[1], tot[2], tot[3]};
+                if (omega) {
+                    // g_omega = J_l(omega)^T g_delta
+                    const double* w = omega + 3 * r;
+                    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+                    const double th = sqrt(th2);
+                    double A, B;
+                    if (th < 1e-4) {
+                        A = 0.5 - th2 / 24.0;
+                        B = 1.0 / 6.0 - th2 / 120.0;
+                    } else {
+                        A = (1.0 - cos(th)) / th2;
+                        B = (th - sin(th)) / (th2 * th);
+                    }
+                    // J_l = I + A [w]x + B [w]x^2;  J_l^T g = g - A (w x g) + B (w x (w x g))
+                    const double c1[3] = {w[1] * g[2] - w[2] * g[1], w[2] * g[0] - w[0] * g[2], w[0] * g[1] - w[1] * g[0]};
+                    const double c2[3] = {w[1] * c1[2] - w[2] * c1[1], w[2] * c1[0] - w[0] * c1[2], w[0] * c1[1] - w[1] * c1[0]};
+                    for (int i = 0; i < 3; ++i) g[i] = g[i] - A * c1[i] + B * c2[i];
+                }
+                grad[3 * r] = (float)g[0];
+                grad[3 * r + 1] = (float)g[1];
+                grad[3 * r + 2] = (float)g[2];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// `iters` Gauss-Newton steps per ROI in one CTA: per step the direction terms
+// give J^T J and J^T r (FP32 partials, FP64 block sums), thread 0 solves
+// (J^T J + lambda I) delta = -J^T r with lambda = 1e-6 tr(J^T J) in FP64 and
+// updates q <- exp(delta) q with FP64 renormalisation.
+__global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restrict__ S, const float4* __restrict__ dirs,
+                                                           int32_t nv, const float* __restrict__ img,
+                                                           const double* __restrict__ q0, int64_t nroi, int iters,
+                                                           double* q_out, float* loss_out) {
+    __shared__ double scratch[10 * (kRefThreads / 32)];
+    __shared__ double tot[10];
+    __shared__ double qs[4];
+    __shared__ float Rs[9];
+    for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
+        if (threadIdx.x == 0) {
+            double n = 0.0;
+            for (int i = 0; i < 4; ++i) n += q0[4 * r + i] * q0[4 * r + i];
+            n = sqrt(n);
+            for (int i = 0; i < 4; ++i) qs[i] = q0[4 * r + i] / n;
+        }
+        const float* srow = S + r * (int64_t)nv;
+        for (int it = 0; it <= iters; ++it) {
+            const bool last = it == iters;   // final pass: loss only
+            if (threadIdx.x == 0) matrix_f32(qs, Rs);
+            __syncthreads();
+            float Rf[9];
+            for (int i = 0; i < 9; ++i) Rf[i] = Rs[i];
+            float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // L, Jtr[3], JtJ[6]
+            for (int v = threadIdx.x; v < nv; v += kRefThreads) {
+                const float4 u = dirs[v];
+                const DirTerm t = dir_term(Rf, u.x, u.y, u.z, srow[v], img, !last);
+                if (!t.ok) continue;
+                acc[0] = fmaf(t.r, t.r, acc[0]);
+                if (!last) {
+                    acc[1] = fmaf(t.J[0], t.r, acc[1]);
+                    acc[2] = fmaf(t.J[1], t.r, acc[2]);
+                    acc[3] = fmaf(t.J[2], t.r, acc[3]);
+                    acc[4] = fmaf(t.J[0], t.J[0], acc[4]);
+                    acc[5] = fmaf(t.J[0], t.J[1], acc[5]);
+                    acc[6] = fmaf(t.J[0], t.J[2], acc[6]);
+                    acc[7] = fmaf(t.J[1], t.J[1], acc[7]);
+                    acc[8] = fmaf(t.J[1], t.J[2], acc[8]);
+                    acc[9] = fmaf(t.J[2], t.J[2], acc[9]);
+                }
+            }
+            block_sum<10>(acc, tot, scratch);
+            if (threadIdx.x == 0) {
+                if (last) {
+                    if (loss_out) loss_out[r] = (float)tot[0];
+                } else {
+                    double H[9] = {tot[4], tot[5], tot[6], tot[5], tot[7], tot[8], tot[6], tot[8], tot[9]};
+                    const double lam = 1e-6 * (H[0] + H[4] + H[8]);
+                    H[0] += lam;
+                    H[4] += lam;
+                    H[8] += lam;
+                    const double b[3] = {-tot[1], -tot[2], -tot[3]};
+                    const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                                       H[2] * (H[3] * H[7] - H[4] * H[6]);
+                    double d[3] = {0.0, 0.0, 0.0};
+                    if (fabs(det) > 0.0) {
+                        for (int c = 0; c < 3; ++c) {
+                            double Bm[9];
+                            for (int i = 0; i < 9; ++i) Bm[i] = H[i];
+                            Bm[c] = b[0];
+                            Bm[3 + c] = b[1];
+                            Bm[6 + c] = b[2];
+                            d[c] = (Bm[0] * (Bm[4] * Bm[8] - Bm[5] * Bm[7]) - Bm[1] * (Bm[3] * Bm[8] - Bm[5] * Bm[6]) +
+                                    Bm[2] * (Bm[3] * Bm[7] - Bm[4] * Bm[6])) / det;
+                        }
+                    }
+                    double e[4], qn[4];
+                    exp_quat(d, e);
+                    quat_mul(e, qs, qn);
+                    const double n = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+                    for (int i = 0; i < 4; ++i) qs[i] = qn[i] / n;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double sgn = qs[0] < 0.0 ? -1.0 : 1.0;
+            for (int i = 0; i < 4; ++i) q_out[4 * r + i] = sgn * qs[i];
+        }
+        __syncthreads();
+    }
+}
+
+// k-major table to g-major
+__global__ void k_lut_transpose(const int32_t* __restrict__ lut_t, int64_t ng, int32_t n_hat, int32_t* out) {
+    const int64_t n = ng * n_hat;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = i / n_hat;
+        const int k = (int)(i % n_hat);
+        out[i] = lut_t[(int64_t)k * ng + g];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_lut_export(Ctx* c, Reference* r, int32_t* out) {
+    const int64_t n = r->ng * r->n_hat;
+    k_lut_transpose<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, c->stream>>>(r->d_lut, r->ng, r->n_hat, out);
+    return cudaGetLastError();
+}
+
+// ---- launches ------------------------------------------------------------------------
+
+cudaError_t launch_top_nodes(Ctx* c, Reference* r) {
+    int32_t npow2 = 1;
+    while (npow2 < c->nv) npow2 <<= 1;
+    uint64_t* keys = nullptr;
+    if (dev_alloc(c, (void**)&keys, (size_t)npow2 * sizeof(uint64_t))) return cudaErrorMemoryAllocation;
+    k_top_nodes<<<1, 1024, 0, c->stream>>>(r->d_node_sig, c->nv, npow2, keys, r->n_hat, r->d_top, r->d_top_val);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(keys);
+    return e;
+}
+
+cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng) {
+    const int64_t nq = ng * r->n_hat;
+    const int64_t per = (int64_t)kLutThreads * kLutPer;
+    k_build_lut<<<(unsigned)((nq + per - 1) / per), kLutThreads, 0, c->stream>>>(c->d_dirs, c->nv, r->d_top, r->n_hat,
+                                                                                 d_quats, ng, r->d_lut);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score) {
+    const size_t smem = ((size_t)c->nv + r->n_hat) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_match, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match, kMatchThreads, smem);
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, nroi);
+    k_match<<<(unsigned)grid, kMatchThreads, smem, c->stream>>>(S, nroi, c->nv, r->d_lut, r->ng, r->d_top_val, r->n_hat,
+                                                                 best, score);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q0, const double* omega,
+                               int64_t nroi, float* loss, float* grad) {
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * 8, nroi);
+    if (grad)
+        k_refine_eval<true><<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, omega,
+                                                                          nroi, loss, grad);
+    else
+        k_refine_eval<false><<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, omega,
+                                                                           nroi, loss, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, int64_t nroi, int iters,
+                             double* q_out, float* loss) {
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * 8, nroi);
+    k_refine_gn<<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, nroi, iters, q_out,
+                                                               loss);
+    return cudaGetLastError();
+}
+
+}  // namespace aptidx

@@ -106,10 +106,6 @@ struct Ctx {
 
     Reference ref[kMaxCandidates];
 
-    // refinement scratch
-    double* d_q = nullptr;
-    double* d_acc = nullptr;           // [nroi x 16] FP64 accumulators
-    int64_t q_cap = 0;
 
     // profiling (CUDA events on the stream around phases)
     bool prof = false;
@@ -162,12 +158,12 @@ size_t plain_smem_bytes(int m, int atom_cap);
 // indexing / refinement
 cudaError_t launch_top_nodes(Ctx* c, Reference* r);
 cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng);
-cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best,
-                         float* score);
-cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q, int64_t nroi,
-                               float* loss, float* grad, double* acc);
-cudaError_t launch_refine_update(Ctx* c, double* q, const double* acc, int64_t nroi);
-cudaError_t launch_refine_finish(Ctx* c, double* q, int64_t nroi);
+cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score);
+cudaError_t launch_lut_export(Ctx* c, Reference* r, int32_t* out);
+cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q0, const double* omega,
+                               int64_t nroi, float* loss, float* grad);
+cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, int64_t nroi, int iters,
+                             double* q_out, float* loss);
 
 }  // namespace aptidx
 
