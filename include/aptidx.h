@@ -205,12 +205,15 @@ int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, in
 int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const double* omega,
                        int64_t nroi, float* loss, float* grad, int mem);
 
-/* `iters` Gauss-Newton steps per ROI from q0: delta = -(J^T J + lambda I)^-1
- * J^T r with lambda = 1e-6 tr(J^T J), R <- exp([delta]x) R, FP64
- * renormalisation.  q_out: nroi x 4 FP64 (w >= 0); loss: nroi FP32 at q_out
- * (NULL to skip).  All in `mem`. */
-int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, int64_t nroi,
-                  int32_t iters, double* q_out, float* loss, int mem);
+/* `iters` Gauss-Newton steps per ROI: delta = -(J^T J + lambda I)^-1 J^T r
+ * with lambda = 1e-6 tr(J^T J), R <- exp([delta]x) R, FP64 renormalisation.
+ * The start is q0[roi] (nroi x 4 FP64), or, when `best` (nroi int32) is
+ * given, the candidate's test orientation best[roi] from the last
+ * aptidx_build_lut (as aptidx_match returns it); q0 may then be NULL.
+ * q_out: nroi x 4 FP64 (w >= 0); loss: nroi FP32 at q_out (NULL to skip).
+ * All arrays in `mem`.  Errors: STATE, INVALID_ARG, OOM, CUDA. */
+int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const int32_t* best,
+                  int64_t nroi, int32_t iters, double* q_out, float* loss, int mem);
 
 /* ---- capabilities and profiling ------------------------------------------- */
 

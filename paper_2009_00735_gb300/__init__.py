@@ -73,7 +73,7 @@ _SIGS = {
     "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_int]),
-    "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
+    "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
     "aptidx_set_profiling": (C.c_int, [_vp, C.c_int]),
     "aptidx_get_profile": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -302,13 +302,16 @@ def aptidx_refine_loss(ctx, cand: int, S, q0, loss, grad=None, omega=None):
     _check(ctx, load().aptidx_refine_loss(ctx, cand, pS, pq, pw, nroi, pl, pg, _one_mem(mS, mq, mw, ml, mg)))
 
 
-def aptidx_refine(ctx, cand: int, S, q0, iters: int, q_out, loss=None):
+def aptidx_refine(ctx, cand: int, S, q0, iters: int, q_out, loss=None, best=None):
+    """Gauss-Newton from q0 [nroi, 4], or from the test orientations best
+    [nroi] of the candidate's look-up table when `best` is given."""
     pS, mS, kS = _arg(S, np.float32)
     pq, mq, kq = _arg(q0, np.float64)
+    pb, mb, kb = _arg(best, np.int32)
     po, mo = _out(q_out, np.float64)
     pl, ml = _out(loss, np.float32)
     nroi = q_out.shape[0]
-    _check(ctx, load().aptidx_refine(ctx, cand, pS, pq, nroi, iters, po, pl, _one_mem(mS, mq, mo, ml)))
+    _check(ctx, load().aptidx_refine(ctx, cand, pS, pq, pb, nroi, iters, po, pl, _one_mem(mS, mq, mb, mo, ml)))
 
 
 def aptidx_path_supported(ctx, path: int) -> bool:

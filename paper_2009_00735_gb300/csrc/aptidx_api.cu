@@ -283,6 +283,7 @@ int aptidx_destroy(aptidx_ctx* ctx) {
         free_ptr(r.d_top_val);
         free_ptr(r.d_img);
         free_ptr(r.d_lut);
+        free_ptr(r.d_quats);
     }
     delete ctx;
     return APTIDX_OK;
@@ -752,6 +753,7 @@ int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, i
     free_ptr(r.d_top);
     free_ptr(r.d_top_val);
     free_ptr(r.d_lut);
+    free_ptr(r.d_quats);
     free_ptr(r.d_img);
     r.ng = 0;
     r.nv_at_set = -1;
@@ -792,12 +794,12 @@ int aptidx_build_lut(aptidx_ctx* ctx, int32_t cand, const double* quats, int64_t
     }
     Reference& r = c->ref[cand];
     free_ptr(r.d_lut);
+    free_ptr(r.d_quats);
     r.ng = 0;
-    DevTmp tq;
-    if ((rc = dev_alloc(c, &tq.p, (size_t)ng * 4 * sizeof(double)))) return rc;
-    APTIDX_CUDA(c, cudaMemcpyAsync(tq.p, hq.data(), (size_t)ng * 4 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if ((rc = dev_alloc(c, (void**)&r.d_quats, (size_t)ng * 4 * sizeof(double)))) return rc;
+    APTIDX_CUDA(c, cudaMemcpyAsync(r.d_quats, hq.data(), (size_t)ng * 4 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if ((rc = dev_alloc(c, (void**)&r.d_lut, (size_t)ng * r.n_hat * sizeof(int32_t)))) return rc;
-    cudaError_t e = launch_build_lut(c, &r, static_cast<const double*>(tq.p), ng);
+    cudaError_t e = launch_build_lut(c, &r, r.d_quats, ng);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "look-up table");
     c->launches += 1;
@@ -878,25 +880,35 @@ int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const doub
     return APTIDX_OK;
 }
 
-int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, int64_t nroi, int32_t iters,
-                  double* q_out, float* loss, int mem) {
+int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const int32_t* best, int64_t nroi,
+                  int32_t iters, double* q_out, float* loss, int mem) {
     CTX_OR_FAIL(ctx);
     int rc;
     if ((rc = check_mem(c, mem))) return rc;
-    if ((rc = check_ref(c, cand, false, true))) return rc;
-    if (!S || !q0 || !q_out || nroi <= 0 || iters < 0 || iters > 1000)
-        return set_error(c, APTIDX_E_INVALID_ARG, "refine: need S, q0, q_out, nroi > 0, 0 <= iters <= 1000");
-    DevTmp tS, tq, to, tl;
+    if ((rc = check_ref(c, cand, best != nullptr, true))) return rc;
+    if (!S || (!q0 && !best) || !q_out || nroi <= 0 || iters < 0 || iters > 1000)
+        return set_error(c, APTIDX_E_INVALID_ARG, "refine: need S, q0 or best, q_out, nroi > 0, 0 <= iters <= 1000");
+    DevTmp tS, tq, tb, to, tl;
     const float* dS;
-    const double* dq;
+    const double* dq = nullptr;
+    const int32_t* db = nullptr;
     double* dqo;
     float* dl;
     if ((rc = dev_view(c, S, (size_t)nroi * c->nv, mem, tS, &dS))) return rc;
-    if ((rc = dev_view(c, q0, (size_t)nroi * 4, mem, tq, &dq))) return rc;
+    if (best) {
+        HostView<int32_t> hb;
+        if ((rc = to_host(c, best, (size_t)nroi, mem, hb))) return rc;
+        for (int64_t i = 0; i < nroi; ++i)
+            if (hb[i] < 0 || hb[i] >= c->ref[cand].ng)
+                return set_error(c, APTIDX_E_INVALID_ARG, "refine: best[%lld] = %d outside the table", (long long)i, hb[i]);
+        if ((rc = dev_view(c, best, (size_t)nroi, mem, tb, &db))) return rc;
+    } else if ((rc = dev_view(c, q0, (size_t)nroi * 4, mem, tq, &dq))) {
+        return rc;
+    }
     if ((rc = dev_out(c, q_out, (size_t)nroi * 4, mem, to, &dqo))) return rc;
     if ((rc = dev_out(c, loss, (size_t)nroi, mem, tl, &dl))) return rc;
     prof_begin(c, APTIDX_PHASE_REFINE);
-    cudaError_t e = launch_refine_gn(c, &c->ref[cand], dS, dq, nroi, iters, dqo, dl);
+    cudaError_t e = launch_refine_gn(c, &c->ref[cand], dS, dq, db, nroi, iters, dqo, dl);
     if (e != cudaSuccess) return cuda_check(c, e, "refine");
     prof_end(c, APTIDX_PHASE_REFINE, 1);
     if ((rc = copy_back(c, q_out, dqo, (size_t)nroi * 4, mem))) return rc;

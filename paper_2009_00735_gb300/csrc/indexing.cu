@@ -404,7 +404,8 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __rest
 // updates q <- exp(delta) q with FP64 renormalisation.
 __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restrict__ S, const float4* __restrict__ dirs,
                                                            int32_t nv, const float* __restrict__ img,
-                                                           const double* __restrict__ q0, int64_t nroi, int iters,
+                                                           const double* __restrict__ q0, const int32_t* __restrict__ best,
+                                                           const double* __restrict__ quats, int64_t nroi, int iters,
                                                            double* q_out, float* loss_out) {
     __shared__ double scratch[10 * (kRefThreads / 32)];
     __shared__ double tot[10];
@@ -412,10 +413,11 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restri
     __shared__ float Rs[9];
     for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
         if (threadIdx.x == 0) {
+            const double* qa = best ? quats + 4 * (int64_t)best[r] : q0 + 4 * r;
             double n = 0.0;
-            for (int i = 0; i < 4; ++i) n += q0[4 * r + i] * q0[4 * r + i];
+            for (int i = 0; i < 4; ++i) n += qa[i] * qa[i];
             n = sqrt(n);
-            for (int i = 0; i < 4; ++i) qs[i] = q0[4 * r + i] / n;
+            for (int i = 0; i < 4; ++i) qs[i] = qa[i] / n;
         }
         const float* srow = S + r * (int64_t)nv;
         for (int it = 0; it <= iters; ++it) {
@@ -549,11 +551,11 @@ cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, int64_t nroi, int iters,
-                             double* q_out, float* loss) {
+cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, const int32_t* best,
+                             int64_t nroi, int iters, double* q_out, float* loss) {
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * 8, nroi);
-    k_refine_gn<<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, nroi, iters, q_out,
-                                                               loss);
+    k_refine_gn<<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, best, r->d_quats,
+                                                               nroi, iters, q_out, loss);
     return cudaGetLastError();
 }
 

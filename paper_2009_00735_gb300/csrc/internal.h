@@ -27,7 +27,8 @@ struct Reference {
     float* d_top_val = nullptr;    // [n_hat] their values
     int32_t n_hat = 0;
     float* d_img = nullptr;        // [181 x 360] or null
-    int32_t* d_lut = nullptr;      // [ng x n_hat]
+    int32_t* d_lut = nullptr;      // [n_hat x ng] (k-major)
+    double* d_quats = nullptr;     // [ng x 4] test orientations of the table
     int64_t ng = 0;
     int32_t nv_at_set = 0;
 };
@@ -162,8 +163,8 @@ cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int
 cudaError_t launch_lut_export(Ctx* c, Reference* r, int32_t* out);
 cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q0, const double* omega,
                                int64_t nroi, float* loss, float* grad);
-cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, int64_t nroi, int iters,
-                             double* q_out, float* loss);
+cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, const int32_t* best,
+                             int64_t nroi, int iters, double* q_out, float* loss);
 
 }  // namespace aptidx
 

@@ -239,3 +239,24 @@ def test_autograd_function(torch_cuda, refine_case):
         l1 = refine_loss(omega, Sd, qd, ctx.handle).detach().cpu().numpy()
     assert np.all(l1 < l0)
     ctx.close()
+
+
+def test_refine_from_matched_orientation(torch_cuda, refine_case):
+    """Starting from the table's test orientation best[roi] equals starting
+    from that quaternion explicitly."""
+    u, img, S, q0, truth = refine_case
+    n = S.shape[0]
+    rng = np.random.default_rng(8)
+    grid = np.concatenate([synth.random_quaternions(rng, 5), q0])
+    ctx = context_with(torch_cuda, u, ref_node_sig(u), 10, img)
+    apt.aptidx_build_lut(ctx.handle, 0, grid)
+    qa = np.empty((n, 4))
+    qb = np.empty((n, 4))
+    la = np.empty(n, np.float32)
+    lb = np.empty(n, np.float32)
+    apt.aptidx_refine(ctx.handle, 0, S, q0, 20, qa, la)
+    apt.aptidx_refine(ctx.handle, 0, S, None, 20, qb, lb, best=np.arange(5, 5 + n, dtype=np.int32))
+    assert np.array_equal(qa, qb) and np.array_equal(la, lb)
+    with pytest.raises(apt.AptidxError):
+        apt.aptidx_refine(ctx.handle, 0, S, None, 20, qb, lb, best=np.full(n, grid.shape[0], np.int32))
+    ctx.close()
