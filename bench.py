@@ -228,9 +228,8 @@ def run_gb300(args):
     import paper_2009_00735_gb300 as apt
     from paper_2009_00735_gb300 import build as B
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2009_00735_gb300 import ranks
+    rank, world, local = ranks.rank_info()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -290,9 +289,7 @@ def run_gb300(args):
     def signatures_only(path):
         apt.aptidx_compute_signatures(h, code[path], 0, S, None, None)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     def timed(fn, path, clocks=False):
         for _ in range(args.warmup):
@@ -317,10 +314,7 @@ def run_gb300(args):
         prof, launches = apt.aptidx_get_profile(h)
         apt.aptidx_set_profiling(h, False)
         apt.aptidx_sync(h)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = ranks.max_over_ranks(ms, device="cuda")
         return ms, prof, launches, clk
 
     # the timed step: the whole hot path (a1-a7)
@@ -388,11 +382,7 @@ def run_gb300(args):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        dt = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = ranks.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
         e2e = {"value": world * nroi * nv / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(w.xyz.nbytes + w.centres.nbytes + w.radii.nbytes),
                "d2h_bytes_per_step": int(nroi * nv * 4 + nroi * 4 * 8),
