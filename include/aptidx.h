@@ -123,7 +123,7 @@ int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem);
 int aptidx_set_binning(aptidx_ctx* ctx, int m, int32_t k_lo, int32_t k_hi, int flags);
 
 /* The ROI list (Section 2.4: ROIs on a grid or randomly placed).
- * centres: nroi x 3 FP64 nm; radii: nroi FP64 nm (> 0); band_lo/band_hi:
+ * centres: nroi x 3 FP64 nm; radii: nroi FP64 nm in [1e-6, 1e6]; band_lo/band_hi:
  * per-ROI signature bands (NULL: the default band of aptidx_set_binning);
  * type_mask: bit t selects atoms of type t (0xFFFFFFFF: all).  All arrays
  * live in `mem`.  Requires positions, directions and binning.  Counts the

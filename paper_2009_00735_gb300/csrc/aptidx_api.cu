@@ -422,7 +422,8 @@ int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii,
         for (int d = 0; d < 3; ++d)
             if (!isfinite(hc[3 * r + d])) return set_error(c, APTIDX_E_INVALID_ARG, "centre %lld not finite", (long long)r);
         const double R = hr[r];
-        if (!(R > 0.0) || !isfinite(R)) return set_error(c, APTIDX_E_INVALID_ARG, "radius %lld must be > 0", (long long)r);
+        if (!(R >= 1e-6 && R <= 1e6))
+            return set_error(c, APTIDX_E_INVALID_ARG, "radius %lld must lie in [1e-6, 1e6] nm", (long long)r);
         scale[r] = (float)((double)(half - 1) / R);
         int32_t lo = band_lo ? hlo[r] : c->k_lo, hi = band_lo ? hhi[r] : c->k_hi;
         if (lo < 0 || hi < lo || hi > half)

@@ -14,6 +14,10 @@ __host__ __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T>
 __host__ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
 // -----------------------------------------------------------------------------
 // Eq. 1, the bin of a projected atom.  With dR = R / (2^(m-1) - 1) (Fig. 2
 // caption) Eq. 1 is b = floor(2^(m-1) + s (2^(m-1) - 1) / R).  The library
@@ -54,31 +58,47 @@ __device__ __forceinline__ float u23_to_float(uint32_t c) {
 // One atom into the histograms of a 64-direction tile: lane l owns
 // directions 2l (low 16 bits) and 2l + 1 (high 16 bits) of the word
 // H[b * 32 + l].  The word of a lane lies in bank l for every bin b, so the
-// 32 atomics of one warp instruction never share a bank.
-__device__ __forceinline__ void hist_add_atom(uint32_t* H, int lane, float4 a, float4 d0, float4 d1,
-                                              float scale, float magic, int nbm1) {
+// 32 atomics of one warp instruction never share a bank.  `hbase` is the
+// shared address of H plus 4 * lane.
+//   kMasked: the bin is masked to m bits (memory-safe for any input).
+//   otherwise: the inputs are known to give bins in range (the library's own
+//   gather and validated directions and radii), and the word address is one
+//   multiply-add of the fma result's bit pattern 0x4B000000 + b.
+template <bool kMasked>
+__device__ __forceinline__ void hist_add_atom(uint32_t hbase, float4 a, float4 d0, float4 d1, float scale,
+                                              float magic, int nbm1) {
     const float s0 = project_f32(d0.x, d0.y, d0.z, a);
     const float s1 = project_f32(d1.x, d1.y, d1.z, a);
-    const uint32_t b0 = bin_of_valid(s0, scale, magic, (uint32_t)nbm1);
-    const uint32_t b1 = bin_of_valid(s1, scale, magic, (uint32_t)nbm1);
-    atomicAdd(&H[(b0 << 5) + lane], 1u);
-    atomicAdd(&H[(b1 << 5) + lane], 0x10000u);
+    const uint32_t t0 = __float_as_uint(__fmaf_rd(s0, scale, magic));
+    const uint32_t t1 = __float_as_uint(__fmaf_rd(s1, scale, magic));
+    uint32_t w0, w1;
+    if (kMasked) {
+        w0 = hbase + ((t0 & (uint32_t)nbm1) << 7);
+        w1 = hbase + ((t1 & (uint32_t)nbm1) << 7);
+    } else {
+        // (t - 0x4B000000) * 128 + hbase, in wrapping 32-bit arithmetic
+        w0 = t0 * 128u + (hbase - 0x80000000u);
+        w1 = t1 * 128u + (hbase - 0x80000000u);
+    }
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(w0), "r"(1u) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(w1), "r"(0x10000u) : "memory");
 }
 
 // Histograms of one 64-direction tile over `cn` staged atoms; warp w takes
 // atoms w, w + W, w + 2W, ...
-template <int W>
+template <int W, bool kMasked>
 __device__ __forceinline__ void hist_tile(uint32_t* H, const float4* A, int cn, int warp, int lane, float4 d0,
                                           float4 d1, float scale, float magic, int nbm1) {
+    const uint32_t hbase = smem_u32(H) + 4u * (uint32_t)lane;
     int j = warp;
     for (; j + 3 * W < cn; j += 4 * W) {
         const float4 a0 = A[j], a1 = A[j + W], a2 = A[j + 2 * W], a3 = A[j + 3 * W];
-        hist_add_atom(H, lane, a0, d0, d1, scale, magic, nbm1);
-        hist_add_atom(H, lane, a1, d0, d1, scale, magic, nbm1);
-        hist_add_atom(H, lane, a2, d0, d1, scale, magic, nbm1);
-        hist_add_atom(H, lane, a3, d0, d1, scale, magic, nbm1);
+        hist_add_atom<kMasked>(hbase, a0, d0, d1, scale, magic, nbm1);
+        hist_add_atom<kMasked>(hbase, a1, d0, d1, scale, magic, nbm1);
+        hist_add_atom<kMasked>(hbase, a2, d0, d1, scale, magic, nbm1);
+        hist_add_atom<kMasked>(hbase, a3, d0, d1, scale, magic, nbm1);
     }
-    for (; j < cn; j += W) hist_add_atom(H, lane, A[j], d0, d1, scale, magic, nbm1);
+    for (; j < cn; j += W) hist_add_atom<kMasked>(hbase, A[j], d0, d1, scale, magic, nbm1);
 }
 
 // Debug export of a tile's histograms: h_out[v * 2^m + b] for v < nv.
@@ -109,10 +129,6 @@ __device__ __forceinline__ void raise_status(int* status, int bit) {
 // -----------------------------------------------------------------------------
 // shared-memory addresses, mbarriers and bulk copies (inline PTX)
 // -----------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }

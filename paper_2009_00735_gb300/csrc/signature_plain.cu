@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
             for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
                 const int cn = min(p.atom_cap, nw - c0);
                 if (!one_chunk && !stage_atoms(A, p.atoms + abase + c0, cn, bar, phase, p.status, flag)) return;
-                hist_tile<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
+                hist_tile<kWarps, true>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
                 if (!one_chunk) __syncthreads();
             }
             __syncthreads();

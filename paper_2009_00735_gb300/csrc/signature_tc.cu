@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     failed = true;
                     break;
                 }
-                hist_tile<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
+                hist_tile<kWarps, false>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
                 if (!one_chunk) __syncthreads();
             }
             if (failed) break;
@@ -238,11 +238,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 if (warp >= kIssuers) {
                     for (int r0 = q * rows_q + (warp - kIssuers) * 4; r0 < (q + 1) * rows_q;
                          r0 += (kWarps - kIssuers) * 4) {
-                        const int k = r0 + (lane >> 3), c = lane & 7;
+                        const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
                         uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
-                        const uint4 x = row[c];
+                        uint4 x;
+                        if (sw) x = row[c];          // rows with k & 7 == 0 stay in place
                         __syncwarp();
-                        row[c ^ (k & 7)] = x;
+                        if (sw) row[c ^ sw] = x;
                     }
                 }
                 fence_proxy_async_smem();
