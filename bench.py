@@ -281,13 +281,16 @@ def run_gb300(args):
     rloss = torch.empty(nroi, dtype=torch.float32, device="cuda")
     iters = 20
 
-    def full_step(path):
-        apt.aptidx_compute_signatures(h, code[path], apt.APTIDX_NORMALISE_MAX, S, None, None)
+    tuned = apt.APTIDX_AUTOTUNE | apt.APTIDX_GRAPH   # launch configuration by the autotuner, graph replay
+
+    def full_step(path, flags=tuned):
+        apt.aptidx_compute_signatures(h, code[path], apt.APTIDX_NORMALISE_MAX | flags, S, None, None)
         apt.aptidx_match(h, 0, S, best, score)
         apt.aptidx_refine(h, 0, S, None, iters, q_out, rloss, best=best)
 
     def signatures_only(path):
-        apt.aptidx_compute_signatures(h, code[path], 0, S, None, None)
+        # no graph: the profile then separates gather, order and signature kernel
+        apt.aptidx_compute_signatures(h, code[path], apt.APTIDX_AUTOTUNE, S, None, None)
 
     barrier = ranks.barrier
 
@@ -320,6 +323,8 @@ def run_gb300(args):
     # the timed step: the whole hot path (a1-a7)
     ms, prof, launches, clk = timed(full_step, headline, clocks=True)
     value = world * nroi * nv / (ms / 1e3)
+    # the same step without graph replay, for the per-phase breakdown
+    _, prof, _, _ = timed(lambda p: full_step(p, apt.APTIDX_AUTOTUNE), headline)
     mis = cubic_disorientation_deg(q_out.cpu().numpy(), np.broadcast_to(w.truth["quat"], (nroi, 4)))
     mis_coarse = cubic_disorientation_deg(grid[best.cpu().numpy()], np.broadcast_to(w.truth["quat"], (nroi, 4)))
     per_phase = {k: (v[0] / max(v[1], 1)) for k, v in prof.items() if v[1] > 0}
@@ -328,9 +333,11 @@ def run_gb300(args):
     per_path = {}
     for p in paths:
         pms, pprof, _, _ = timed(signatures_only, p)
+        tpi, iss = apt.aptidx_get_tuning(h, code[p])
         per_path[p] = {"ms_per_step": pms, "value": world * nroi * nv / (pms / 1e3),
                        "signature_kernel_ms": pprof["signature"][0] / max(pprof["signature"][1], 1),
-                       "gather_ms": pprof["gather"][0] / max(pprof["gather"][1], 1)}
+                       "gather_ms": pprof["gather"][0] / max(pprof["gather"][1], 1),
+                       "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
 
     # roofline of the dominant kernel (the signature kernel of the headline path)
     sig_ms = prof["signature"][0] / max(prof["signature"][1], 1)

@@ -73,6 +73,8 @@ typedef struct aptidx_ctx aptidx_ctx;
 
 /* flags of aptidx_compute_signatures */
 #define APTIDX_NORMALISE_MAX   1u  /* divide each ROI's signature by its largest value */
+#define APTIDX_AUTOTUNE        2u  /* pick the launch configuration by timing candidates (once per shape) */
+#define APTIDX_GRAPH           4u  /* capture the call's launches in a CUDA graph once, replay afterwards */
 
 /* limits */
 #define APTIDX_MAX_ATOMS_PER_ROI 65535   /* u16 histogram counts */
@@ -138,8 +140,14 @@ int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii,
 /* Signatures of every ROI: gather and centre the ROI atoms (FP64
  * membership), project them on every direction, histogram them (Eq. 1),
  * take the band of the amplitude spectrum and keep its maximum (Section
- * 2.2).  path: APTIDX_PATH_PLAIN_FP32 or APTIDX_PATH_TC_FP16.  flags:
- * APTIDX_NORMALISE_MAX or 0.
+ * 2.2).  path: APTIDX_PATH_PLAIN_FP32 or APTIDX_PATH_TC_FP16.  flags: any of
+ * APTIDX_NORMALISE_MAX; APTIDX_AUTOTUNE (the first call for a new shape --
+ * bins, band width, mean ROI size, directions, device -- times candidate
+ * launch configurations on the first 8 ROIs per SM and keeps the fastest;
+ * with the environment variable APTIDX_TUNE_CACHE naming a file, choices
+ * persist across processes); APTIDX_GRAPH (the launches of the call are
+ * captured in a CUDA graph on first use for these output pointers and sizes
+ * and replayed on later calls; input changes discard the graphs).
  * Outputs (in `mem`; NULL to skip): S nroi x nv FP32; argk nroi x nv u16 (the
  * lowest frequency bin attaining the maximum; not written when normalising
  * is the only change); n_atoms nroi int32 (N_w per ROI).
@@ -216,6 +224,10 @@ int aptidx_refine(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q
                   int64_t nroi, int32_t iters, double* q_out, float* loss, int mem);
 
 /* ---- capabilities and profiling ------------------------------------------- */
+
+/* The launch configuration the next call on `path` uses: 64-direction tiles
+ * per work item and, on the tensor-core path, MMA issuer warps (else 0). */
+int aptidx_get_tuning(aptidx_ctx* ctx, int path, int32_t* tiles_per_item, int32_t* issuers);
 
 /* 1 if `path` can run on the context's device, else 0. */
 int aptidx_path_supported(aptidx_ctx* ctx, int path);

@@ -26,7 +26,7 @@ __all__ = [
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
-    "APTIDX_NORMALISE_MAX",
+    "APTIDX_NORMALISE_MAX", "APTIDX_AUTOTUNE", "APTIDX_GRAPH", "aptidx_get_tuning",
 ]
 
 APTIDX_OK = 0
@@ -41,6 +41,8 @@ APTIDX_MEM_DEVICE = 1
 APTIDX_PATH_PLAIN_FP32 = 0
 APTIDX_PATH_TC_FP16 = 1
 APTIDX_NORMALISE_MAX = 1
+APTIDX_AUTOTUNE = 2
+APTIDX_GRAPH = 4
 
 _ERR_NAMES = {1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "OVERFLOW", 6: "STATE"}
 
@@ -75,6 +77,7 @@ _SIGS = {
     "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
+    "aptidx_get_tuning": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "aptidx_set_profiling": (C.c_int, [_vp, C.c_int]),
     "aptidx_get_profile": (C.c_int, [_vp, _vp, _vp, _vp]),
     "aptidx_signatures_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, C.c_int, _i32, _i32, _vp, _vp, _vp]),
@@ -316,6 +319,14 @@ def aptidx_refine(ctx, cand: int, S, q0, iters: int, q_out, loss=None, best=None
 
 def aptidx_path_supported(ctx, path: int) -> bool:
     return bool(load().aptidx_path_supported(ctx, path))
+
+
+def aptidx_get_tuning(ctx, path: int):
+    """(tiles per work item, MMA issuer warps) the next call on `path` uses."""
+    t = np.zeros(1, np.int32)
+    i = np.zeros(1, np.int32)
+    _check(ctx, load().aptidx_get_tuning(ctx, path, t.ctypes.data, i.ctypes.data))
+    return int(t[0]), int(i[0])
 
 
 def aptidx_set_profiling(ctx, enable: bool):

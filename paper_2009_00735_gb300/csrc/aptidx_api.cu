@@ -123,7 +123,10 @@ static int read_status(Ctx* c) {
     return APTIDX_OK;
 }
 
+static void clear_graphs(Ctx* c);
+
 static void free_rois(Ctx* c) {
+    clear_graphs(c);
     free_ptr(c->d_centres);
     free_ptr(c->d_radii);
     free_ptr(c->d_scale);
@@ -197,12 +200,145 @@ static int build_grid(Ctx* c, double h) {
     return rc;
 }
 
+static void clear_graphs(Ctx* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
 // gather count + offsets + fill (step a1), queued on the stream
 static int run_gather(Ctx* c) {
     cudaError_t e = launch_gather_count(c);
     if (e == cudaSuccess) e = launch_gather_fill(c);
     if (e != cudaSuccess) return cuda_check(c, e, "ROI gather");
     return APTIDX_OK;
+}
+
+// The signature sequence of one compute call (a1-a5 and the optional
+// normalisation), queued on the stream.
+static int launch_sequence(Ctx* c, int path, unsigned flags, float* dS, uint16_t* dA) {
+    int rc;
+    prof_begin(c, APTIDX_PHASE_GATHER);
+    if ((rc = run_gather(c))) return rc;
+    prof_end(c, APTIDX_PHASE_GATHER, 6);
+    prof_begin(c, APTIDX_PHASE_ORDER);
+    cudaError_t e = launch_roi_order(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "ROI order");
+    prof_end(c, APTIDX_PHASE_ORDER, 3);
+    prof_begin(c, APTIDX_PHASE_SIGNATURE);
+    if (path == APTIDX_PATH_PLAIN_FP32) {
+        e = launch_signatures_plain(c, dS, dA, nullptr, -1, 0);
+    } else {
+        e = launch_signatures_tc(c, dS, dA, nullptr, -1);
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "signature kernel");
+    prof_end(c, APTIDX_PHASE_SIGNATURE, path == APTIDX_PATH_PLAIN_FP32 ? 1 : 1);
+    if (flags & APTIDX_NORMALISE_MAX) {
+        prof_begin(c, APTIDX_PHASE_NORMALISE);
+        e = launch_normalise(c, dS);
+        if (e != cudaSuccess) return cuda_check(c, e, "normalise");
+        prof_end(c, APTIDX_PHASE_NORMALISE, 1);
+    }
+    return APTIDX_OK;
+}
+
+// ---- autotuner ---------------------------------------------------------------
+// Launch configuration per (path, bins, frequency groups of the band, mean
+// ROI size, directions, device): tiles of 64 directions per work item and,
+// on the tensor-core path, the number of MMA issuer warps.  Candidates are
+// timed with CUDA events on the first ranks of the ROI order (8 per SM) and
+// the fastest is kept for the context, and in the file named by the
+// environment variable APTIDX_TUNE_CACHE when it is set.
+
+static std::string tune_key(Ctx* c, int path) {
+    char buf[160];
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, c->device);
+    const double mean = c->nroi > 0 ? (double)c->atoms_total / (double)c->nroi : 0.0;
+    const int abin = mean > 1.0 ? (int)lround(2.0 * log2(mean)) : 0;
+    const int vbin = (int)lround(2.0 * log2((double)std::max(c->nv, 1)));
+    const int groups = (c->band_max - c->band_min) / 4 + 1;
+    snprintf(buf, sizeof(buf), "%s/%d|p%d|m%d|g%d|a%d|v%d", prop.name, prop.multiProcessorCount, path, c->m, groups,
+             abin, vbin);
+    for (char* q = buf; *q; ++q)
+        if (*q == ' ') *q = '_';
+    return buf;
+}
+
+static void tune_load(Ctx* c) {
+    if (c->tune_loaded) return;
+    c->tune_loaded = true;
+    const char* path = getenv("APTIDX_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[200];
+    int tpi, iss;
+    float ms;
+    while (fscanf(f, "%199s %d %d %f", key, &tpi, &iss, &ms) == 4) c->tune_cache[key] = {tpi, iss, ms};
+    fclose(f);
+}
+
+static void tune_save(Ctx* c) {
+    const char* path = getenv("APTIDX_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (auto& kv : c->tune_cache) fprintf(f, "%s %d %d %.4f\n", kv.first.c_str(), kv.second.tpi, kv.second.iss, kv.second.ms);
+    fclose(f);
+}
+
+static int autotune(Ctx* c, int path, float* dS, uint16_t* dA) {
+    tune_load(c);
+    const int pi = path == APTIDX_PATH_TC_FP16 ? 1 : 0;
+    const std::string key = tune_key(c, path);
+    auto it = c->tune_cache.find(key);
+    if (it != c->tune_cache.end()) {
+        c->tune_tpi[pi] = it->second.tpi;
+        if (pi) c->tune_iss = it->second.iss;
+        return APTIDX_OK;
+    }
+    int rc;
+    if ((rc = run_gather(c))) return rc;
+    cudaError_t e = launch_roi_order(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "ROI order");
+    const bool prof = c->prof;
+    c->prof = false;
+    c->rank_limit = std::min<int64_t>(c->nroi, (int64_t)8 * c->sm_count);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int tpis[] = {4, 8, 16, 32};
+    const int isss[] = {2, 4};
+    Ctx::TuneCfg best{c->tune_tpi[pi], c->tune_iss, 1e30f};
+    for (int tpi : tpis) {
+        for (int iss : isss) {
+            if (!pi && iss != 4) continue;
+            c->tune_tpi[pi] = tpi;
+            if (pi) c->tune_iss = iss;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first launch sets attributes
+                e = cudaEventRecord(e0, c->stream);
+                if (e == cudaSuccess)
+                    e = pi ? launch_signatures_tc(c, dS, dA, nullptr, -1) : launch_signatures_plain(c, dS, dA, nullptr, -1, 0);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e != cudaSuccess) break;
+            if (ms < best.ms) best = {tpi, iss, ms};
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->rank_limit = 0;
+    c->prof = prof;
+    if (e != cudaSuccess) return cuda_check(c, e, "autotune");
+    c->tune_tpi[pi] = best.tpi;
+    if (pi) c->tune_iss = best.iss;
+    c->tune_cache[key] = best;
+    tune_save(c);
+    return read_status(c);
 }
 
 }  // namespace aptidx
@@ -258,6 +394,7 @@ int aptidx_destroy(aptidx_ctx* ctx) {
     cudaStreamSynchronize(c->stream);
     free_rois(c);
     free_grid(c);
+    clear_graphs(c);
     free_ptr(c->d_S);
     free_ptr(c->d_argk);
     free_ptr(c->d_pos);
@@ -268,6 +405,7 @@ int aptidx_destroy(aptidx_ctx* ctx) {
     c->d_twb = nullptr;
     free_ptr(c->d_status);
     free_ptr(c->d_counter);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_ptr(c->d_sort_hist);
     for (auto& pr : c->ev_pending) {
         cudaEventDestroy(pr.a);
@@ -312,6 +450,7 @@ int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const ui
         if (!isfinite(hx[i])) return set_error(c, APTIDX_E_INVALID_ARG, "positions: non-finite coordinate at %zu", i / 3);
     free_rois(c);
     free_grid(c);
+    clear_graphs(c);
     free_ptr(c->d_pos);
     free_ptr(c->d_types);
     c->n_atoms = 0;
@@ -358,6 +497,7 @@ int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem) 
         d4[v] = make_float4(x, y, z, 0.f);
     }
     free_ptr(c->d_dirs);
+    clear_graphs(c);
     c->nv = c->nv_pad = 0;
     if ((rc = dev_alloc(c, (void**)&c->d_dirs, (size_t)nv_pad * sizeof(float4)))) return rc;
     APTIDX_CUDA(c, cudaMemcpyAsync(c->d_dirs, d4.data(), (size_t)nv_pad * sizeof(float4), cudaMemcpyHostToDevice,
@@ -386,6 +526,7 @@ int aptidx_set_binning(aptidx_ctx* ctx, int m, int32_t k_lo, int32_t k_hi, int f
         c->tw_m = m;
     }
     if (c->m != m && c->nroi > 0) free_rois(c);   // per-ROI scales depend on m
+    clear_graphs(c);
     c->m = m;
     c->k_lo = k_lo;
     c->k_hi = k_hi;
@@ -499,7 +640,8 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
     if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "compute_signatures: set ROIs first");
     if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
         return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
-    if (flags & ~APTIDX_NORMALISE_MAX) return set_error(c, APTIDX_E_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (flags & ~(APTIDX_NORMALISE_MAX | APTIDX_AUTOTUNE | APTIDX_GRAPH))
+        return set_error(c, APTIDX_E_INVALID_ARG, "unknown flags 0x%x", flags);
     const int64_t nS = c->nroi * (int64_t)c->nv;
     float* dS = S;
     uint16_t* dA = argk;
@@ -516,26 +658,45 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
         dA = argk ? c->d_argk : nullptr;
     }
     if (path == APTIDX_PATH_TC_FP16 && (rc = prepare_tc(c))) return rc;
-    prof_begin(c, APTIDX_PHASE_GATHER);
-    if ((rc = run_gather(c))) return rc;
-    prof_end(c, APTIDX_PHASE_GATHER, 6);
-    prof_begin(c, APTIDX_PHASE_ORDER);
-    cudaError_t e = launch_roi_order(c);
-    if (e != cudaSuccess) return cuda_check(c, e, "ROI order");
-    prof_end(c, APTIDX_PHASE_ORDER, 3);
-    prof_begin(c, APTIDX_PHASE_SIGNATURE);
-    if (path == APTIDX_PATH_PLAIN_FP32) {
-        e = launch_signatures_plain(c, dS, dA, nullptr, -1, 0);
-    } else {
-        e = launch_signatures_tc(c, dS, dA, nullptr, -1);
-    }
-    if (e != cudaSuccess) return cuda_check(c, e, "signature kernel");
-    prof_end(c, APTIDX_PHASE_SIGNATURE, 1);
-    if (flags & APTIDX_NORMALISE_MAX) {
-        prof_begin(c, APTIDX_PHASE_NORMALISE);
-        e = launch_normalise(c, dS);
-        if (e != cudaSuccess) return cuda_check(c, e, "normalise");
-        prof_end(c, APTIDX_PHASE_NORMALISE, 1);
+    if ((flags & APTIDX_AUTOTUNE) && (rc = autotune(c, path, dS, dA))) return rc;
+    if (flags & APTIDX_GRAPH) {
+        // capture the sequence once per (arguments, configuration), replay after
+        char kb[256];
+        snprintf(kb, sizeof(kb), "%d|%u|%p|%p|%lld|%d|%d|%d|%d", path, flags & APTIDX_NORMALISE_MAX, (void*)dS, (void*)dA,
+                 (long long)c->nroi, c->nv, c->m, c->tune_tpi[path == APTIDX_PATH_TC_FP16], c->tune_iss);
+        auto it = c->graphs.find(kb);
+        if (it == c->graphs.end()) {
+            // capture on a private stream (capture is not possible on the
+            // legacy default stream); the graph then runs on the caller's stream
+            if (!c->cap_stream) APTIDX_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            const bool prof = c->prof;
+            c->prof = false;
+            const int64_t l0 = c->launches;
+            cudaStream_t user = c->stream;
+            cudaGraph_t g = nullptr;
+            APTIDX_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            c->stream = c->cap_stream;
+            rc = launch_sequence(c, path, flags, dS, dA);
+            c->stream = user;
+            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            c->prof = prof;
+            c->launches = l0;
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_check(c, e, "graph capture");
+            cudaGraphExec_t x = nullptr;
+            e = cudaGraphInstantiate(&x, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_check(c, e, "graph instantiate");
+            it = c->graphs.emplace(kb, x).first;
+        }
+        prof_begin(c, APTIDX_PHASE_SIGNATURE);
+        APTIDX_CUDA(c, cudaGraphLaunch(it->second, c->stream));
+        prof_end(c, APTIDX_PHASE_SIGNATURE, (path == APTIDX_PATH_TC_FP16 ? 11 : 10) + ((flags & APTIDX_NORMALISE_MAX) ? 1 : 0));
+    } else if ((rc = launch_sequence(c, path, flags, dS, dA))) {
+        return rc;
     }
     if (mem == APTIDX_MEM_HOST) {
         if (S) APTIDX_CUDA(c, cudaMemcpyAsync(S, dS, (size_t)nS * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -557,6 +718,15 @@ int aptidx_path_supported(aptidx_ctx* ctx, int path) {
     if (path == APTIDX_PATH_PLAIN_FP32) return 1;
     if (path == APTIDX_PATH_TC_FP16) return tc_supported(&ctx->c) ? 1 : 0;
     return 0;
+}
+
+int aptidx_get_tuning(aptidx_ctx* ctx, int path, int32_t* tiles_per_item, int32_t* issuers) {
+    CTX_OR_FAIL(ctx);
+    if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
+        return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
+    if (tiles_per_item) *tiles_per_item = c->tune_tpi[path == APTIDX_PATH_TC_FP16];
+    if (issuers) *issuers = path == APTIDX_PATH_TC_FP16 ? c->tune_iss : 0;
+    return APTIDX_OK;
 }
 
 int aptidx_set_profiling(aptidx_ctx* ctx, int enable) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -104,6 +105,23 @@ struct Ctx {
 
     // status word
     int* d_status = nullptr;
+
+    // launch configuration (tiles per work item per path, MMA issuer warps),
+    // set by the autotuner; rank_limit > 0 restricts a launch to the first
+    // ranks of the ROI order (tuning runs)
+    int tune_tpi[2] = {16, 16};
+    int tune_iss = 4;
+    int64_t rank_limit = 0;
+    struct TuneCfg {
+        int tpi, iss;
+        float ms;
+    };
+    std::map<std::string, TuneCfg> tune_cache;
+    bool tune_loaded = false;
+
+    // CUDA graphs of compute_signatures calls, keyed by their arguments
+    std::map<std::string, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;
 
     Reference ref[kMaxCandidates];
 

@@ -291,9 +291,10 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     p.dirs = c->d_dirs;
     p.nv = c->nv;
     p.tiles_per_roi = c->nv_pad / kDirs;
-    p.tiles_per_item = min(16, p.tiles_per_roi);
+    p.tiles_per_item = min(max(c->tune_tpi[0], 1), p.tiles_per_roi);
     p.items_per_roi = (p.tiles_per_roi + p.tiles_per_item - 1) / p.tiles_per_item;
-    const int64_t nroi_eff = hist_out ? 1 : c->nroi;
+    const int64_t nroi_lim = c->rank_limit > 0 ? tmin<int64_t>(c->nroi, c->rank_limit) : c->nroi;
+    const int64_t nroi_eff = hist_out ? 1 : nroi_lim;
     p.n_items = nroi_eff * p.items_per_roi;
     p.scale = c->d_scale;
     p.band = c->d_band;
@@ -308,7 +309,7 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     p.atom_cap = cap;
     p.n_big = c->d_counter + 1;
     p.rank_mode = hist_out ? kRanksAll : rank_mode;
-    p.nroi = c->nroi;
+    p.nroi = nroi_lim;
     if ((e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);

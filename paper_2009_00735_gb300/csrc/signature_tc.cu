@@ -31,7 +31,7 @@ constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDirs = kTileDirs;     // M = 64
 constexpr int kBtBytes = 64 * 1024;  // shared-memory budget of the B operand
-constexpr int kIssuers = 4;          // warps issuing MMAs, one TMEM partial accumulator each
+constexpr int kIssuers = 4;          // at most this many warps issue MMAs, one TMEM partial accumulator each
 
 struct TcParams {
     const float4* atoms;
@@ -60,6 +60,7 @@ struct TcParams {
     int32_t* counter;
     int* status;
     int atom_cap;
+    int n_iss;              // MMA issuer warps (1 .. kIssuers)
 };
 
 // ---- tcgen05 / descriptor helpers -------------------------------------------
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
             // own partial accumulator while the others permute chunk q + 1.
             // A single tcgen05.mma costs an issuing warp ~75 cycles whatever
             // its N; four issuers overlap that cost.
-            const int n_iss = nbatch == 1 ? kIssuers : 1;
+            const int n_iss = nbatch == 1 ? p.n_iss : 1;
             const int rows_q = NB / 4;
             const int kk_q = NB / 64;   // K steps of 16 bins per chunk
             const uint32_t sbo_b = (uint32_t)KB * 1024u;
@@ -235,9 +236,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 *flag = ok;
             }
             for (int q = 0; q < 4; ++q) {
-                if (warp >= kIssuers) {
-                    for (int r0 = q * rows_q + (warp - kIssuers) * 4; r0 < (q + 1) * rows_q;
-                         r0 += (kWarps - kIssuers) * 4) {
+                if (warp >= p.n_iss) {
+                    for (int r0 = q * rows_q + (warp - p.n_iss) * 4; r0 < (q + 1) * rows_q;
+                         r0 += (kWarps - p.n_iss) * 4) {
                         const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
                         uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
                         uint4 x;
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 float best = -1.f;
                 int bk = klo;
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-                const int n_iss = nbatch == 1 ? kIssuers : 1;
+                const int n_iss = nbatch == 1 ? p.n_iss : 1;
                 const uint32_t cols_b = (uint32_t)(16 * p.gb);
                 for (int b = 0; b < nbatch; ++b) {
                     const int g0 = fg0 + b * p.gb;
@@ -488,9 +489,9 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     p.dirs = c->d_dirs;
     p.nv = c->nv;
     p.tiles_per_roi = c->nv_pad / kDirs;
-    p.tiles_per_item = std::min(16, p.tiles_per_roi);
+    p.tiles_per_item = std::min(std::max(c->tune_tpi[1], 1), p.tiles_per_roi);
     p.items_per_roi = (p.tiles_per_roi + p.tiles_per_item - 1) / p.tiles_per_item;
-    p.nroi = c->nroi;
+    p.nroi = c->rank_limit > 0 ? std::min<int64_t>(c->nroi, c->rank_limit) : c->nroi;
     p.scale = c->d_scale;
     p.band = c->d_band;
     p.m = c->m;
@@ -506,11 +507,12 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     p.counter = c->d_counter + 2;
     p.status = c->d_status;
     p.atom_cap = cap;
+    p.n_iss = std::min(std::max(c->tune_iss, 1), kIssuers);
     if ((e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_tc, kThreads, smem);
     per_sm = std::max(1, std::min(per_sm, (int)(512 / p.tmem_cols)));
-    const int64_t items = (hist_out ? 1 : c->nroi) * (int64_t)p.items_per_roi;
+    const int64_t items = (hist_out ? 1 : p.nroi) * (int64_t)p.items_per_roi;
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, items);
     if (grid < 1) return cudaSuccess;
     k_sig_tc<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);

@@ -151,3 +151,33 @@ def test_tc_full_size_single_crystal_sampled(tc, single_crystal):
     Sp, _, _ = gpu_signatures(tc, ctx, nroi, nv)
     assert roi_error(S, Sp).max() <= TOL_TC
     ctx.close()
+
+
+def test_autotune_and_graph_replay(tc, tiny, tmp_path, monkeypatch):
+    """APTIDX_AUTOTUNE picks a launch configuration (and persists it in
+    APTIDX_TUNE_CACHE); APTIDX_GRAPH captures the call once and replays it.
+    Results agree with the plain launches of the same path; changing the ROI
+    set discards the graph."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("APTIDX_TUNE_CACHE", str(cache))
+    ctx, band, m, d = make_ctx(tc, tiny)
+    nroi, nv = tiny.centres.shape[0], d.shape[0]
+    for path in (apt.APTIDX_PATH_PLAIN_FP32, TC):
+        S_ref, _, _ = gpu_signatures(tc, ctx, nroi, nv, path=path)
+        flags = apt.APTIDX_AUTOTUNE | apt.APTIDX_GRAPH
+        S1, _, _ = gpu_signatures(tc, ctx, nroi, nv, path=path, flags=flags)
+        S2, _, _ = gpu_signatures(tc, ctx, nroi, nv, path=path, flags=flags)
+        assert np.array_equal(S1, S2)
+        assert roi_error(S1, S_ref).max() <= 1e-5
+        tpi, iss = apt.aptidx_get_tuning(ctx.handle, path)
+        assert tpi in (4, 8, 16, 32)
+        assert iss in ((2, 4) if path == TC else (0,))
+    assert cache.exists() and len(cache.read_text().splitlines()) == 2
+    # a new ROI set discards the captured graphs
+    apt.aptidx_set_rois(ctx.handle, tiny.centres[:5], tiny.radii[:5])
+    S3 = tc.empty((5, nv), dtype=tc.float32, device="cuda")
+    apt.aptidx_compute_signatures(ctx.handle, TC, apt.APTIDX_GRAPH, S3, None, None)
+    apt.aptidx_sync(ctx.handle)
+    So, _, _ = oracle.signatures(tiny.xyz, tiny.centres[:5], tiny.radii[:5], band[0], band[1], d, m)
+    assert roi_error(S3.cpu().numpy(), So).max() <= TOL_TC
+    ctx.close()
