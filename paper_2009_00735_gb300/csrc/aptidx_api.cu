@@ -250,7 +250,7 @@ static int launch_sequence(Ctx* c, int path, unsigned flags, float* dS, uint16_t
 // environment variable APTIDX_TUNE_CACHE when it is set.
 
 static std::string tune_key(Ctx* c, int path) {
-    char buf[160];
+    char buf[384];
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, c->device);
     const double mean = c->nroi > 0 ? (double)c->atoms_total / (double)c->nroi : 0.0;
@@ -967,9 +967,13 @@ int aptidx_build_lut(aptidx_ctx* ctx, int32_t cand, const double* quats, int64_t
     free_ptr(r.d_lut);
     free_ptr(r.d_quats);
     r.ng = 0;
+    r.ng_pad = 0;
     if ((rc = dev_alloc(c, (void**)&r.d_quats, (size_t)ng * 4 * sizeof(double)))) return rc;
     APTIDX_CUDA(c, cudaMemcpyAsync(r.d_quats, hq.data(), (size_t)ng * 4 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if ((rc = dev_alloc(c, (void**)&r.d_lut, (size_t)ng * r.n_hat * sizeof(int32_t)))) return rc;
+    r.ng_pad = (ng + 7) / 8 * 8;
+    r.lut_bytes = c->nv <= 65536 ? 2 : 4;
+    if ((rc = dev_alloc(c, &r.d_lut, (size_t)r.ng_pad * r.n_hat * r.lut_bytes))) return rc;
+    APTIDX_CUDA(c, cudaMemsetAsync(r.d_lut, 0, (size_t)r.ng_pad * r.n_hat * r.lut_bytes, c->stream));
     cudaError_t e = launch_build_lut(c, &r, r.d_quats, ng);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "look-up table");

@@ -106,13 +106,15 @@ constexpr int kLutThreads = 256;
 constexpr int kLutPer = 4;                       // queries per thread
 constexpr int kLutTile = 2048;                   // nodes per shared-memory tile
 
-// lut_t[k * ng + g] = argmax_p u_p . r with r = (float)(R(q_g) n_top[k]) (FP64
-// products summed left to right), the dot product by the FP32 contract
+// lut_t[k * ng_pad + g] = argmax_p u_p . r with r = (float)(R(q_g) n_top[k])
+// (FP64 products summed left to right), the dot product by the FP32 contract
 // fma(u_z, r_z, fma(u_y, r_y, u_x r_x)); ties resolve to the lowest index.
+// IdxT is uint16_t when every node index fits (nv <= 65536), else int32_t.
+template <typename IdxT>
 __global__ void __launch_bounds__(kLutThreads) k_build_lut(const float4* __restrict__ dirs, int32_t nv,
                                                            const int32_t* __restrict__ top, int32_t n_hat,
                                                            const double* __restrict__ quats, int64_t ng,
-                                                           int32_t* lut_t) {
+                                                           int64_t ng_pad, IdxT* lut_t) {
     __shared__ float4 tile[kLutTile];
     const int64_t nq = ng * n_hat;
     const int64_t q0 = (int64_t)blockIdx.x * kLutThreads * kLutPer;
@@ -160,46 +162,91 @@ __global__ void __launch_bounds__(kLutThreads) k_build_lut(const float4* __restr
         if (q < nq) {
             const int64_t g = q / n_hat;
             const int k = (int)(q % n_hat);
-            lut_t[(int64_t)k * ng + g] = bi[j];
+            lut_t[(int64_t)k * ng_pad + g] = (IdxT)bi[j];
         }
     }
 }
 
 // ---- Eq. 3 -----------------------------------------------------------------------
 
-constexpr int kMatchThreads = 512;
-
 // One CTA per ROI (persistent): the ROI's signature row in shared memory,
 // Delta(g) = sum_k (S[lut[k, g]] - ref[k])^2 accumulated in FP32 in k order,
-// argmin with ties to the lowest g.
-__global__ void __launch_bounds__(kMatchThreads) k_match(const float* __restrict__ S, int64_t nroi, int32_t nv,
-                                                         const int32_t* __restrict__ lut_t, int64_t ng,
-                                                         const float* __restrict__ top_val, int32_t n_hat,
-                                                         int32_t* best, float* score) {
+// argmin with ties to the lowest g.  The table streams from L2 once per ROI:
+// each thread reads 16 bytes of a table row per k (G = 16 / sizeof(IdxT)
+// consecutive orientations) and keeps four rows in flight.
+template <typename IdxT>
+__device__ __forceinline__ uint4 lut_load(const IdxT* p) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+template <typename IdxT>
+__device__ __forceinline__ void lut_accumulate(const uint4 w, const float* row, float rk, float* acc) {
+    if (sizeof(IdxT) == 2) {
+        const float d0 = row[w.x & 0xFFFFu] - rk, d1 = row[w.x >> 16] - rk;
+        const float d2 = row[w.y & 0xFFFFu] - rk, d3 = row[w.y >> 16] - rk;
+        const float d4 = row[w.z & 0xFFFFu] - rk, d5 = row[w.z >> 16] - rk;
+        const float d6 = row[w.w & 0xFFFFu] - rk, d7 = row[w.w >> 16] - rk;
+        acc[0] = fmaf(d0, d0, acc[0]);
+        acc[1] = fmaf(d1, d1, acc[1]);
+        acc[2] = fmaf(d2, d2, acc[2]);
+        acc[3] = fmaf(d3, d3, acc[3]);
+        acc[4] = fmaf(d4, d4, acc[4]);
+        acc[5] = fmaf(d5, d5, acc[5]);
+        acc[6] = fmaf(d6, d6, acc[6]);
+        acc[7] = fmaf(d7, d7, acc[7]);
+    } else {
+        const float d0 = row[w.x] - rk, d1 = row[w.y] - rk, d2 = row[w.z] - rk, d3 = row[w.w] - rk;
+        acc[0] = fmaf(d0, d0, acc[0]);
+        acc[1] = fmaf(d1, d1, acc[1]);
+        acc[2] = fmaf(d2, d2, acc[2]);
+        acc[3] = fmaf(d3, d3, acc[3]);
+    }
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, int64_t nroi, int32_t nv,
+                                                const IdxT* __restrict__ lut_t, int64_t ng, int64_t ng_pad,
+                                                const float* __restrict__ top_val, int32_t n_hat, int32_t* best,
+                                                float* score) {
+    constexpr int G = 16 / (int)sizeof(IdxT);
     extern __shared__ float sm[];
     float* row = sm;                     // nv
     float* ref = sm + nv;                // n_hat
-    __shared__ float red_v[kMatchThreads / 32];
-    __shared__ int32_t red_g[kMatchThreads / 32];
-    for (int i = threadIdx.x; i < n_hat; i += kMatchThreads) ref[i] = top_val[i];
+    __shared__ float red_v[32];
+    __shared__ int32_t red_g[32];
+    const int nwarps = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < n_hat; i += blockDim.x) ref[i] = top_val[i];
     for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
         __syncthreads();
         const float* src = S + r * (int64_t)nv;
-        for (int i = threadIdx.x; i < nv; i += kMatchThreads) row[i] = src[i];
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) row[i] = src[i];
         __syncthreads();
         float bv = INFINITY;
         int32_t bg = 0x7FFFFFFF;
-        for (int64_t g = threadIdx.x; g < ng; g += kMatchThreads) {
-            float acc = 0.f;
-            const int32_t* lp = lut_t + g;
-            for (int k = 0; k < n_hat; ++k) {
-                const float d = row[lp[(int64_t)k * ng]] - ref[k];
-                acc = fmaf(d, d, acc);
+        for (int64_t g0 = (int64_t)threadIdx.x * G; g0 < ng; g0 += (int64_t)blockDim.x * G) {
+            float acc[G];
+#pragma unroll
+            for (int e = 0; e < G; ++e) acc[e] = 0.f;
+            const IdxT* lp = lut_t + g0;
+            int k = 0;
+            for (; k + 4 <= n_hat; k += 4) {
+                uint4 w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = lut_load(lp + (int64_t)(k + j) * ng_pad);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) lut_accumulate<IdxT>(w[j], row, ref[k + j], acc);
             }
-            if (acc < bv) {
-                bv = acc;
-                bg = (int32_t)g;
-            }
+            for (; k < n_hat; ++k) lut_accumulate<IdxT>(lut_load(lp + (int64_t)k * ng_pad), row, ref[k], acc);
+#pragma unroll
+            for (int e = 0; e < G; ++e)
+                if (g0 + e < ng && acc[e] < bv) {
+                    bv = acc[e];
+                    bg = (int32_t)(g0 + e);
+                }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -215,7 +262,7 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const float* __restrict
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 1; w < kMatchThreads / 32; ++w)
+            for (int w = 1; w < nwarps; ++w)
                 if (red_v[w] < bv || (red_v[w] == bv && red_g[w] < bg)) {
                     bv = red_v[w];
                     bg = red_g[w];
@@ -271,9 +318,14 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
     if (want_j) {
         const float dfi = (1.f - tj) * (I10 - I00) + tj * (I11 - I01);
         const float dfj = (1.f - ti) * (I01 - I00) + ti * (I11 - I10);
+        // partial derivatives of (alpha, beta) in radians; the 2-ulp
+        // reciprocals are far inside the FP32 error of the sums they feed
         const float n2 = rho2 + cz * cz;
-        const float da0 = -cz * cx / (rho * n2), da1 = -cz * cy / (rho * n2), da2 = rho / n2;
-        const float db0 = -cy / rho2, db1 = cx / rho2;
+        const float inv_n2 = __fdividef(1.f, n2);
+        const float inv_rho2 = __fdividef(1.f, rho2);
+        const float t_a = -cz * __fdividef(inv_n2, rho);
+        const float da0 = t_a * cx, da1 = t_a * cy, da2 = rho * inv_n2;
+        const float db0 = -cy * inv_rho2, db1 = cx * inv_rho2;
         const float g0 = kRad2Deg * (dfi * da0 + dfj * db0);
         const float g1 = kRad2Deg * (dfi * da1 + dfj * db1);
         const float g2 = kRad2Deg * (dfi * da2);
@@ -285,6 +337,20 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
         t.J[2] = -(ax * uy - ay * ux);
     }
     return t;
+}
+
+// direction and signature reads stream past L1 so that the reference image
+// (181 x 360 floats) stays resident there for the bilinear gathers
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float ld_stream(const float* p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
 }
 
 // block sum of n FP32 partials per thread into FP64 totals (thread 0 holds them)
@@ -356,8 +422,8 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __rest
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         const float* srow = S + r * (int64_t)nv;
         for (int v = threadIdx.x; v < nv; v += kRefThreads) {
-            const float4 u = dirs[v];
-            const DirTerm t = dir_term(Rf, u.x, u.y, u.z, srow[v], img, kGrad);
+            const float4 u = ld_stream4(dirs + v);
+            const DirTerm t = dir_term(Rf, u.x, u.y, u.z, ld_stream(srow + v), img, kGrad);
             if (!t.ok) continue;
             acc[0] = fmaf(t.r, t.r, acc[0]);
             if (kGrad) {
@@ -428,8 +494,8 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restri
             for (int i = 0; i < 9; ++i) Rf[i] = Rs[i];
             float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // L, Jtr[3], JtJ[6]
             for (int v = threadIdx.x; v < nv; v += kRefThreads) {
-                const float4 u = dirs[v];
-                const DirTerm t = dir_term(Rf, u.x, u.y, u.z, srow[v], img, !last);
+                const float4 u = ld_stream4(dirs + v);
+                const DirTerm t = dir_term(Rf, u.x, u.y, u.z, ld_stream(srow + v), img, !last);
                 if (!t.ok) continue;
                 acc[0] = fmaf(t.r, t.r, acc[0]);
                 if (!last) {
@@ -486,13 +552,15 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restri
     }
 }
 
-// k-major table to g-major
-__global__ void k_lut_transpose(const int32_t* __restrict__ lut_t, int64_t ng, int32_t n_hat, int32_t* out) {
+// k-major table to g-major int32
+template <typename IdxT>
+__global__ void k_lut_transpose(const IdxT* __restrict__ lut_t, int64_t ng, int64_t ng_pad, int32_t n_hat,
+                                int32_t* out) {
     const int64_t n = ng * n_hat;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = i / n_hat;
         const int k = (int)(i % n_hat);
-        out[i] = lut_t[(int64_t)k * ng + g];
+        out[i] = (int32_t)lut_t[(int64_t)k * ng_pad + g];
     }
 }
 
@@ -500,7 +568,13 @@ __global__ void k_lut_transpose(const int32_t* __restrict__ lut_t, int64_t ng, i
 
 cudaError_t launch_lut_export(Ctx* c, Reference* r, int32_t* out) {
     const int64_t n = r->ng * r->n_hat;
-    k_lut_transpose<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, c->stream>>>(r->d_lut, r->ng, r->n_hat, out);
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
+    if (r->lut_bytes == 2)
+        k_lut_transpose<<<grid, 256, 0, c->stream>>>(static_cast<const uint16_t*>(r->d_lut), r->ng, r->ng_pad,
+                                                     r->n_hat, out);
+    else
+        k_lut_transpose<<<grid, 256, 0, c->stream>>>(static_cast<const int32_t*>(r->d_lut), r->ng, r->ng_pad,
+                                                     r->n_hat, out);
     return cudaGetLastError();
 }
 
@@ -521,22 +595,37 @@ cudaError_t launch_top_nodes(Ctx* c, Reference* r) {
 cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng) {
     const int64_t nq = ng * r->n_hat;
     const int64_t per = (int64_t)kLutThreads * kLutPer;
-    k_build_lut<<<(unsigned)((nq + per - 1) / per), kLutThreads, 0, c->stream>>>(c->d_dirs, c->nv, r->d_top, r->n_hat,
-                                                                                 d_quats, ng, r->d_lut);
+    const unsigned grid = (unsigned)((nq + per - 1) / per);
+    if (r->lut_bytes == 2)
+        k_build_lut<<<grid, kLutThreads, 0, c->stream>>>(c->d_dirs, c->nv, r->d_top, r->n_hat, d_quats, ng, r->ng_pad,
+                                                         static_cast<uint16_t*>(r->d_lut));
+    else
+        k_build_lut<<<grid, kLutThreads, 0, c->stream>>>(c->d_dirs, c->nv, r->d_top, r->n_hat, d_quats, ng, r->ng_pad,
+                                                         static_cast<int32_t*>(r->d_lut));
+    return cudaGetLastError();
+}
+
+template <typename IdxT>
+static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score) {
+    constexpr int G = 16 / (int)sizeof(IdxT);
+    const size_t smem = ((size_t)c->nv + r->n_hat) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_match<IdxT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // one thread per G orientations, whole warps, at most 1024 threads
+    const int64_t want = (r->ng + G - 1) / G;
+    const int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (want + 31) / 32 * 32));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match<IdxT>, threads, smem);
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, nroi);
+    k_match<IdxT><<<(unsigned)grid, threads, smem, c->stream>>>(S, nroi, c->nv, static_cast<const IdxT*>(r->d_lut),
+                                                                r->ng, r->ng_pad, r->d_top_val, r->n_hat, best, score);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score) {
-    const size_t smem = ((size_t)c->nv + r->n_hat) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_match, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match, kMatchThreads, smem);
-    per_sm = std::max(per_sm, 1);
-    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, nroi);
-    k_match<<<(unsigned)grid, kMatchThreads, smem, c->stream>>>(S, nroi, c->nv, r->d_lut, r->ng, r->d_top_val, r->n_hat,
-                                                                 best, score);
-    return cudaGetLastError();
+    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score)
+                             : launch_match_t<int32_t>(c, r, S, nroi, best, score);
 }
 
 cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q0, const double* omega,

@@ -28,9 +28,11 @@ struct Reference {
     float* d_top_val = nullptr;    // [n_hat] their values
     int32_t n_hat = 0;
     float* d_img = nullptr;        // [181 x 360] or null
-    int32_t* d_lut = nullptr;      // [n_hat x ng] (k-major)
+    void* d_lut = nullptr;         // [n_hat x ng_pad] (k-major), uint16 node indices when nv <= 65536, else int32
+    int lut_bytes = 4;             // bytes per table entry (2 or 4)
     double* d_quats = nullptr;     // [ng x 4] test orientations of the table
     int64_t ng = 0;
+    int64_t ng_pad = 0;            // row length of the table: ng rounded up to a multiple of 8
     int32_t nv_at_set = 0;
 };
 

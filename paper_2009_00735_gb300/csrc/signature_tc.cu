@@ -12,7 +12,7 @@
 //      to 0x0800) and the histogram is the A operand as it stands;
 //   2. an in-place permutation of 16-byte chunks gives the MN-major 128-byte
 //      swizzled layout (chunk c of bin row k moves to c ^ (k & 7));
-//   3. one thread issues 2^m / 16 tcgen05.mma (M = 64, K = 16, N = 16 per
+//   3. up to four issuer threads issue the 2^m / 16 tcgen05.mma (M = 64, K = 16, N = 16 per
 //      group of 4 frequencies: 8 hi columns, then 8 lo columns, where
 //      T = T_hi + T_lo with both parts fp16) into FP32 accumulators in TMEM;
 //   4. four warps read the accumulators (tcgen05.ld), add hi and lo parts,
@@ -203,18 +203,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 __syncthreads();   // every row is read before the permutation moves it
             }
 
-            // ---- 2 + 3. swizzle and contraction, pipelined over four K chunks.
-            // Warps kIssuers.. bring the bin rows of chunk q into the MN-major
+            // ---- 2. swizzle: every warp brings bin rows into the MN-major
             // 128-byte swizzled layout in place (a warp holds four rows, 512
             // contiguous bytes, one 16-byte chunk per lane, and writes chunk c
-            // of row k to chunk c ^ (k & 7)); then lane 0 of each of warps
-            // 0 .. n_iss-1 issues its share of the K steps of chunk q into its
-            // own partial accumulator while the others permute chunk q + 1.
-            // A single tcgen05.mma costs an issuing warp ~75 cycles whatever
-            // its N; four issuers overlap that cost.
+            // of row k to chunk c ^ (k & 7); rows with k & 7 == 0 stay).  The
+            // pass runs at the shared-memory bandwidth; interleaving it with
+            // the MMAs below slows both, so the two run one after the other.
+            // ---- 3. contraction: lane 0 of warps 0 .. n_iss-1 issues every
+            // n_iss-th K step into its own partial accumulator (a single
+            // tcgen05.mma costs the issuing warp ~75 cycles whatever its N;
+            // several issuers overlap that cost).
             const int n_iss = nbatch == 1 ? p.n_iss : 1;
-            const int rows_q = NB / 4;
-            const int kk_q = NB / 64;   // K steps of 16 bins per chunk
             const uint32_t sbo_b = (uint32_t)KB * 1024u;
             const uint32_t cols_b = (uint32_t)(16 * p.gb);   // TMEM columns per accumulator
             const bool issuer = lane == 0 && warp < n_iss;
@@ -235,64 +234,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 }
                 *flag = ok;
             }
-            for (int q = 0; q < 4; ++q) {
-                if (warp >= p.n_iss) {
-                    for (int r0 = q * rows_q + (warp - p.n_iss) * 4; r0 < (q + 1) * rows_q;
-                         r0 += (kWarps - p.n_iss) * 4) {
-                        const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
-                        uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
-                        uint4 x;
-                        if (sw) x = row[c];          // rows with k & 7 == 0 stay in place
-                        __syncwarp();
-                        if (sw) row[c ^ sw] = x;
-                    }
+            for (int r0 = warp * 4; r0 < NB; r0 += kWarps * 4) {
+                const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
+                uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
+                uint4 x;
+                if (sw) x = row[c];
+                __syncwarp();
+                if (sw) row[c ^ sw] = x;
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            ok = *flag;
+            if (issuer && ok) {
+                tc_fence_after();
+                const int nb0 = min(p.gb, fg1 + 1 - fg0);
+                const uint32_t idesc = idesc_f16(16 * nb0);
+                const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
+                const uint64_t a0 = sdesc_sw128(h_addr, 1024u, 1024u);
+                const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
+                // descriptors advance by constant steps: A by 2 KB per K step,
+                // B by 32 bytes inside a 128-byte row and 1 KB per 64-bin
+                // block (the address field counts 16-byte units)
+                for (int kk = warp; kk < NB / 16; kk += n_iss) {
+                    const uint64_t ad = a0 + (uint64_t)(kk * 128);
+                    const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+                    mma_f16(dcol, ad, bd, idesc, kk >= n_iss ? 1u : 0u);
                 }
-                fence_proxy_async_smem();
-                tc_fence_before();
-                __syncthreads();
-                if (q == 0) ok = *flag;
-                if (issuer && ok) {
-                    tc_fence_after();
-                    const int nb0 = min(p.gb, fg1 + 1 - fg0);
-                    const uint32_t idesc = idesc_f16(16 * nb0);
-                    const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
-                    const uint64_t a0 = sdesc_sw128(h_addr, 1024u, 1024u);
-                    const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
-                    // descriptors advance by constant steps: A by 2 KB per K
-                    // step, B by 32 bytes inside a 128-byte row and 1 KB per
-                    // 64-bin block (the address field counts 16-byte units)
-                    for (int kk = q * kk_q + warp; kk < (q + 1) * kk_q; kk += n_iss) {
-                        const uint64_t ad = a0 + (uint64_t)(kk * 128);
-                        const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
-                        mma_f16(dcol, ad, bd, idesc, kk >= n_iss ? 1u : 0u);
-                    }
-                    if (q == 3 && tid == 0 && nbatch > 1) {
-                        // wide band: further batches, each reloading the B buffer
-                        for (int b = 1; b < nbatch && ok; ++b) {
-                            mma_commit(&bars[2]);
-                            ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
-                            ph_mma ^= 1u;
-                            if (!ok) break;
-                            const int g0 = fg0 + b * p.gb;
-                            const int nb = min(p.gb, fg1 + 1 - g0);
-                            const uint32_t part = (uint32_t)nb * KB * 1024u;
-                            mbar_arrive_expect_tx(&bars[1], 2 * part);
-                            bulk_g2s(BT, p.twb + (size_t)g0 * KB * 1024, part, &bars[1]);
-                            bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + g0) * KB * 1024, part, &bars[1]);
-                            ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
-                            if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
-                            ph_b ^= 1u;
-                            cur_g0 = ok ? g0 : -1;
-                            cur_nb = nb;
-                            if (!ok) break;
-                            tc_fence_after();
-                            const uint32_t idb = idesc_f16(16 * nb);
-                            const uint32_t dcb = tmem + (uint32_t)b * cols_b;
-                            for (int kk = 0; kk < NB / 16; ++kk) {
-                                const uint64_t ad = a0 + (uint64_t)(kk * 128);
-                                const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
-                                mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : 0u);
-                            }
+                if (tid == 0 && nbatch > 1) {
+                    // wide band: further batches, each reloading the B buffer
+                    for (int b = 1; b < nbatch && ok; ++b) {
+                        mma_commit(&bars[2]);
+                        ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
+                        ph_mma ^= 1u;
+                        if (!ok) break;
+                        const int g0 = fg0 + b * p.gb;
+                        const int nb = min(p.gb, fg1 + 1 - g0);
+                        const uint32_t part = (uint32_t)nb * KB * 1024u;
+                        mbar_arrive_expect_tx(&bars[1], 2 * part);
+                        bulk_g2s(BT, p.twb + (size_t)g0 * KB * 1024, part, &bars[1]);
+                        bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + g0) * KB * 1024, part, &bars[1]);
+                        ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                        if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                        ph_b ^= 1u;
+                        cur_g0 = ok ? g0 : -1;
+                        cur_nb = nb;
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t idb = idesc_f16(16 * nb);
+                        const uint32_t dcb = tmem + (uint32_t)b * cols_b;
+                        for (int kk = 0; kk < NB / 16; ++kk) {
+                            const uint64_t ad = a0 + (uint64_t)(kk * 128);
+                            const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+                            mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : 0u);
                         }
                     }
                 }
