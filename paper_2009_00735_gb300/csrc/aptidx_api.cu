@@ -400,6 +400,9 @@ int aptidx_destroy(aptidx_ctx* ctx) {
     free_ptr(c->d_pos);
     free_ptr(c->d_types);
     free_ptr(c->d_dirs);
+    free_ptr(c->d_dirs_sorted);
+    free_ptr(c->d_gn_scratch);
+    c->gn_scratch_bytes = 0;
     free_ptr(c->d_tw);
     dev_free(c->d_twb);
     c->d_twb = nullptr;
@@ -496,11 +499,37 @@ int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem) 
             return set_error(c, APTIDX_E_INVALID_ARG, "directions: |u[%d]| = %g is not 1", v, sqrt(n2));
         d4[v] = make_float4(x, y, z, 0.f);
     }
+    // spatial order: Morton key of the (elevation, azimuth) 1-degree cell
+    std::vector<std::pair<uint32_t, int32_t>> key((size_t)nv);
+    for (int32_t v = 0; v < nv; ++v) {
+        const double x = d4[v].x, y = d4[v].y, z = d4[v].z;
+        const double el = asin(std::max(-1.0, std::min(1.0, z))) * (180.0 / M_PI) + 90.0;
+        double az = atan2(y, x) * (180.0 / M_PI);
+        if (az < 0.0) az += 360.0;
+        const uint32_t i = (uint32_t)std::min(180.0, std::max(0.0, floor(el)));
+        const uint32_t j = (uint32_t)std::min(359.0, std::max(0.0, floor(az)));
+        uint32_t k = 0;
+        for (int b = 0; b < 9; ++b) k |= ((i >> b) & 1u) << (2 * b + 1) | ((j >> b) & 1u) << (2 * b);
+        key[v] = {k, v};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<float4> ds((size_t)nv);
+    for (int32_t k = 0; k < nv; ++k) {
+        const int32_t v = key[k].second;
+        int32_t bits = v;
+        float w;
+        memcpy(&w, &bits, sizeof(w));
+        ds[k] = make_float4(d4[v].x, d4[v].y, d4[v].z, w);
+    }
     free_ptr(c->d_dirs);
+    free_ptr(c->d_dirs_sorted);
     clear_graphs(c);
     c->nv = c->nv_pad = 0;
     if ((rc = dev_alloc(c, (void**)&c->d_dirs, (size_t)nv_pad * sizeof(float4)))) return rc;
+    if ((rc = dev_alloc(c, (void**)&c->d_dirs_sorted, (size_t)nv * sizeof(float4)))) return rc;
     APTIDX_CUDA(c, cudaMemcpyAsync(c->d_dirs, d4.data(), (size_t)nv_pad * sizeof(float4), cudaMemcpyHostToDevice,
+                                   c->stream));
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_dirs_sorted, ds.data(), (size_t)nv * sizeof(float4), cudaMemcpyHostToDevice,
                                    c->stream));
     APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
     c->nv = nv;

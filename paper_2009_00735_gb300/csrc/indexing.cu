@@ -279,6 +279,34 @@ constexpr int kRefThreads = 256;
 constexpr float kPoleDeg = 89.0f;
 constexpr float kRad2Deg = 57.295779513082320876f;
 
+// atan(t) for t in [0, 1] as t * P(t^2), P of degree 7 with coefficients that
+// minimise the maximum error on [0, 1] (Lawson's iteratively reweighted least
+// squares; atan_fit.py regenerates them): |error| < 4e-8 rad in exact
+// arithmetic, < 2e-7 rad with FP32 Horner steps.
+__device__ __forceinline__ float atan01(float t) {
+    const float s = t * t;
+    float p = -4.054556496e-03f;
+    p = fmaf(p, s, 2.186292078e-02f);
+    p = fmaf(p, s, -5.591227578e-02f);
+    p = fmaf(p, s, 9.642193788e-02f);
+    p = fmaf(p, s, -1.390862825e-01f);
+    p = fmaf(p, s, 1.994656541e-01f);
+    p = fmaf(p, s, -3.332986076e-01f);
+    p = fmaf(p, s, 9.999993356e-01f);
+    return t * p;
+}
+
+// atan2(y, x) in degrees, (-180, 180]: octant reduction to atan01 of
+// min(|x|, |y|) / max(|x|, |y|) (a 2-ulp quotient).  NaN when x = y = 0.
+__device__ __forceinline__ float atan2_deg(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    float a = atan01(__fdividef(fminf(ax, ay), fmaxf(ax, ay)));
+    if (ay > ax) a = 1.57079632679489662f - a;
+    if (x < 0.f) a = 3.14159265358979324f - a;
+    if (y < 0.f) a = -a;
+    return a * kRad2Deg;
+}
+
 struct DirTerm {
     bool ok;
     float r;       // residual S - I
@@ -295,11 +323,12 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
     const float cy = Rf[1] * ux + Rf[4] * uy + Rf[7] * uz;
     const float cz = Rf[2] * ux + Rf[5] * uy + Rf[8] * uz;
     const float rho2 = cx * cx + cy * cy;
-    const float rho = sqrtf(rho2);
-    const float alpha = atan2f(cz, rho) * kRad2Deg;
-    t.ok = fabsf(alpha) <= kPoleDeg;
+    const float inv_rho = rsqrtf(rho2);
+    const float rho = rho2 * inv_rho;
+    const float alpha = atan2_deg(cz, rho);
+    t.ok = fabsf(alpha) <= kPoleDeg;   // also false for NaN at the exact poles
     if (!t.ok) return t;
-    float beta = atan2f(cy, cx) * kRad2Deg;
+    float beta = atan2_deg(cy, cx);
     if (beta < 0.f) beta += 360.f;
     const float fi = alpha + 90.f;
     int i0 = (int)floorf(fi);
@@ -322,8 +351,8 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
         // reciprocals are far inside the FP32 error of the sums they feed
         const float n2 = rho2 + cz * cz;
         const float inv_n2 = __fdividef(1.f, n2);
-        const float inv_rho2 = __fdividef(1.f, rho2);
-        const float t_a = -cz * __fdividef(inv_n2, rho);
+        const float inv_rho2 = inv_rho * inv_rho;
+        const float t_a = -cz * inv_n2 * inv_rho;
         const float da0 = t_a * cx, da1 = t_a * cy, da2 = rho * inv_n2;
         const float db0 = -cy * inv_rho2, db1 = cx * inv_rho2;
         const float g0 = kRad2Deg * (dfi * da0 + dfj * db0);
@@ -353,26 +382,33 @@ __device__ __forceinline__ float ld_stream(const float* p) {
     return v;
 }
 
+// coherent read that skips L1 (for data this kernel writes)
+__device__ __forceinline__ float ld_l2(const float* p) {
+    float v;
+    asm volatile("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // block sum of n FP32 partials per thread into FP64 totals (thread 0 holds them)
 template <int N>
-__device__ __forceinline__ void block_sum(float* v, double* out, double* scratch /* [N * 8] */) {
+__device__ __forceinline__ void block_sum(float* v, double* out, double* scratch /* [N * 32] */) {
     double d[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         d[i] = (double)v[i];
         for (int o = 16; o > 0; o >>= 1) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
     }
-    const int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int i = 0; i < N; ++i) scratch[i * (kRefThreads / 32) + w] = d[i];
+        for (int i = 0; i < N; ++i) scratch[i * 32 + w] = d[i];
     __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             double s = 0.0;
-            for (int k = 0; k < kRefThreads / 32; ++k) s += scratch[i * (kRefThreads / 32) + k];
+            for (int k = 0; k < nw; ++k) s += scratch[i * 32 + k];
             out[i] = s;
         }
 }
@@ -407,7 +443,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __rest
                                                              int32_t nv, const float* __restrict__ img,
                                                              const double* __restrict__ q0, const double* __restrict__ omega,
                                                              int64_t nroi, float* loss, float* grad) {
-    __shared__ double scratch[4 * (kRefThreads / 32)];
+    __shared__ double scratch[4 * 32];
     __shared__ double tot[4];
     __shared__ float Rs[9];
     for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
@@ -467,17 +503,30 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __rest
 // `iters` Gauss-Newton steps per ROI in one CTA: per step the direction terms
 // give J^T J and J^T r (FP32 partials, FP64 block sums), thread 0 solves
 // (J^T J + lambda I) delta = -J^T r with lambda = 1e-6 tr(J^T J) in FP64 and
-// updates q <- exp(delta) q with FP64 renormalisation.
-__global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restrict__ S, const float4* __restrict__ dirs,
-                                                           int32_t nv, const float* __restrict__ img,
-                                                           const double* __restrict__ q0, const int32_t* __restrict__ best,
-                                                           const double* __restrict__ quats, int64_t nroi, int iters,
-                                                           double* q_out, float* loss_out) {
-    __shared__ double scratch[10 * (kRefThreads / 32)];
+// updates q <- exp(delta) q with FP64 renormalisation.  The directions are
+// walked in the spatial order of `dsort` (w = index into the signature row),
+// so that neighbouring lanes sample neighbouring pixels of the image; the
+// CTA first gathers the ROI's row into that order in its own scratch row
+// (global memory, L2-resident while the steps run).
+constexpr int kGnThreads = 256;
+
+__global__ void __launch_bounds__(kGnThreads) k_refine_gn(const float* __restrict__ S, const float4* __restrict__ dsort,
+                                                          int32_t nv, const float* __restrict__ img,
+                                                          const double* __restrict__ q0,
+                                                          const int32_t* __restrict__ best,
+                                                          const double* __restrict__ quats, int64_t nroi, int iters,
+                                                          float* scratch, double* q_out, float* loss_out) {
+    __shared__ double red[10 * 32];
     __shared__ double tot[10];
     __shared__ double qs[4];
     __shared__ float Rs[9];
+    float* srow = scratch + (int64_t)blockIdx.x * nv;
     for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
+        __syncthreads();   // the previous ROI is done with srow
+        {
+            const float* src = S + r * (int64_t)nv;
+            for (int i = threadIdx.x; i < nv; i += blockDim.x) srow[i] = src[__float_as_int(__ldg(&dsort[i].w))];
+        }
         if (threadIdx.x == 0) {
             const double* qa = best ? quats + 4 * (int64_t)best[r] : q0 + 4 * r;
             double n = 0.0;
@@ -485,7 +534,6 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restri
             n = sqrt(n);
             for (int i = 0; i < 4; ++i) qs[i] = qa[i] / n;
         }
-        const float* srow = S + r * (int64_t)nv;
         for (int it = 0; it <= iters; ++it) {
             const bool last = it == iters;   // final pass: loss only
             if (threadIdx.x == 0) matrix_f32(qs, Rs);
@@ -493,9 +541,9 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restri
             float Rf[9];
             for (int i = 0; i < 9; ++i) Rf[i] = Rs[i];
             float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // L, Jtr[3], JtJ[6]
-            for (int v = threadIdx.x; v < nv; v += kRefThreads) {
-                const float4 u = ld_stream4(dirs + v);
-                const DirTerm t = dir_term(Rf, u.x, u.y, u.z, ld_stream(srow + v), img, !last);
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                const float4 u = ld_stream4(dsort + v);
+                const DirTerm t = dir_term(Rf, u.x, u.y, u.z, ld_l2(srow + v), img, !last);
                 if (!t.ok) continue;
                 acc[0] = fmaf(t.r, t.r, acc[0]);
                 if (!last) {
@@ -510,7 +558,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_gn(const float* __restri
                     acc[9] = fmaf(t.J[2], t.J[2], acc[9]);
                 }
             }
-            block_sum<10>(acc, tot, scratch);
+            block_sum<10>(acc, tot, red);
             if (threadIdx.x == 0) {
                 if (last) {
                     if (loss_out) loss_out[r] = (float)tot[0];
@@ -642,9 +690,19 @@ cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const doubl
 
 cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double* q0, const int32_t* best,
                              int64_t nroi, int iters, double* q_out, float* loss) {
-    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * 8, nroi);
-    k_refine_gn<<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, best, r->d_quats,
-                                                               nroi, iters, q_out, loss);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_gn, kGnThreads, 0);
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * std::max(per_sm, 1), nroi);
+    const size_t need = (size_t)grid * c->nv * sizeof(float);
+    if (need > c->gn_scratch_bytes) {
+        dev_free(c->d_gn_scratch);
+        c->d_gn_scratch = nullptr;
+        c->gn_scratch_bytes = 0;
+        if (dev_alloc(c, (void**)&c->d_gn_scratch, need)) return cudaErrorMemoryAllocation;
+        c->gn_scratch_bytes = need;
+    }
+    k_refine_gn<<<(unsigned)grid, kGnThreads, 0, c->stream>>>(S, c->d_dirs_sorted, c->nv, r->d_img, q0, best,
+                                                              r->d_quats, nroi, iters, c->d_gn_scratch, q_out, loss);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,13 @@ struct Ctx {
     // directions (padded to a multiple of kTileDirs with (1, 0, 0))
     int32_t nv = 0, nv_pad = 0;
     float4* d_dirs = nullptr;
+    // the same directions in a spatially coherent order (Morton order of 1-degree
+    // elevation-azimuth cells), w = the direction's index as int bits; the
+    // refinement walks this order so that neighbouring lanes sample
+    // neighbouring pixels of the reference image
+    float4* d_dirs_sorted = nullptr;
+    float* d_gn_scratch = nullptr;   // one signature row per refinement CTA, in the order above
+    size_t gn_scratch_bytes = 0;
 
     // binning
     int m = 0;

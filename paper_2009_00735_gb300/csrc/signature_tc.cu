@@ -5,6 +5,13 @@
 // spectrum of every SDM; the paper notes that the SDMs of a ROI share one
 // bin count, which permits batching their transforms).
 //
+// The contraction runs as M = 128 rows: rows 0-63 are the 64 directions over
+// bins [0, 2^m / 2), rows 64-127 the same directions over [2^m / 2, 2^m).
+// Both halves use the twiddles of the first half, since
+// w^(k (n + 2^m / 2)) = (-1)^k w^(k n) for w = exp(-2 pi i / 2^m); the
+// epilogue forms X(k) = D_lo(k) + (-1)^k D_hi(k).  Half the K steps of an
+// M = 64 contraction, so half the MMA instructions.
+//
 // Per 64-direction tile of a ROI:
 //   1. histograms by shared-memory atomics (bank-private columns, as in the
 //      FP32 path); counts c <= 2048, so the u16 bit pattern of c is the fp16
@@ -12,11 +19,12 @@
 //      to 0x0800) and the histogram is the A operand as it stands;
 //   2. an in-place permutation of 16-byte chunks gives the MN-major 128-byte
 //      swizzled layout (chunk c of bin row k moves to c ^ (k & 7));
-//   3. up to four issuer threads issue the 2^m / 16 tcgen05.mma (M = 64, K = 16, N = 16 per
-//      group of 4 frequencies: 8 hi columns, then 8 lo columns, where
-//      T = T_hi + T_lo with both parts fp16) into FP32 accumulators in TMEM;
-//   4. four warps read the accumulators (tcgen05.ld), add hi and lo parts,
-//      scale by 2^24 and keep the band maximum of |X(k)|.
+//   3. up to four issuer threads issue the 2^m / 32 tcgen05.mma (M = 128,
+//      K = 16, N = 16 per group of 4 frequencies: 8 hi columns, then 8 lo
+//      columns, where T = T_hi + T_lo with both parts fp16) into FP32
+//      accumulators in TMEM;
+//   4. four warps read the accumulators (tcgen05.ld), add hi and lo parts and
+//      the two bin halves, scale by 2^24 and keep the band maximum of |X(k)|.
 // ROIs with more than 2048 atoms (where a bin could exceed fp16's exact
 // range) run on the FP32 kernel in the same call.
 #include <cuda_fp16.h>
@@ -29,8 +37,10 @@ namespace {
 
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
-constexpr int kDirs = kTileDirs;     // M = 64
-constexpr int kBtBytes = 64 * 1024;  // shared-memory budget of the B operand
+constexpr int kDirs = kTileDirs;     // 64 directions per tile
+constexpr int kRows = 2 * kDirs;     // MMA M: (direction, bin half)
+constexpr int kBtBytes = 32 * 1024;  // shared-memory budget of the B operand
+constexpr int kExBytes = kDirs * 8 * 4;   // epilogue exchange: one group's (re, im) x 4 per direction
 constexpr int kIssuers = 4;          // at most this many warps issue MMAs, one TMEM partial accumulator each
 
 struct TcParams {
@@ -76,9 +86,9 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr, uint32_t lbo, uin
     return d;
 }
 
-// instruction descriptor: D f32, A f16 MN-major, B f16 K-major, M = 64
+// instruction descriptor: D f32, A f16 MN-major, B f16 K-major, M = 128
 __device__ __forceinline__ uint32_t idesc_f16(int n) {
-    return (1u << 4) | (1u << 15) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kDirs >> 4) << 24);
+    return (1u << 4) | (1u << 15) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -117,10 +127,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int NB = 1 << p.m;
     const int nbm1 = NB - 1;
-    const int KB = NB / 64;   // 1 KB K-blocks per 8-row column group
+    const int KB = NB / 128;   // 1 KB K-blocks of the B operand (K = 2^m / 2 rows)
     uint32_t* H = reinterpret_cast<uint32_t*>(smem);
     unsigned char* BT = smem + (size_t)NB * 128;
-    float4* A = reinterpret_cast<float4*>(BT + kBtBytes);
+    float* EX = reinterpret_cast<float*>(BT + kBtBytes);   // [kDirs][8]
+    float4* A = reinterpret_cast<float4*>(BT + kBtBytes + kExBytes);
     // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per issuer
     uint64_t* bars = reinterpret_cast<uint64_t*>(A + p.atom_cap);
     int* flag = reinterpret_cast<int*>(bars + 2 + kIssuers);
@@ -251,12 +262,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 const int nb0 = min(p.gb, fg1 + 1 - fg0);
                 const uint32_t idesc = idesc_f16(16 * nb0);
                 const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
-                const uint64_t a0 = sdesc_sw128(h_addr, 1024u, 1024u);
+                // A: rows 64-127 (second bin half) one swizzle atom along M
+                // away, NB / 2 bin rows of 128 bytes
+                const uint64_t a0 = sdesc_sw128(h_addr, (uint32_t)NB * 64u, 1024u);
                 const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
                 // descriptors advance by constant steps: A by 2 KB per K step,
                 // B by 32 bytes inside a 128-byte row and 1 KB per 64-bin
                 // block (the address field counts 16-byte units)
-                for (int kk = warp; kk < NB / 16; kk += n_iss) {
+                for (int kk = warp; kk < NB / 32; kk += n_iss) {
                     const uint64_t ad = a0 + (uint64_t)(kk * 128);
                     const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
                     mma_f16(dcol, ad, bd, idesc, kk >= n_iss ? 1u : 0u);
@@ -283,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                         tc_fence_after();
                         const uint32_t idb = idesc_f16(16 * nb);
                         const uint32_t dcb = tmem + (uint32_t)b * cols_b;
-                        for (int kk = 0; kk < NB / 16; ++kk) {
+                        for (int kk = 0; kk < NB / 32; ++kk) {
                             const uint64_t ad = a0 + (uint64_t)(kk * 128);
                             const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
                             mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : 0u);
@@ -318,11 +331,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 for (int i = tid - 128; i < NB * 8; i += kThreads - 128)
                     reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
             } else {
+                // warps 0, 1 hold rows 0-63 (bins of the first half), warps
+                // 2, 3 rows 64-127; per frequency group the second-half warps
+                // hand their sums over through shared memory
                 float best = -1.f;
                 int bk = klo;
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
                 const int n_iss = nbatch == 1 ? p.n_iss : 1;
                 const uint32_t cols_b = (uint32_t)(16 * p.gb);
+                const int dir = (warp & 1) * 32 + lane;
                 for (int b = 0; b < nbatch; ++b) {
                     const int g0 = fg0 + b * p.gb;
                     const int nb = min(p.gb, fg1 + 1 - g0);
@@ -340,20 +357,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                                 im[q] += hi[2 * q + 1] + lo[2 * q + 1];
                             }
                         }
+                        if (warp >= 2) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int f = p.kbase + 4 * (g0 + j) + q;
-                            const float a = sqrtf(re[q] * re[q] + im[q] * im[q]) * 16777216.0f;
-                            if (f >= klo && f <= khi && a > best) {
-                                best = a;
-                                bk = f;
+                            for (int q = 0; q < 4; ++q) {
+                                EX[dir * 8 + 2 * q] = re[q];
+                                EX[dir * 8 + 2 * q + 1] = im[q];
                             }
                         }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (warp < 2) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int f = p.kbase + 4 * (g0 + j) + q;
+                                const float sg = (f & 1) ? -1.f : 1.f;
+                                const float xr = re[q] + sg * EX[dir * 8 + 2 * q];
+                                const float xi = im[q] + sg * EX[dir * 8 + 2 * q + 1];
+                                const float a = sqrtf(xr * xr + xi * xi) * 16777216.0f;
+                                if (f >= klo && f <= khi && a > best) {
+                                    best = a;
+                                    bk = f;
+                                }
+                            }
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
                     }
                 }
-                if (lane < 16) {
-                    const int mrow = warp * 16 + lane;
-                    const int64_t v = (int64_t)tile * kDirs + mrow;
+                if (warp < 2) {
+                    const int64_t v = (int64_t)tile * kDirs + dir;
                     if (v < p.nv) {
                         const int64_t o = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv + v;
                         p.S[o] = best;
@@ -377,15 +407,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
 
 // ---- the global B operand: DFT matrix columns, fp16 hi + lo, K-major SW128 ----
 
+// K runs over the first half of the bins, n in [0, 2^m / 2).
 __global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng) {
     const int NB = 1 << m;
-    const int KB = NB / 64;
-    const int64_t total = (int64_t)2 * ng * NB * 8;   // [hi|lo] x groups x bins x 8 rows
+    const int NK = NB / 2;
+    const int KB = NK / 64;
+    const int64_t total = (int64_t)2 * ng * NK * 8;   // [hi|lo] x groups x K rows x 8 columns
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i & 7);
         const int64_t t = i >> 3;
-        const int k = (int)(t % NB);
-        const int64_t t2 = t / NB;
+        const int k = (int)(t % NK);
+        const int64_t t2 = t / NK;
         const int g = (int)(t2 % ng);
         const int part = (int)(t2 / ng);   // 0 hi, 1 lo
         const int f = kbase + 4 * g + (r >> 1);
@@ -412,14 +444,14 @@ bool tc_supported(Ctx* c) {
 }
 
 static size_t tc_smem_bytes(int m, int atom_cap) {
-    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + (size_t)atom_cap * 16 + 256;
+    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 256;
 }
 
 // Build the B operand for the current ROI bands and pick the TMEM size.
 int prepare_tc(Ctx* c) {
     if (!tc_supported(c)) return set_error(c, APTIDX_E_INVALID_ARG, "tensor-core path needs an sm_103 device");
     const int NB = 1 << c->m;
-    const int KB = NB / 64;
+    const int KB = NB / 128;   // 1 KB blocks of 64 K rows, K = NB / 2
     const int kbase = c->band_min;
     const int ng = (c->band_max - kbase) / 4 + 1;
     const int gb = kBtBytes / (2 * KB * 1024);
@@ -444,7 +476,7 @@ int prepare_tc(Ctx* c) {
         const size_t bytes = (size_t)2 * ng * KB * 1024;
         int rc = dev_alloc(c, &c->d_twb, bytes);
         if (rc) return rc;
-        k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)2 * ng * NB * 8 + 255) / 256, 4096), 256, 0, c->stream>>>(
+        k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)ng * NB * 8 + 255) / 256, 4096), 256, 0, c->stream>>>(
             (uint8_t*)c->d_twb, c->m, kbase, ng);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(c, e, "twiddle operand");
