@@ -173,7 +173,9 @@ __global__ void __launch_bounds__(kLutThreads) k_build_lut(const float4* __restr
 // Delta(g) = sum_k (S[lut[k, g]] - ref[k])^2 accumulated in FP32 in k order,
 // argmin with ties to the lowest g.  The table streams from L2 once per ROI:
 // each thread reads 16 bytes of a table row per k (G = 16 / sizeof(IdxT)
-// consecutive orientations) and keeps four rows in flight.
+// consecutive orientations) and keeps kMatchDepth rows in flight.
+constexpr int kMatchDepth = 8;   // table rows in flight per thread
+
 template <typename IdxT>
 __device__ __forceinline__ uint4 lut_load(const IdxT* p) {
     uint4 v;
@@ -233,12 +235,12 @@ __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, 
             for (int e = 0; e < G; ++e) acc[e] = 0.f;
             const IdxT* lp = lut_t + g0;
             int k = 0;
-            for (; k + 4 <= n_hat; k += 4) {
-                uint4 w[4];
+            for (; k + kMatchDepth <= n_hat; k += kMatchDepth) {
+                uint4 w[kMatchDepth];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w[j] = lut_load(lp + (int64_t)(k + j) * ng_pad);
+                for (int j = 0; j < kMatchDepth; ++j) w[j] = lut_load(lp + (int64_t)(k + j) * ng_pad);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) lut_accumulate<IdxT>(w[j], row, ref[k + j], acc);
+                for (int j = 0; j < kMatchDepth; ++j) lut_accumulate<IdxT>(w[j], row, ref[k + j], acc);
             }
             for (; k < n_hat; ++k) lut_accumulate<IdxT>(lut_load(lp + (int64_t)k * ng_pad), row, ref[k], acc);
 #pragma unroll
