@@ -399,11 +399,21 @@ def run_gb300(args):
         S_h = torch.empty((nroi, nv), dtype=torch.float32).pin_memory()
         q_h = torch.empty((nroi, 4), dtype=torch.float64).pin_memory()
 
+        copy_stream = torch.cuda.Stream()
+
         def e2e_step():
+            # the signature array streams to the host while Eq. 3 and the
+            # refinement (which only read it) run on the library's stream
             apt.aptidx_load_positions(h, xyz_h)
             apt.aptidx_set_rois(h, cen_h, rad_h)
-            full_step(headline)
-            S_h.copy_(S, non_blocking=True)
+            apt.aptidx_compute_signatures(h, code[headline], apt.APTIDX_NORMALISE_MAX | tuned, S, None, None)
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            copy_stream.wait_event(ready)
+            with torch.cuda.stream(copy_stream):
+                S_h.copy_(S, non_blocking=True)
+            apt.aptidx_match(h, 0, S, best, score)
+            apt.aptidx_refine(h, 0, S, None, iters, q_out, rloss, best=best)
             q_h.copy_(q_out, non_blocking=True)
             torch.cuda.synchronize()
 

@@ -317,7 +317,9 @@ struct DirTerm {
 
 // residual and its derivative with respect to the lab-frame perturbation delta
 // of R = exp([delta]x) R(q) for one direction: c = R^T u, (alpha, beta) of c,
-// bilinear sample of the image, r = s - I, J = -(R grad_c I) x u.
+// bilinear sample of the image, r = s - I, J = -(R grad_c I) x u
+// = -R (grad_c I x c); kCrystalJ returns grad_c I x c instead.
+template <bool kCrystalJ = false>
 __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy, float uz, float s,
                                             const float* __restrict__ img, bool want_j) {
     DirTerm t;
@@ -360,12 +362,19 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
         const float g0 = kRad2Deg * (dfi * da0 + dfj * db0);
         const float g1 = kRad2Deg * (dfi * da1 + dfj * db1);
         const float g2 = kRad2Deg * (dfi * da2);
-        const float ax = Rf[0] * g0 + Rf[1] * g1 + Rf[2] * g2;
-        const float ay = Rf[3] * g0 + Rf[4] * g1 + Rf[5] * g2;
-        const float az = Rf[6] * g0 + Rf[7] * g1 + Rf[8] * g2;
-        t.J[0] = -(ay * uz - az * uy);
-        t.J[1] = -(az * ux - ax * uz);
-        t.J[2] = -(ax * uy - ay * ux);
+        if (kCrystalJ) {
+            // J = -R (g x c): keep g x c; the caller rotates the sums once
+            t.J[0] = g1 * cz - g2 * cy;
+            t.J[1] = g2 * cx - g0 * cz;
+            t.J[2] = g0 * cy - g1 * cx;
+        } else {
+            const float ax = Rf[0] * g0 + Rf[1] * g1 + Rf[2] * g2;
+            const float ay = Rf[3] * g0 + Rf[4] * g1 + Rf[5] * g2;
+            const float az = Rf[6] * g0 + Rf[7] * g1 + Rf[8] * g2;
+            t.J[0] = -(ay * uz - az * uy);
+            t.J[1] = -(az * ux - ax * uz);
+            t.J[2] = -(ax * uy - ay * ux);
+        }
     }
     return t;
 }
@@ -545,7 +554,7 @@ __global__ void __launch_bounds__(kGnThreads) k_refine_gn(const float* __restric
             float acc[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // L, Jtr[3], JtJ[6]
             for (int v = threadIdx.x; v < nv; v += blockDim.x) {
                 const float4 u = ld_stream4(dsort + v);
-                const DirTerm t = dir_term(Rf, u.x, u.y, u.z, ld_l2(srow + v), img, !last);
+                const DirTerm t = dir_term<true>(Rf, u.x, u.y, u.z, ld_l2(srow + v), img, !last);
                 if (!t.ok) continue;
                 acc[0] = fmaf(t.r, t.r, acc[0]);
                 if (!last) {
@@ -570,7 +579,10 @@ __global__ void __launch_bounds__(kGnThreads) k_refine_gn(const float* __restric
                     H[0] += lam;
                     H[4] += lam;
                     H[8] += lam;
-                    const double b[3] = {-tot[1], -tot[2], -tot[3]};
+                    // crystal-frame sums: J = -R j with j = g x c, so the lab system
+                    // (R H_c R^T + lambda I) delta = R sum(j r) is solved as
+                    // delta = R (H_c + lambda I)^-1 sum(j r)
+                    const double b[3] = {tot[1], tot[2], tot[3]};
                     const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
                                        H[2] * (H[3] * H[7] - H[4] * H[6]);
                     double d[3] = {0.0, 0.0, 0.0};
@@ -585,8 +597,12 @@ __global__ void __launch_bounds__(kGnThreads) k_refine_gn(const float* __restric
                                     Bm[2] * (Bm[3] * Bm[7] - Bm[4] * Bm[6])) / det;
                         }
                     }
+                    const M3 Rq = quat_to_matrix(qs[0], qs[1], qs[2], qs[3]);
+                    const double dl[3] = {Rq.a[0] * d[0] + Rq.a[1] * d[1] + Rq.a[2] * d[2],
+                                          Rq.a[3] * d[0] + Rq.a[4] * d[1] + Rq.a[5] * d[2],
+                                          Rq.a[6] * d[0] + Rq.a[7] * d[1] + Rq.a[8] * d[2]};
                     double e[4], qn[4];
-                    exp_quat(d, e);
+                    exp_quat(dl, e);
                     quat_mul(e, qs, qn);
                     const double n = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
                     for (int i = 0; i < 4; ++i) qs[i] = qn[i] / n;
