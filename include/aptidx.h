@@ -197,6 +197,19 @@ int aptidx_get_lut(aptidx_ctx* ctx, int32_t cand, int32_t* lut, int32_t* n_hat_o
 int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, int32_t* best,
                  float* score, int mem);
 
+/* Eq. 3 keeping the topk best orientations per ROI (the paper keeps up to
+ * 1000 solutions per ROI, supplement "Indexing algorithm"):
+ * best[roi * topk + i] and score[roi * topk + i], i < topk, ascending by
+ * (Delta, g) -- ties resolve to the lower g, so topk = 1 equals
+ * aptidx_match.  1 <= topk <= min(ng, APTIDX_MAX_TOPK).  Delta is
+ * accumulated in FP32 in k order as in aptidx_match.  The scores of a chunk
+ * of ROIs are staged on the device (at most 1 GiB, library-owned) and
+ * reduced by a radix select per ROI.  S, best, score (NULL to skip) in
+ * `mem`.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
+#define APTIDX_MAX_TOPK 1024
+int aptidx_match_topk(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, int32_t topk, int32_t* best,
+                      float* score, int mem);
+
 /* ---- orientation refinement ------------------------------------------------ */
 
 /* Loss and gradient of the misfit between measured signatures and the

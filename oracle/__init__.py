@@ -244,6 +244,16 @@ def lut(dirs, top, quats, threads=0):
     return out
 
 
+def match_topk(S_msr, S_ref, top, lut_, k, threads=0):
+    """The k best test orientations per ROI under Eq. 3 (supplement "Indexing
+    algorithm": the paper keeps up to 1000 solutions per ROI): Delta(g) of
+    every g in FP64 (orc_match), then a stable sort by (Delta, g).
+    Returns (g int32 [nroi, k], Delta float64 [nroi, k])."""
+    _, _, sc = match(S_msr, S_ref, top, lut_, return_scores=True, threads=threads)
+    order = np.argsort(sc, axis=1, kind="stable")[:, :k]
+    return order.astype(np.int32), np.take_along_axis(sc, order, axis=1)
+
+
 def match(S_msr, S_ref, top, lut_, return_scores=False, threads=0):
     S = _c(S_msr, np.float32)
     S = S.reshape(-1, S.shape[-1])

@@ -22,7 +22,7 @@ __all__ = [
     "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
-    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_refine_loss", "aptidx_refine",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
@@ -30,6 +30,7 @@ __all__ = [
 ]
 
 APTIDX_OK = 0
+APTIDX_MAX_TOPK = 1024
 APTIDX_E_INVALID_ARG = 1
 APTIDX_E_CUDA = 2
 APTIDX_E_OOM = 3
@@ -74,6 +75,7 @@ _SIGS = {
     "aptidx_build_lut": (C.c_int, [_vp, _i32, _vp, _i64, C.c_int]),
     "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
+    "aptidx_match_topk": (C.c_int, [_vp, _i32, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
@@ -293,6 +295,15 @@ def aptidx_match(ctx, cand: int, S, best, score=None):
     ps, ms = _out(score, np.float32)
     nroi = best.shape[0]
     _check(ctx, load().aptidx_match(ctx, cand, pS, nroi, pb, ps, _one_mem(mS, mb, ms)))
+
+
+def aptidx_match_topk(ctx, cand: int, S, topk: int, best, score=None):
+    """best, score: [nroi, topk] outputs, ascending by (Delta, g)."""
+    pS, mS, kS = _arg(S, np.float32)
+    pb, mb = _out(best, np.int32)
+    ps, ms = _out(score, np.float32)
+    nroi = best.shape[0]
+    _check(ctx, load().aptidx_match_topk(ctx, cand, pS, nroi, int(topk), pb, ps, _one_mem(mS, mb, ms)))
 
 
 def aptidx_refine_loss(ctx, cand: int, S, q0, loss, grad=None, omega=None):

@@ -403,6 +403,8 @@ int aptidx_destroy(aptidx_ctx* ctx) {
     free_ptr(c->d_dirs_sorted);
     free_ptr(c->d_gn_scratch);
     c->gn_scratch_bytes = 0;
+    free_ptr(c->d_match_scratch);
+    c->match_scratch_bytes = 0;
     free_ptr(c->d_tw);
     dev_free(c->d_twb);
     c->d_twb = nullptr;
@@ -1054,6 +1056,61 @@ int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, in
     prof_end(c, APTIDX_PHASE_MATCH, 1);
     if ((rc = copy_back(c, best, db, (size_t)nroi, mem))) return rc;
     if ((rc = copy_back(c, score, ds, (size_t)nroi, mem))) return rc;
+    if (mem == APTIDX_MEM_HOST) return read_status(c);
+    return APTIDX_OK;
+}
+
+int aptidx_match_topk(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, int32_t topk, int32_t* best,
+                      float* score, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if ((rc = check_ref(c, cand, true, false))) return rc;
+    Reference& r = c->ref[cand];
+    if (!S || !best || nroi <= 0) return set_error(c, APTIDX_E_INVALID_ARG, "match_topk: need S, best and nroi > 0");
+    if (topk < 1 || topk > APTIDX_MAX_TOPK || topk > r.ng)
+        return set_error(c, APTIDX_E_INVALID_ARG, "match_topk: topk = %d outside [1, min(ng = %lld, %d)]", topk,
+                         (long long)r.ng, APTIDX_MAX_TOPK);
+    static int max_optin = -1;
+    if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (((size_t)c->nv + r.n_hat) * sizeof(float) > (size_t)max_optin)
+        return set_error(c, APTIDX_E_INVALID_ARG, "match: %d directions do not fit one shared-memory signature row", c->nv);
+    DevTmp tS, tb, ts;
+    const float* dS;
+    int32_t* db;
+    float* ds;
+    const size_t nout = (size_t)nroi * topk;
+    if ((rc = dev_view(c, S, (size_t)nroi * c->nv, mem, tS, &dS))) return rc;
+    if ((rc = dev_out(c, best, nout, mem, tb, &db))) return rc;
+    if ((rc = dev_out(c, score, nout, mem, ts, &ds))) return rc;
+    prof_begin(c, APTIDX_PHASE_MATCH);
+    int launches = 0;
+    if (topk == 1) {
+        cudaError_t e = launch_match(c, &r, dS, nroi, db, ds);
+        if (e != cudaSuccess) return cuda_check(c, e, "match");
+        launches = 1;
+    } else {
+        // scores of a chunk of ROIs (at most 1 GiB), then a radix select per ROI
+        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nroi, ((int64_t)1 << 30) / (r.ng * 4)));
+        const size_t need = (size_t)chunk * r.ng * sizeof(float);
+        if (need > c->match_scratch_bytes) {
+            free_ptr(c->d_match_scratch);
+            c->match_scratch_bytes = 0;
+            if ((rc = dev_alloc(c, (void**)&c->d_match_scratch, need))) return rc;
+            c->match_scratch_bytes = need;
+        }
+        for (int64_t r0 = 0; r0 < nroi; r0 += chunk) {
+            const int64_t n = std::min(chunk, nroi - r0);
+            cudaError_t e = launch_match(c, &r, dS + r0 * c->nv, n, nullptr, nullptr, c->d_match_scratch);
+            if (e == cudaSuccess)
+                e = launch_topk(c, c->d_match_scratch, r.ng, n, topk, db + r0 * topk, ds ? ds + r0 * topk : nullptr);
+            if (e != cudaSuccess) return cuda_check(c, e, "match_topk");
+            launches += 2;
+        }
+    }
+    prof_end(c, APTIDX_PHASE_MATCH, launches);
+    if ((rc = copy_back(c, best, db, nout, mem))) return rc;
+    if ((rc = copy_back(c, score, ds, nout, mem))) return rc;
     if (mem == APTIDX_MEM_HOST) return read_status(c);
     return APTIDX_OK;
 }

@@ -209,11 +209,12 @@ __device__ __forceinline__ void lut_accumulate(const uint4 w, const float* row, 
     }
 }
 
+// With scores_out, Delta(g) of ROI r also goes to scores_out[r * ng + g].
 template <typename IdxT>
 __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, int64_t nroi, int32_t nv,
                                                 const IdxT* __restrict__ lut_t, int64_t ng, int64_t ng_pad,
                                                 const float* __restrict__ top_val, int32_t n_hat, int32_t* best,
-                                                float* score) {
+                                                float* score, float* scores_out) {
     constexpr int G = 16 / (int)sizeof(IdxT);
     extern __shared__ float sm[];
     float* row = sm;                     // nv
@@ -249,6 +250,11 @@ __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, 
                     bv = acc[e];
                     bg = (int32_t)(g0 + e);
                 }
+            if (scores_out) {
+#pragma unroll
+                for (int e = 0; e < G; ++e)
+                    if (g0 + e < ng) scores_out[r * ng + g0 + e] = acc[e];
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -269,9 +275,109 @@ __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, 
                     bv = red_v[w];
                     bg = red_g[w];
                 }
-            best[r] = bg;
+            if (best) best[r] = bg;
             if (score) score[r] = bv;
         }
+    }
+}
+
+// ---- the topk smallest Delta(g) of a ROI (ties: lower g), ascending ----------
+// One CTA per ROI: radix select of the topk-th smallest key (Delta >= 0, so
+// its FP32 bit pattern orders like the value) over four 8-bit digits, then
+// every g below that key plus the lowest-g ones equal to it, then a bitonic
+// sort of the (key, g) pairs.
+constexpr int kTopkThreads = 256;
+
+__global__ void __launch_bounds__(kTopkThreads) k_topk(const float* __restrict__ scores, int64_t ng, int64_t nroi,
+                                                       int32_t topk, int32_t* best, float* score) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint64_t sel[APTIDX_MAX_TOPK];
+    __shared__ uint32_t s_prefix, s_remaining, s_count;
+    __shared__ uint32_t warp_cnt[kTopkThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int kp = 1;
+    while (kp < topk) kp <<= 1;
+    for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
+        const uint32_t* key = reinterpret_cast<const uint32_t*>(scores + r * ng);
+        if (tid == 0) {
+            s_prefix = 0;
+            s_remaining = (uint32_t)topk;
+        }
+        // 1. radix select: the topk-th smallest key
+        for (int pass = 3; pass >= 0; --pass) {
+            for (int i = tid; i < 256; i += kTopkThreads) hist[i] = 0;
+            __syncthreads();
+            const uint32_t prefix = s_prefix;
+            const uint32_t hmask = pass == 3 ? 0u : (0xFFFFFFFFu << (8 * (pass + 1)));
+            for (int64_t g = tid; g < ng; g += kTopkThreads) {
+                const uint32_t k = key[g];
+                if ((k & hmask) == (prefix & hmask)) atomicAdd(&hist[(k >> (8 * pass)) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t rem = s_remaining, d = 0;
+                while (hist[d] < rem) {
+                    rem -= hist[d];
+                    ++d;
+                }
+                s_remaining = rem;
+                s_prefix = prefix | (d << (8 * pass));
+            }
+            __syncthreads();
+        }
+        const uint32_t kth = s_prefix;
+        const uint32_t need_eq = s_remaining;   // how many keys equal to kth are kept
+        const uint32_t n_less = (uint32_t)topk - need_eq;
+        // 2. every key below kth (any order), then the lowest-g keys equal to it
+        if (tid == 0) s_count = 0;
+        for (int i = tid; i < kp; i += kTopkThreads) sel[i] = ~0ull;
+        __syncthreads();
+        for (int64_t g = tid; g < ng; g += kTopkThreads) {
+            const uint32_t k = key[g];
+            if (k < kth) sel[atomicAdd(&s_count, 1u)] = ((uint64_t)k << 32) | (uint32_t)g;
+        }
+        __syncthreads();
+        uint32_t taken = 0;
+        for (int64_t g0 = 0; g0 < ng && taken < need_eq; g0 += kTopkThreads) {
+            const int64_t g = g0 + tid;
+            const bool eq = g < ng && key[g] == kth;
+            const uint32_t bal = __ballot_sync(0xffffffffu, eq);
+            if (lane == 0) warp_cnt[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+            for (int w = 0; w < kTopkThreads / 32; ++w) {
+                if (w < warp) before += warp_cnt[w];
+                total += warp_cnt[w];
+            }
+            const uint32_t rank = taken + before + __popc(bal & ((1u << lane) - 1u));
+            if (eq && rank < need_eq) sel[n_less + rank] = ((uint64_t)kth << 32) | (uint32_t)g;
+            taken += total;
+            __syncthreads();
+        }
+        __syncthreads();
+        // 3. bitonic sort of the kp slots (unused slots hold ~0)
+        for (int size = 2; size <= kp; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < kp; i += kTopkThreads) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const bool up = (i & size) == 0;
+                        const uint64_t a = sel[i], b = sel[j];
+                        if ((a > b) == up) {
+                            sel[i] = b;
+                            sel[j] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < topk; i += kTopkThreads) {
+            const uint64_t v = sel[i];
+            if (best) best[r * topk + i] = (int32_t)(uint32_t)v;
+            if (score) score[r * topk + i] = __uint_as_float((uint32_t)(v >> 32));
+        }
+        __syncthreads();
     }
 }
 
@@ -672,7 +778,8 @@ cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_
 }
 
 template <typename IdxT>
-static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score) {
+static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
+                                  float* scores_out) {
     constexpr int G = 16 / (int)sizeof(IdxT);
     const size_t smem = ((size_t)c->nv + r->n_hat) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_match<IdxT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -685,13 +792,22 @@ static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t 
     per_sm = std::max(per_sm, 1);
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, nroi);
     k_match<IdxT><<<(unsigned)grid, threads, smem, c->stream>>>(S, nroi, c->nv, static_cast<const IdxT*>(r->d_lut),
-                                                                r->ng, r->ng_pad, r->d_top_val, r->n_hat, best, score);
+                                                                r->ng, r->ng_pad, r->d_top_val, r->n_hat, best, score,
+                                                                scores_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score) {
-    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score)
-                             : launch_match_t<int32_t>(c, r, S, nroi, best, score);
+cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
+                         float* scores_out) {
+    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score, scores_out)
+                             : launch_match_t<int32_t>(c, r, S, nroi, best, score, scores_out);
+}
+
+cudaError_t launch_topk(Ctx* c, const float* scores, int64_t ng, int64_t nroi, int32_t topk, int32_t* best,
+                        float* score) {
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * 8, nroi);
+    k_topk<<<(unsigned)grid, kTopkThreads, 0, c->stream>>>(scores, ng, nroi, topk, best, score);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q0, const double* omega,

@@ -65,6 +65,8 @@ struct Ctx {
     float4* d_dirs_sorted = nullptr;
     float* d_gn_scratch = nullptr;   // one signature row per refinement CTA, in the order above
     size_t gn_scratch_bytes = 0;
+    float* d_match_scratch = nullptr;   // Eq. 3 scores of a chunk of ROIs (top-k matching)
+    size_t match_scratch_bytes = 0;
 
     // binning
     int m = 0;
@@ -186,7 +188,10 @@ size_t plain_smem_bytes(int m, int atom_cap);
 // indexing / refinement
 cudaError_t launch_top_nodes(Ctx* c, Reference* r);
 cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng);
-cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score);
+cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
+                         float* scores_out = nullptr);
+cudaError_t launch_topk(Ctx* c, const float* scores, int64_t ng, int64_t nroi, int32_t topk, int32_t* best,
+                        float* score);
 cudaError_t launch_lut_export(Ctx* c, Reference* r, int32_t* out);
 cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const double* q0, const double* omega,
                                int64_t nroi, float* loss, float* grad);

@@ -112,6 +112,44 @@ def test_match_parity(torch_cuda):
     ctx.close()
 
 
+@pytest.mark.parametrize("k", [1, 7, 64, 1000])
+def test_match_topk_parity(torch_cuda, k):
+    """Top-k of Eq. 3 (radix select per ROI): ascending scores, distinct
+    orientations, each score the oracle's Delta of its g within FP32
+    summation error, and the k smallest Delta values of the oracle."""
+    u = synth.icosphere(3)
+    sig = ref_node_sig(u)
+    n_hat = 100
+    grid = synth.so3_grid(8.0)
+    rng = np.random.default_rng(7)
+    S = _measured_set(u, rng, 12)
+    S[3] = 0.05                      # constant row: every g ties, so g = 0 .. k-1
+    ctx = context_with(torch_cuda, u, sig, n_hat)
+    apt.aptidx_build_lut(ctx.handle, 0, grid)
+    ng = grid.shape[0]
+    k = min(k, ng)
+    best = torch_cuda.empty((12, k), dtype=torch_cuda.int32, device="cuda")
+    score = torch_cuda.empty((12, k), dtype=torch_cuda.float32, device="cuda")
+    apt.aptidx_match_topk(ctx.handle, 0, torch_cuda.from_numpy(S).cuda(), k, best, score)
+    best = best.cpu().numpy()
+    score = score.cpu().numpy()
+    top = oracle.top_nodes(sig, n_hat)
+    L = oracle.lut(u, top, grid)
+    go, do = oracle.match_topk(S, sig, top, L, k)
+    _, _, sc = oracle.match(S, sig, top, L, return_scores=True)
+    for r in range(12):
+        assert len(np.unique(best[r])) == k and best[r].min() >= 0 and best[r].max() < ng
+        assert np.all(np.diff(score[r]) >= 0)
+        assert np.allclose(score[r], sc[r, best[r]], rtol=1e-5, atol=1e-6)
+        assert np.allclose(score[r], do[r], rtol=1e-5, atol=1e-6)
+    assert list(best[3]) == list(range(k))
+    b1 = np.empty(12, np.int32)
+    apt.aptidx_match(ctx.handle, 0, S, b1)
+    if k == 1:
+        assert np.array_equal(best[:, 0], b1)
+    ctx.close()
+
+
 def test_match_planted(torch_cuda):
     u = synth.icosphere(3)
     sig = ref_node_sig(u)

@@ -426,6 +426,32 @@ def test_match_recovers_planted_orientation():
     assert sc[0, g] == pytest.approx(float(np.sum((msr[0, L[g]].astype(float) - ref[top]) ** 2)), rel=1e-12)
 
 
+def test_match_topk_orders_solutions():
+    """Top-k of Eq. 3: the planted orientation first with Delta = 0, then the
+    rest ascending by (Delta, g) as a brute-force ranking of the hand-computed
+    Delta gives; k = 1 is the plain argmin; equal Delta keeps the lower g."""
+    u = synth.icosphere(3)
+    ref = synth.bump_values(synth.family_100(), 12.0, u)
+    ref = ref / ref.max()
+    top = oracle.top_nodes(ref, 60)
+    rng = np.random.default_rng(4)
+    Q = synth.random_quaternions(rng, 50)
+    L = oracle.lut(u, top, Q)
+    gstar = next(g for g in range(10, 50) if len(np.unique(L[g])) == len(top))
+    msr = np.full((2, u.shape[0]), 0.05, np.float32)
+    msr[0, L[gstar]] = ref[top]
+    g, d = oracle.match_topk(msr, ref, top, L, 7)
+    assert g[0, 0] == gstar and d[0, 0] == 0.0
+    hand = [(float(np.sum((msr[0, L[h]].astype(float) - ref[top]) ** 2)), h) for h in range(Q.shape[0])]
+    assert [h for _, h in sorted(hand)[:7]] == list(g[0])
+    assert np.all(np.diff(d[0]) >= 0)
+    best, _ = oracle.match(msr, ref, top, L)
+    g1, _ = oracle.match_topk(msr, ref, top, L, 1)
+    assert np.array_equal(g1[:, 0], best)
+    # a constant measured signature gives every g the same Delta: ties keep g order
+    assert list(g[1]) == list(range(7))
+
+
 def test_match_indexes_rotated_crystal_end_to_end():
     """Signatures of a rotated perfect f.c.c. ROI, matched against the
     unrotated reference over a test-orientation set that contains the true
