@@ -339,9 +339,26 @@ def so3_grid(step_deg: float = 5.0, oversample: int = 16) -> np.ndarray:
                   np.sqrt(1 - u1) * np.sin(2 * np.pi * u2),
                   np.sqrt(1 - u1) * np.cos(2 * np.pi * u2),
                   np.sqrt(u1) * np.sin(2 * np.pi * u3)], axis=1)
-    sym = cubic_rotation_matrices()
-    symq = np.array([_matrix_to_quat(m) for m in sym])
-    # q_fz = q * s for the s maximising |w|
+    best = _reduce_cubic_fz(q)
+    # greedy thinning in the chordal metric of the 4-vectors (monotone in angle)
+    chord = 2 * math.sin(theta / 4)  # |q1 - q2| for rotation angle theta
+    tree = cKDTree(best)
+    taken = np.zeros(len(best), bool)
+    blocked = np.zeros(len(best), bool)
+    for i in range(len(best)):
+        if blocked[i]:
+            continue
+        taken[i] = True
+        for j in tree.query_ball_point(best[i], chord):
+            blocked[j] = True
+    return np.ascontiguousarray(best[taken])
+
+
+def _reduce_cubic_fz(q: np.ndarray) -> np.ndarray:
+    """Each quaternion's symmetry-equivalent q * s (s one of the 24 proper
+    cubic rotations) with the largest |w|, sign-fixed to w >= 0: the cubic
+    fundamental-zone representative."""
+    symq = np.array([_matrix_to_quat(m) for m in cubic_rotation_matrices()])
     best = None
     bestw = None
     for s in symq:
@@ -357,18 +374,35 @@ def so3_grid(step_deg: float = 5.0, oversample: int = 16) -> np.ndarray:
             best[upd] = qs[upd]
             bestw[upd] = w[upd]
     best[best[:, 0] < 0] *= -1
-    # greedy thinning in the chordal metric of the 4-vectors (monotone in angle)
-    chord = 2 * math.sin(theta / 4)  # |q1 - q2| for rotation angle theta
-    tree = cKDTree(best)
-    taken = np.zeros(len(best), bool)
-    blocked = np.zeros(len(best), bool)
-    for i in range(len(best)):
-        if blocked[i]:
-            continue
-        taken[i] = True
-        for j in tree.query_ball_point(best[i], chord):
-            blocked[j] = True
-    return np.ascontiguousarray(best[taken])
+    return best
+
+
+def so3_halton_fz(n: int, skip: int = 1) -> np.ndarray:
+    """n quasi-uniform orientations in the cubic fundamental zone: the Halton
+    points (bases 2, 3, 5) from index `skip` on, through Shoemake's
+    volume-preserving map [0,1)^3 -> SO(3), reduced to the fundamental zone.
+    A fast stand-in at the size of the paper's 1-degree set (n = 618324,
+    Section 2.3) where greedy thinning (so3_grid) is too slow; no minimum
+    separation is enforced.  float64 [n, 4] (w, x, y, z), w >= 0."""
+    idx = np.arange(skip, skip + n)
+    u1, u2, u3 = _halton_idx(idx, 2), _halton_idx(idx, 3), _halton_idx(idx, 5)
+    q = np.stack([np.sqrt(u1) * np.cos(2 * np.pi * u3),
+                  np.sqrt(1 - u1) * np.sin(2 * np.pi * u2),
+                  np.sqrt(1 - u1) * np.cos(2 * np.pi * u2),
+                  np.sqrt(u1) * np.sin(2 * np.pi * u3)], axis=1)
+    return np.ascontiguousarray(_reduce_cubic_fz(q))
+
+
+def _halton_idx(idx: np.ndarray, base: int) -> np.ndarray:
+    """Radical inverse of the integers idx in `base` (vectorised)."""
+    out = np.zeros(idx.shape[0])
+    f = 1.0 / base
+    i = idx.astype(np.int64).copy()
+    while np.any(i > 0):
+        out += f * (i % base)
+        i //= base
+        f /= base
+    return out
 
 
 def _matrix_to_quat(m) -> np.ndarray:
