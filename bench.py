@@ -51,7 +51,12 @@ def parse():
     ap.add_argument("--path", default="auto", choices=["auto", "tc", "plain"])
     ap.add_argument("--cpu-rois", type=int, default=0, help="oracle sample size (0: sized for ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="bcc", choices=["bcc", "polycrystal"],
+                    help="bcc: the timed step; polycrystal: signature throughput of both paths on the "
+                         "uneven-ROI polycrystal (1e5 ROIs, per-ROI bands), not a step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-paper-index", action="store_true",
+                    help="skip the paper-scale indexing measurement (618324 orientations, top-1000)")
     ap.add_argument("--rois", type=int, default=0,
                     help="use only the first N ROIs (a smaller case for profiling; 0: all 8192)")
     return ap.parse_args()
@@ -360,6 +365,34 @@ def run_gb300(args):
                        "gather_ms": pprof["gather"][0] / max(pprof["gather"][1], 1),
                        "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
 
+    # paper-scale indexing (not part of the step): the 1-degree-sized set of
+    # 618324 orientations, n_hat = 1000, the 1000 best solutions per ROI
+    paper_index = None
+    if not args.no_paper_index:
+        full_step(headline)                                       # normalised signatures in S
+        Qp = synth.so3_halton_fz(618324)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        apt.aptidx_set_reference(h, 1, node_sig, n_hat, None)
+        ev[0].record(stream)
+        apt.aptidx_build_lut(h, 1, torch.from_numpy(Qp).cuda())
+        ev[1].record(stream)
+        n_pi = min(nroi, 1024)
+        S_pi = S[:n_pi]
+        b_pi = torch.empty((n_pi, 1000), dtype=torch.int32, device="cuda")
+        s_pi = torch.empty((n_pi, 1000), dtype=torch.float32, device="cuda")
+        apt.aptidx_match_topk(h, 1, S_pi, 1000, b_pi, s_pi)     # warm-up
+        ev[2].record(stream)
+        apt.aptidx_match_topk(h, 1, S_pi, 1000, b_pi, s_pi)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        lut_s = ev[0].elapsed_time(ev[1]) / 1e3
+        m_ms = ev[2].elapsed_time(ev[3])
+        paper_index = {"orientations": int(Qp.shape[0]), "n_hat": n_hat, "topk": 1000, "rois": n_pi,
+                       "lut_build_s": lut_s, "match_topk_ms": m_ms,
+                       "lookups_per_s": n_pi * Qp.shape[0] * n_hat / (m_ms / 1e3),
+                       "rois_per_s": n_pi / (m_ms / 1e3),
+                       "set": "Halton points through Shoemake's map, reduced to the cubic fundamental zone"}
+
     # roofline of the dominant kernel (the signature kernel of the headline path)
     sig_ms = prof["signature"][0] / max(prof["signature"][1], 1)
     K = band[1] - band[0] + 1
@@ -451,6 +484,7 @@ def run_gb300(args):
                          "p90_misorientation_deg": float(np.percentile(mis, 90)),
                          "frac_below_0p5_deg": float((mis <= 0.5).mean()),
                          "median_coarse_match_deg": float(np.median(mis_coarse))},
+            "paper_scale_indexing": paper_index,
             "roofline": roof,
             "clocks": clk,
             "gpu_launches": int(launches),
@@ -463,10 +497,69 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def run_polycrystal(args):
+    """Signature throughput of both paths on the Voronoi polycrystal: 60 x 60 x
+    120 nm, 200 f.c.c. grains with L1_2 precipitates (1.3e7 atoms), 1e5 ROIs
+    with radii uniform in [1.0, 2.5] nm, per-ROI {200} bands, 40962
+    directions, 2^10 bins; autotuned launch and graph replay."""
+    import torch
+    import synth
+    import paper_2009_00735_gb300 as apt
+    from paper_2009_00735_gb300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    w = synth.polycrystal()
+    nroi, nv = w.centres.shape[0], w.dirs.shape[0]
+    blo = np.empty(nroi, np.int32)
+    bhi = np.empty(nroi, np.int32)
+    for i, R in enumerate(w.radii):
+        blo[i], bhi[i] = apt.band_for_spacing(*w.d_spacing, float(R), w.m)
+    stream = torch.cuda.current_stream()
+    ctx = apt.Context(0, stream)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(w.xyz).cuda(), torch.from_numpy(w.types).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(w.dirs).cuda())
+    apt.aptidx_set_binning(h, w.m, int(blo.min()), int(bhi.max()))
+    apt.aptidx_set_rois(h, torch.from_numpy(w.centres).cuda(), torch.from_numpy(w.radii).cuda(),
+                        torch.from_numpy(blo).cuda(), torch.from_numpy(bhi).cuda())
+    S = torch.empty((nroi, nv), dtype=torch.float32, device="cuda")
+    N = torch.empty(nroi, dtype=torch.int32, device="cuda")
+    apt.aptidx_compute_signatures(h, apt.APTIDX_PATH_PLAIN_FP32, 0, S, None, N)
+    apt.aptidx_sync(h)
+    n_atoms = N.cpu().numpy().astype(np.int64)
+    out = {}
+    flags = apt.APTIDX_AUTOTUNE | apt.APTIDX_GRAPH
+    for name, code in (("plain", apt.APTIDX_PATH_PLAIN_FP32), ("tc", apt.APTIDX_PATH_TC_FP16)):
+        for _ in range(args.warmup):
+            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
+        apt.aptidx_sync(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        tpi, iss = apt.aptidx_get_tuning(h, code)
+        out[name] = {"ms_per_call": ms, "value": nroi * nv / (ms / 1e3),
+                     "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
+    print(json.dumps({
+        "metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": w.name, "n_roi": nroi, "n_dir": nv, "bins": 1 << w.m, "atoms": int(w.xyz.shape[0]),
+                   "atoms_per_roi": {"mean": float(n_atoms.mean()), "min": int(n_atoms.min()),
+                                     "max": int(n_atoms.max()), "above_2048": int((n_atoms > 2048).sum())},
+                   "bands": [int(blo.min()), int(bhi.max())], "pairs": int(n_atoms.sum()) * nv},
+        "paths": out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "polycrystal":
+        run_polycrystal(args)
     else:
         run_gb300(args)
 

@@ -1,6 +1,6 @@
-"""Precision of the wide-band spectrum on the b.c.c. single crystal (4.33 M
-atoms, 8192 ROIs of R = 2 nm, 40962 directions, 2^10 bins) with the signature
-taken over frequency bins 8..128 instead of the {110} band.
+"""Precision of the band spectrum on the b.c.c. single crystal (4.33 M atoms,
+8192 ROIs of R = 2 nm, 40962 directions, 2^10 bins), with the signature taken
+over frequency bins 8..128 and over the {110} band (k = 18..21).
 
 Three arithmetic paths of Eq. 1 + the amplitude spectrum are compared per ROI,
 e = max_v |S - S_ref| / max_v S_ref:
@@ -21,11 +21,12 @@ from test_gpu_plain import TOL_PLAIN, gpu_signatures, make_ctx, roi_error, singl
 pytestmark = pytest.mark.gpu
 
 TOL_TC = 5e-3
-BAND = (8, 128)
 
 
-def test_wide_band_precision(torch_cuda, single_crystal):
+@pytest.mark.parametrize("which", ["wide", "110"])
+def test_band_precision(torch_cuda, single_crystal, which):
     w = single_crystal
+    BAND = (8, 128) if which == "wide" else oracle.band_for_spacing(*w.d_spacing, float(w.radii[0]), w.m)
     ctx, band, m, d = make_ctx(torch_cuda, w, band=BAND)
     nroi, nv = w.centres.shape[0], d.shape[0]
     St, At, Nt = gpu_signatures(torch_cuda, ctx, nroi, nv, path=apt.APTIDX_PATH_TC_FP16)
@@ -45,7 +46,7 @@ def test_wide_band_precision(torch_cuda, single_crystal):
         e_t.append(roi_error(St[r, vs], So))
         e_p.append(roi_error(Sp[r, vs], So))
     e_t, e_p = np.array(e_t), np.array(e_p)
-    print(f"\nwide band {BAND[0]}..{BAND[1]}, {rois.size} ROIs x {vs.size} directions vs FP64 oracle: "
+    print(f"\nband {BAND[0]}..{BAND[1]}, {rois.size} ROIs x {vs.size} directions vs FP64 oracle: "
           f"tensor cores max {e_t.max():.3e} median {np.median(e_t):.3e}; "
           f"FP32 max {e_p.max():.3e} median {np.median(e_p):.3e}; "
           f"tensor cores vs FP32 over all {nroi} ROIs x {nv} directions: max {e_tp.max():.3e} "
