@@ -91,12 +91,26 @@ __device__ __forceinline__ void hist_tile(uint32_t* H, const float4* A, int cn, 
                                           float4 d1, float scale, float magic, int nbm1) {
     const uint32_t hbase = smem_u32(H) + 4u * (uint32_t)lane;
     int j = warp;
-    for (; j + 3 * W < cn; j += 4 * W) {
-        const float4 a0 = A[j], a1 = A[j + W], a2 = A[j + 2 * W], a3 = A[j + 3 * W];
+    if (j + 3 * W < cn) {
+        // groups of four atoms, the next group's loads issued before the
+        // current group's increments
+        float4 a0 = A[j], a1 = A[j + W], a2 = A[j + 2 * W], a3 = A[j + 3 * W];
+        for (; j + 7 * W < cn; j += 4 * W) {
+            const float4 b0 = A[j + 4 * W], b1 = A[j + 5 * W], b2 = A[j + 6 * W], b3 = A[j + 7 * W];
+            hist_add_atom<kMasked>(hbase, a0, d0, d1, scale, magic, nbm1);
+            hist_add_atom<kMasked>(hbase, a1, d0, d1, scale, magic, nbm1);
+            hist_add_atom<kMasked>(hbase, a2, d0, d1, scale, magic, nbm1);
+            hist_add_atom<kMasked>(hbase, a3, d0, d1, scale, magic, nbm1);
+            a0 = b0;
+            a1 = b1;
+            a2 = b2;
+            a3 = b3;
+        }
         hist_add_atom<kMasked>(hbase, a0, d0, d1, scale, magic, nbm1);
         hist_add_atom<kMasked>(hbase, a1, d0, d1, scale, magic, nbm1);
         hist_add_atom<kMasked>(hbase, a2, d0, d1, scale, magic, nbm1);
         hist_add_atom<kMasked>(hbase, a3, d0, d1, scale, magic, nbm1);
+        j += 4 * W;
     }
     for (; j < cn; j += W) hist_add_atom<kMasked>(hbase, A[j], d0, d1, scale, magic, nbm1);
 }
