@@ -156,6 +156,25 @@ int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii,
 int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* S, uint16_t* argk,
                               int32_t* n_atoms, int mem);
 
+/* Several signatures per ROI in one call (Section 3.1: signatures per atom
+ * type and per lattice-plane family distinguish crystal structures; the
+ * aluminium bicrystal uses {002}, {220} and {111} signatures).  Signature s
+ * uses the ROI atoms whose type bit is set in type_mask[s] and the
+ * frequency band [k_lo[s], k_hi[s]] (the same band for every ROI).
+ * Signatures with the same type mask share one gather and one spectrum
+ * contraction over the union of their bands, up to APTIDX_MAX_BANDS bands
+ * per contraction, the band maxima taken in the kernels' epilogue.
+ * type_mask, k_lo, k_hi: host arrays of n_sig (1 <= n_sig <= 64).
+ * S: n_sig x nroi x nv FP32 (signature-major); argk: same shape uint16
+ * (NULL to skip); n_atoms: n_sig x nroi int32 (NULL to skip); these three
+ * in `mem`.
+ * flags: APTIDX_NORMALISE_MAX or 0.  The context's ROI bands and type mask
+ * are left as they were.  Errors: INVALID_ARG, STATE, OOM, CUDA, TIMEOUT. */
+#define APTIDX_MAX_BANDS 4
+int aptidx_compute_signatures_multi(aptidx_ctx* ctx, int path, unsigned flags, int32_t n_sig,
+                                    const uint32_t* type_mask, const int32_t* k_lo, const int32_t* k_hi, float* S,
+                                    uint16_t* argk, int32_t* n_atoms, int mem);
+
 /* Debug/parity: the 2^m-bin histograms of ROI `roi` for every direction, as
  * computed by the histogram stage of `path` (same kernel code).  h: nv x 2^m
  * u16 in `mem`. */

@@ -22,7 +22,7 @@ __all__ = [
     "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
-    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_refine_loss", "aptidx_refine",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
@@ -31,6 +31,7 @@ __all__ = [
 
 APTIDX_OK = 0
 APTIDX_MAX_TOPK = 1024
+APTIDX_MAX_BANDS = 4
 APTIDX_E_INVALID_ARG = 1
 APTIDX_E_CUDA = 2
 APTIDX_E_OOM = 3
@@ -76,6 +77,8 @@ _SIGS = {
     "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_match_topk": (C.c_int, [_vp, _i32, _vp, _i64, _i32, _vp, _vp, C.c_int]),
+    "aptidx_compute_signatures_multi": (C.c_int, [_vp, C.c_int, C.c_uint, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                  C.c_int]),
     "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_refine": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_path_supported": (C.c_int, [_vp, C.c_int]),
@@ -246,6 +249,23 @@ def aptidx_compute_signatures(ctx, path: int, flags: int, S=None, argk=None, n_a
     pA, mA = _out(argk, np.uint16)
     pN, mN = _out(n_atoms, np.int32)
     _check(ctx, load().aptidx_compute_signatures(ctx, path, flags, pS, pA, pN, _one_mem(mS, mA, mN)))
+
+
+def aptidx_compute_signatures_multi(ctx, path: int, flags: int, type_masks, k_lo, k_hi, S, argk=None, n_atoms=None):
+    """Several signatures per ROI: S[s, roi, v] for signature s with atom
+    types type_masks[s] and band [k_lo[s], k_hi[s]] (host sequences)."""
+    tm = np.ascontiguousarray(np.asarray(type_masks, dtype=np.uint32))
+    lo = np.ascontiguousarray(np.asarray(k_lo, dtype=np.int32))
+    hi = np.ascontiguousarray(np.asarray(k_hi, dtype=np.int32))
+    n_sig = tm.size
+    if lo.size != n_sig or hi.size != n_sig:
+        raise ValueError("type_masks, k_lo and k_hi need the same length")
+    pS, mS = _out(S, np.float32)
+    pA, mA = _out(argk, np.uint16)
+    pN, mN = _out(n_atoms, np.int32)
+    _check(ctx, load().aptidx_compute_signatures_multi(ctx, path, flags, n_sig, tm.ctypes.data_as(_vp),
+                                                       lo.ctypes.data_as(_vp), hi.ctypes.data_as(_vp), pS, pA, pN,
+                                                       _one_mem(mS, mA, mN)))
 
 
 def aptidx_get_histograms(ctx, roi: int, path: int, h):

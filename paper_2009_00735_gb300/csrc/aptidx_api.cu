@@ -1115,6 +1115,126 @@ int aptidx_match_topk(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nro
     return APTIDX_OK;
 }
 
+// Several signatures per ROI: signatures are grouped by type mask (one gather
+// each) and their bands by up to APTIDX_MAX_BANDS per contraction; the ROI
+// band of a pass spans the union of its bands, the kernels' epilogue takes
+// each band's maximum and writes it to that signature's slab of S.
+int aptidx_compute_signatures_multi(aptidx_ctx* ctx, int path, unsigned flags, int32_t n_sig,
+                                    const uint32_t* type_mask, const int32_t* k_lo, const int32_t* k_hi, float* S,
+                                    uint16_t* argk, int32_t* n_atoms, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "compute_signatures_multi: set ROIs first");
+    if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
+        return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
+    if (flags & ~APTIDX_NORMALISE_MAX) return set_error(c, APTIDX_E_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (n_sig < 1 || n_sig > 64 || !type_mask || !k_lo || !k_hi || !S)
+        return set_error(c, APTIDX_E_INVALID_ARG, "compute_signatures_multi: need 1 <= n_sig <= 64, masks, bands, S");
+    const int half = 1 << (c->m - 1);
+    for (int s = 0; s < n_sig; ++s)
+        if (k_lo[s] < 0 || k_hi[s] < k_lo[s] || k_hi[s] > half)
+            return set_error(c, APTIDX_E_INVALID_ARG, "signature %d: band [%d, %d] outside [0, %d]", s, k_lo[s], k_hi[s],
+                             half);
+    const int64_t nS = c->nroi * (int64_t)c->nv;
+    DevTmp tS, tA, tN;
+    float* dS;
+    uint16_t* dA;
+    int32_t* dN;
+    if ((rc = dev_out(c, S, (size_t)n_sig * nS, mem, tS, &dS))) return rc;
+    if ((rc = dev_out(c, argk, (size_t)n_sig * nS, mem, tA, &dA))) return rc;
+    if ((rc = dev_out(c, n_atoms, (size_t)n_sig * c->nroi, mem, tN, &dN))) return rc;
+
+    // passes: signatures with the same type mask, in order of first use, in
+    // groups of up to APTIDX_MAX_BANDS
+    std::vector<std::vector<int>> passes;
+    {
+        std::vector<bool> used((size_t)n_sig, false);
+        for (int s = 0; s < n_sig; ++s) {
+            if (used[s]) continue;
+            std::vector<int> grp;
+            for (int t = s; t < n_sig; ++t)
+                if (!used[t] && type_mask[t] == type_mask[s]) {
+                    grp.push_back(t);
+                    used[t] = true;
+                }
+            for (size_t i = 0; i < grp.size(); i += APTIDX_MAX_BANDS)
+                passes.emplace_back(grp.begin() + i, grp.begin() + std::min(grp.size(), i + APTIDX_MAX_BANDS));
+        }
+    }
+    // the context's ROI bands and type mask are restored afterwards; cached
+    // graphs may hold the B operand of other bands, so they are dropped
+    clear_graphs(c);
+    const uint32_t mask0 = c->type_mask;
+    const std::vector<int32_t> band0 = c->h_band;
+    const int32_t bmin0 = c->band_min, bmax0 = c->band_max;
+    auto restore = [&]() {
+        c->multi = BandSet();
+        c->type_mask = mask0;
+        c->h_band = band0;
+        c->band_min = bmin0;
+        c->band_max = bmax0;
+        cudaMemcpyAsync(c->d_band, band0.data(), band0.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        clear_graphs(c);
+    };
+    std::vector<int32_t> band((size_t)c->nroi * 2);
+    for (const auto& ps : passes) {
+        int lo_u = half, hi_u = 0;
+        BandSet bs;
+        bs.n = (int)ps.size();
+        for (int b = 0; b < bs.n; ++b) {
+            bs.lo[b] = k_lo[ps[b]];
+            bs.hi[b] = k_hi[ps[b]];
+            bs.off[b] = (int64_t)ps[b] * nS;
+            lo_u = std::min(lo_u, bs.lo[b]);
+            hi_u = std::max(hi_u, bs.hi[b]);
+        }
+        for (int64_t r = 0; r < c->nroi; ++r) {
+            band[2 * r] = lo_u;
+            band[2 * r + 1] = hi_u;
+        }
+        c->type_mask = type_mask[ps[0]];
+        c->h_band = band;
+        c->band_min = lo_u;
+        c->band_max = hi_u;
+        c->multi = bs;
+        cudaError_t e = cudaMemcpyAsync(c->d_band, band.data(), band.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // the host band vector is reused
+        if (e != cudaSuccess) {
+            restore();
+            return cuda_check(c, e, "band upload");
+        }
+        if (path == APTIDX_PATH_TC_FP16 && (rc = prepare_tc(c))) {
+            restore();
+            return rc;
+        }
+        if ((rc = launch_sequence(c, path, 0, dS, dA))) {
+            restore();
+            return rc;
+        }
+        if (dN)
+            for (int b = 0; b < bs.n; ++b)
+                cudaMemcpyAsync(dN + (int64_t)ps[b] * c->nroi, c->d_nw, (size_t)c->nroi * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (flags & APTIDX_NORMALISE_MAX) {
+        prof_begin(c, APTIDX_PHASE_NORMALISE);
+        cudaError_t e = launch_normalise(c, dS, (int64_t)n_sig * c->nroi);
+        if (e != cudaSuccess) {
+            restore();
+            return cuda_check(c, e, "normalise");
+        }
+        prof_end(c, APTIDX_PHASE_NORMALISE, 1);
+    }
+    restore();
+    if ((rc = copy_back(c, S, dS, (size_t)n_sig * nS, mem))) return rc;
+    if ((rc = copy_back(c, argk, dA, (size_t)n_sig * nS, mem))) return rc;
+    if ((rc = copy_back(c, n_atoms, dN, (size_t)n_sig * c->nroi, mem))) return rc;
+    return read_status(c);
+}
+
 int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const double* omega,
                        int64_t nroi, float* loss, float* grad, int mem) {
     CTX_OR_FAIL(ctx);

@@ -127,6 +127,32 @@ __device__ __forceinline__ void hist_export(const uint32_t* H, int NB, int tile,
     }
 }
 
+// Band maxima of one direction: frequency f with amplitude a updates every
+// band holding f (strictly greater, so with f ascending ties keep the lowest
+// f).  bs.n == 0: the single band [klo, khi] of the ROI.
+__device__ __forceinline__ int band_count(const BandSet& bs) { return bs.n == 0 ? 1 : bs.n; }
+
+__device__ __forceinline__ void band_init(const BandSet& bs, int klo, float* best, int* bk) {
+#pragma unroll
+    for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
+        best[b] = -1.f;
+        bk[b] = bs.n == 0 ? klo : bs.lo[b];
+    }
+}
+
+__device__ __forceinline__ void band_update(const BandSet& bs, int klo, int khi, int f, float a, float* best,
+                                            int* bk) {
+    const int nb = band_count(bs);
+#pragma unroll
+    for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
+        const int lo = bs.n == 0 ? klo : bs.lo[b], hi = bs.n == 0 ? khi : bs.hi[b];
+        if (b < nb && f >= lo && f <= hi && a > best[b]) {
+            best[b] = a;
+            bk[b] = f;
+        }
+    }
+}
+
 // ROI rank ranges of a signature launch (ranks index the longest-first order)
 constexpr int kRanksAll = 0;       // [0, nroi)
 constexpr int kRanksBig = 1;       // [0, n_big): ROIs above 2048 atoms

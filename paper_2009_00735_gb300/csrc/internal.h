@@ -22,6 +22,15 @@ constexpr int kStatusTimeout = 1;
 constexpr int kStatusOverflow = 2;
 constexpr int kStatusInvalid = 4;
 
+// Bands whose maxima one signature pass takes (aptidx_compute_signatures_multi);
+// n == 0: the ROI's own band only.  Band b is written at S + off[b] (elements).
+struct BandSet {
+    int n = 0;
+    int lo[APTIDX_MAX_BANDS] = {0, 0, 0, 0};
+    int hi[APTIDX_MAX_BANDS] = {0, 0, 0, 0};
+    int64_t off[APTIDX_MAX_BANDS] = {0, 0, 0, 0};
+};
+
 struct Reference {
     float* d_node_sig = nullptr;   // [nv] normalised reference signature
     int32_t* d_top = nullptr;      // [n_hat] strongest nodes, strongest first
@@ -65,6 +74,7 @@ struct Ctx {
     float4* d_dirs_sorted = nullptr;
     float* d_gn_scratch = nullptr;   // one signature row per refinement CTA, in the order above
     size_t gn_scratch_bytes = 0;
+    BandSet multi;                       // bands of the current pass (multi-signature calls)
     float* d_match_scratch = nullptr;   // Eq. 3 scores of a chunk of ROIs (top-k matching)
     size_t match_scratch_bytes = 0;
 
@@ -182,7 +192,7 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
                                  int64_t hist_roi);
 int prepare_tc(Ctx* c);
 bool tc_supported(Ctx* c);
-cudaError_t launch_normalise(Ctx* c, float* S);
+cudaError_t launch_normalise(Ctx* c, float* S, int64_t rows = -1);   // rows of nv values; -1: nroi
 size_t plain_smem_bytes(int m, int atom_cap);
 
 // indexing / refinement

@@ -53,6 +53,7 @@ struct SigParams {
     const int32_t* n_big;
     int rank_mode;
     int64_t nroi;
+    BandSet bands;
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
@@ -160,8 +161,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                 __syncthreads();
                 if (tid < kDirs) {
                     const int64_t v = (int64_t)tile * kDirs + tid;
-                    float best = -1.f;
-                    int bk = klo;
+                    float best[APTIDX_MAX_BANDS];
+                    int bk[APTIDX_MAX_BANDS];
+                    band_init(p.bands, klo, best, bk);
                     for (int kk = 0; kk < K; ++kk) {
                         const int g = kk / kKpw, q = kk % kKpw;
                         float sr = 0.f, si = 0.f;
@@ -170,20 +172,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                             sr += t.x;
                             si += t.y;
                         }
-                        const float a = sqrtf(sr * sr + si * si);
-                        if (a > best) {
-                            best = a;
-                            bk = klo + kk;
-                        }
+                        band_update(p.bands, klo, khi, klo + kk, sqrtf(sr * sr + si * si), best, bk);
                     }
                     if (v < p.nv) {
-                        p.S[out_base + tid] = best;
-                        if (p.argk) p.argk[out_base + tid] = (uint16_t)bk;
+#pragma unroll
+                        for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
+                            if (b < band_count(p.bands)) {
+                                p.S[p.bands.off[b] + out_base + tid] = best[b];
+                                if (p.argk) p.argk[p.bands.off[b] + out_base + tid] = (uint16_t)bk[b];
+                            }
+                        }
                     }
                 }
             } else {
-                float b0 = -1.f, b1 = -1.f;
-                int bk0 = klo, bk1 = klo;
+                float b0[APTIDX_MAX_BANDS], b1[APTIDX_MAX_BANDS];
+                int bk0[APTIDX_MAX_BANDS], bk1[APTIDX_MAX_BANDS];
+                band_init(p.bands, klo, b0, bk0);
+                band_init(p.bands, klo, b1, bk1);
                 for (int g = warp; g < G; g += kWarps) {
                     const int k0 = klo + g * kKpw;
                     float re[kKpw][2], im[kKpw][2];
@@ -211,28 +216,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                         if (k0 + q > khi) break;
                         const float a0 = sqrtf(re[q][0] * re[q][0] + im[q][0] * im[q][0]);
                         const float a1 = sqrtf(re[q][1] * re[q][1] + im[q][1] * im[q][1]);
-                        if (a0 > b0) { b0 = a0; bk0 = k0 + q; }
-                        if (a1 > b1) { b1 = a1; bk1 = k0 + q; }
+                        band_update(p.bands, klo, khi, k0 + q, a0, b0, bk0);
+                        band_update(p.bands, klo, khi, k0 + q, a1, b1, bk1);
                     }
                 }
-                PART[(size_t)warp * kDirs + 2 * lane] = make_float2(b0, __int_as_float(bk0));
-                PART[(size_t)warp * kDirs + 2 * lane + 1] = make_float2(b1, __int_as_float(bk1));
+                // per band, each warp's best over its frequency groups; the
+                // band's slab of PART holds kWarps x kDirs (value, k) pairs
+#pragma unroll
+                for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
+                    if (b < band_count(p.bands)) {
+                        PART[((size_t)b * kWarps + warp) * kDirs + 2 * lane] = make_float2(b0[b], __int_as_float(bk0[b]));
+                        PART[((size_t)b * kWarps + warp) * kDirs + 2 * lane + 1] =
+                            make_float2(b1[b], __int_as_float(bk1[b]));
+                    }
+                }
                 __syncthreads();
                 if (tid < kDirs) {
                     const int64_t v = (int64_t)tile * kDirs + tid;
-                    float best = -1.f;
-                    int bk = klo;
-                    for (int w = 0; w < kWarps; ++w) {
-                        const float2 t = PART[(size_t)w * kDirs + tid];
-                        const int k = __float_as_int(t.y);
-                        if (t.x > best || (t.x == best && k < bk)) {
-                            best = t.x;
-                            bk = k;
+                    for (int b = 0; b < band_count(p.bands); ++b) {
+                        float best = -1.f;
+                        int bk = p.bands.n == 0 ? klo : p.bands.lo[b];
+                        for (int w = 0; w < kWarps; ++w) {
+                            const float2 t = PART[((size_t)b * kWarps + w) * kDirs + tid];
+                            const int k = __float_as_int(t.y);
+                            if (t.x > best || (t.x == best && k < bk)) {
+                                best = t.x;
+                                bk = k;
+                            }
                         }
-                    }
-                    if (v < p.nv) {
-                        p.S[out_base + tid] = best;
-                        if (p.argk) p.argk[out_base + tid] = (uint16_t)bk;
+                        if (v < p.nv) {
+                            p.S[p.bands.off[b] + out_base + tid] = best;
+                            if (p.argk) p.argk[p.bands.off[b] + out_base + tid] = (uint16_t)bk;
+                        }
                     }
                 }
             }
@@ -258,9 +273,10 @@ __global__ void __launch_bounds__(256) k_normalise(float* S, int32_t nv) {
 
 }  // namespace
 
-cudaError_t launch_normalise(Ctx* c, float* S) {
-    if (c->nroi <= 0) return cudaSuccess;
-    k_normalise<<<(unsigned)c->nroi, 256, 0, c->stream>>>(S, c->nv);
+cudaError_t launch_normalise(Ctx* c, float* S, int64_t rows) {
+    if (rows < 0) rows = c->nroi;
+    if (rows <= 0) return cudaSuccess;
+    k_normalise<<<(unsigned)rows, 256, 0, c->stream>>>(S, c->nv);
     return cudaGetLastError();
 }
 
@@ -310,6 +326,7 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     p.n_big = c->d_counter + 1;
     p.rank_mode = hist_out ? kRanksAll : rank_mode;
     p.nroi = nroi_lim;
+    p.bands = hist_out ? BandSet() : c->multi;
     if ((e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);

@@ -71,6 +71,7 @@ struct TcParams {
     int* status;
     int atom_cap;
     int n_iss;              // MMA issuer warps (1 .. kIssuers)
+    BandSet bands;
 };
 
 // ---- tcgen05 / descriptor helpers -------------------------------------------
@@ -334,8 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 // warps 0, 1 hold rows 0-63 (bins of the first half), warps
                 // 2, 3 rows 64-127; per frequency group the second-half warps
                 // hand their sums over through shared memory
-                float best = -1.f;
-                int bk = klo;
+                float best[APTIDX_MAX_BANDS];
+                int bk[APTIDX_MAX_BANDS];
+                band_init(p.bands, klo, best, bk);
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
                 const int n_iss = nbatch == 1 ? p.n_iss : 1;
                 const uint32_t cols_b = (uint32_t)(16 * p.gb);
@@ -372,11 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                                 const float sg = (f & 1) ? -1.f : 1.f;
                                 const float xr = re[q] + sg * EX[dir * 8 + 2 * q];
                                 const float xi = im[q] + sg * EX[dir * 8 + 2 * q + 1];
-                                const float a = sqrtf(xr * xr + xi * xi) * 16777216.0f;
-                                if (f >= klo && f <= khi && a > best) {
-                                    best = a;
-                                    bk = f;
-                                }
+                                band_update(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f, best, bk);
                             }
                         }
                         asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -386,8 +384,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     const int64_t v = (int64_t)tile * kDirs + dir;
                     if (v < p.nv) {
                         const int64_t o = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv + v;
-                        p.S[o] = best;
-                        if (p.argk) p.argk[o] = (uint16_t)bk;
+#pragma unroll
+                        for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
+                            if (b < band_count(p.bands)) {
+                                p.S[p.bands.off[b] + o] = best[b];
+                                if (p.argk) p.argk[p.bands.off[b] + o] = (uint16_t)bk[b];
+                            }
+                        }
                     }
                 }
             }
@@ -534,6 +537,7 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     p.status = c->d_status;
     p.atom_cap = cap;
     p.n_iss = std::min(std::max(c->tune_iss, 1), kIssuers);
+    p.bands = hist_out ? BandSet() : c->multi;
     if ((e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_tc, kThreads, smem);
