@@ -186,6 +186,27 @@ int aptidx_get_histograms(aptidx_ctx* ctx, int64_t roi, int path, uint16_t* h, i
 int aptidx_get_roi_atoms(aptidx_ctx* ctx, int64_t roi, float* xc, int64_t cap, int64_t* n_out,
                          int mem);
 
+/* Local octree-like refinement of a cubic ROI grid (Section 3.4, aluminium
+ * bicrystal): a ROI of the current set qualifies when the maximum of its
+ * signature row reaches kappa times the largest signature value over all
+ * ROIs (the paper's "kappa >= 0.75 normalised image intensity", read with
+ * the dataset's largest value as the normalisation); the cubic grid cell of
+ * edge `spacing` centred on each qualifying ROI is split into split^3 cells
+ * and a new ROI is placed at every cell centre: new ROI k = q * split^3 + j
+ * for the q-th qualifying ROI (in ROI order) and cell j = ix + split * (iy +
+ * split * iz), centre + (i - (split - 1) / 2) * spacing / split per axis in
+ * FP64.  S: nroi x nv FP32 signatures of the current ROIs (raw, or
+ * normalised the same way for every ROI) in `mem`; nroi must equal the
+ * context's ROI count.  centres_out: cap x 3 FP64, parent_out: cap int32
+ * (the coarse ROI, NULL to skip), both in `mem`; *n_out (host) receives the
+ * number of new ROIs, which may exceed cap (then the first cap are
+ * written).  0 < kappa <= 1, spacing > 0, 2 <= split <= 16.  The new ROIs
+ * are not installed: pass them to aptidx_set_rois for the second pass.
+ * Errors: INVALID_ARG, STATE, OOM, CUDA. */
+int aptidx_refine_roi_grid(aptidx_ctx* ctx, const float* S, int64_t nroi, float kappa, double spacing,
+                           int32_t split, double* centres_out, int32_t* parent_out, int64_t cap, int64_t* n_out,
+                           int mem);
+
 /* ---- indexing (supplement "Indexing algorithm", Eq. 3) ---------------------- */
 
 /* Reference of crystal-structure candidate `cand` (0 <= cand < 8):

@@ -244,6 +244,28 @@ def lut(dirs, top, quats, threads=0):
     return out
 
 
+def refine_roi_grid(S, centres, kappa, spacing, split=5):
+    """Local refinement of a cubic ROI grid (Section 3.4, aluminium
+    bicrystal): ROIs whose largest signature value reaches kappa times the
+    largest value over all ROIs qualify; the cubic cell of edge `spacing`
+    centred on each is split into split^3 cells and a new ROI goes to every
+    cell centre, centre + (i - (split - 1) / 2) * spacing / split per axis.
+    New ROIs in order of the qualifying ROI, then cell j = ix + split * (iy +
+    split * iz).  Returns (centres float64 [n, 3], parent int32 [n])."""
+    S = np.asarray(S, np.float64)
+    centres = np.asarray(centres, np.float64).reshape(-1, 3)
+    peak = S.max(axis=1)
+    g = peak.max() if peak.size else 0.0
+    sel = np.nonzero(peak >= np.float32(kappa) * np.float32(g))[0] if g > 0 else np.zeros(0, np.int64)
+    h = spacing / split
+    i = np.arange(split, dtype=np.float64)
+    iz, iy, ix = np.meshgrid(i, i, i, indexing="ij")
+    offs = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1)
+    offs = (offs - (split - 1) * 0.5) * h
+    out = (centres[sel][:, None, :] + offs[None, :, :]).reshape(-1, 3)
+    return np.ascontiguousarray(out), np.repeat(sel.astype(np.int32), split ** 3)
+
+
 def match_topk(S_msr, S_ref, top, lut_, k, threads=0):
     """The k best test orientations per ROI under Eq. 3 (supplement "Indexing
     algorithm": the paper keeps up to 1000 solutions per ROI): Delta(g) of

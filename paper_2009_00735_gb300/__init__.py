@@ -22,7 +22,7 @@ __all__ = [
     "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
-    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_loss", "aptidx_refine",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
@@ -77,6 +77,8 @@ _SIGS = {
     "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_match_topk": (C.c_int, [_vp, _i32, _vp, _i64, _i32, _vp, _vp, C.c_int]),
+    "aptidx_refine_roi_grid": (C.c_int, [_vp, _vp, _i64, C.c_float, C.c_double, _i32, _vp, _vp, _i64, _vp,
+                                         C.c_int]),
     "aptidx_compute_signatures_multi": (C.c_int, [_vp, C.c_int, C.c_uint, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                                                   C.c_int]),
     "aptidx_refine_loss": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i64, _vp, _vp, C.c_int]),
@@ -266,6 +268,31 @@ def aptidx_compute_signatures_multi(ctx, path: int, flags: int, type_masks, k_lo
     _check(ctx, load().aptidx_compute_signatures_multi(ctx, path, flags, n_sig, tm.ctypes.data_as(_vp),
                                                        lo.ctypes.data_as(_vp), hi.ctypes.data_as(_vp), pS, pA, pN,
                                                        _one_mem(mS, mA, mN)))
+
+
+def aptidx_refine_roi_grid(ctx, S, kappa: float, spacing: float, split: int = 5):
+    """New ROI centres (float64 [n, 3]) and their coarse parents (int32 [n])
+    of the local grid refinement; S holds the current ROIs' signatures."""
+    pS, mS, kS = _arg(S, np.float32)
+    nroi = int(kS.shape[0])
+    n = _i64(0)
+    _check(ctx, load().aptidx_refine_roi_grid(ctx, pS, nroi, C.c_float(kappa), C.c_double(spacing), int(split), None,
+                                              None, 0, C.byref(n), mS))
+    cen = np.empty((n.value, 3), np.float64)
+    par = np.empty(n.value, np.int32)
+    if n.value:
+        if mS == APTIDX_MEM_DEVICE:
+            import torch
+            cd = torch.empty((n.value, 3), dtype=torch.float64, device=kS.device)
+            pd = torch.empty(n.value, dtype=torch.int32, device=kS.device)
+            _check(ctx, load().aptidx_refine_roi_grid(ctx, pS, nroi, C.c_float(kappa), C.c_double(spacing), int(split),
+                                                      C.c_void_p(cd.data_ptr()), C.c_void_p(pd.data_ptr()), n.value,
+                                                      C.byref(_i64(0)), mS))
+            return cd.cpu().numpy(), pd.cpu().numpy()
+        _check(ctx, load().aptidx_refine_roi_grid(ctx, pS, nroi, C.c_float(kappa), C.c_double(spacing), int(split),
+                                                  cen.ctypes.data_as(_vp), par.ctypes.data_as(_vp), n.value,
+                                                  C.byref(_i64(0)), mS))
+    return cen, par
 
 
 def aptidx_get_histograms(ctx, roi: int, path: int, h):

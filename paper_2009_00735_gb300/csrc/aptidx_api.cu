@@ -1235,6 +1235,41 @@ int aptidx_compute_signatures_multi(aptidx_ctx* ctx, int path, unsigned flags, i
     return read_status(c);
 }
 
+int aptidx_refine_roi_grid(aptidx_ctx* ctx, const float* S, int64_t nroi, float kappa, double spacing,
+                           int32_t split, double* centres_out, int32_t* parent_out, int64_t cap, int64_t* n_out,
+                           int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "refine_roi_grid: set ROIs first");
+    if (!S || !n_out || nroi != c->nroi)
+        return set_error(c, APTIDX_E_INVALID_ARG, "refine_roi_grid: need S of the current %lld ROIs and n_out",
+                         (long long)c->nroi);
+    if (!(kappa > 0.f && kappa <= 1.f) || !(spacing > 0.0 && isfinite(spacing)) || split < 2 || split > 16 || cap < 0 ||
+        (cap > 0 && !centres_out))
+        return set_error(c, APTIDX_E_INVALID_ARG,
+                         "refine_roi_grid: need 0 < kappa <= 1, spacing > 0, 2 <= split <= 16, cap >= 0 (and "
+                         "centres_out when cap > 0)");
+    DevTmp tS, tc, tp;
+    const float* dS;
+    double* dC;
+    int32_t* dP;
+    if ((rc = dev_view(c, S, (size_t)nroi * c->nv, mem, tS, &dS))) return rc;
+    if ((rc = dev_out(c, centres_out, (size_t)cap * 3, mem, tc, &dC))) return rc;
+    if ((rc = dev_out(c, parent_out, (size_t)cap, mem, tp, &dP))) return rc;
+    int64_t nq = 0;
+    cudaError_t e = launch_roi_refine(c, dS, kappa, spacing, split, cap > 0 ? dC : nullptr, dP, cap, &nq);
+    if (e != cudaSuccess) return cuda_check(c, e, "ROI grid refinement");
+    c->launches += cap > 0 ? 6 : 5;
+    const int64_t n = nq * (int64_t)split * split * split;
+    *n_out = n;
+    const size_t nw = (size_t)std::min(n, cap);
+    if ((rc = copy_back(c, centres_out, dC, nw * 3, mem))) return rc;
+    if ((rc = copy_back(c, parent_out, dP, nw, mem))) return rc;
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
 int aptidx_refine_loss(aptidx_ctx* ctx, int32_t cand, const float* S, const double* q0, const double* omega,
                        int64_t nroi, float* loss, float* grad, int mem) {
     CTX_OR_FAIL(ctx);

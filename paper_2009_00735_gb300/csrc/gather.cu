@@ -457,4 +457,99 @@ cudaError_t launch_twiddles(float2* tw, int m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// -----------------------------------------------------------------------------
+// local refinement of a cubic ROI grid (Section 3.4, aluminium bicrystal): a
+// ROI qualifies when its peak signature value reaches kappa times the largest
+// value over all ROIs; its grid cell is split into split^3 cells with a new
+// ROI at every cell centre
+// -----------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(256) k_roi_peak(const float* __restrict__ S, int64_t nroi, int32_t nv, float* peak,
+                                                  unsigned* gmax_bits) {
+    __shared__ float red[8];
+    for (int64_t r = blockIdx.x; r < nroi; r += gridDim.x) {
+        const float* row = S + r * (int64_t)nv;
+        float mx = 0.f;
+        for (int v = threadIdx.x; v < nv; v += 256) mx = fmaxf(mx, row[v]);
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+            peak[r] = mx;
+            atomicMax(gmax_bits, __float_as_uint(mx));   // non-negative floats order like their bits
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_roi_qualify(const float* __restrict__ peak, int64_t nroi, float kappa,
+                              const unsigned* __restrict__ gmax_bits, int64_t* flag) {
+    const float g = __uint_as_float(*gmax_bits);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nroi; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = (g > 0.f && peak[r] >= __fmul_rn(kappa, g)) ? 1 : 0;
+}
+
+// new ROI k = off[r] * split^3 + j, sub-cell j = ix + split (iy + split iz):
+// centre = c + (i - (split - 1) / 2) * (spacing / split) per axis
+__global__ void k_roi_split(const double* __restrict__ centres, const int64_t* __restrict__ flag,
+                            const int64_t* __restrict__ off, int64_t nroi, double spacing, int split, double* out,
+                            int32_t* parent, int64_t cap) {
+    const int s3 = split * split * split;
+    const double hh = __ddiv_rn(spacing, (double)split);
+    const double mid = (double)(split - 1) * 0.5;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nroi * s3;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / s3;
+        const int j = (int)(t % s3);
+        if (!flag[r]) continue;
+        const int64_t k = off[r] * s3 + j;
+        if (k >= cap) continue;
+        const int ix = j % split, iy = (j / split) % split, iz = j / (split * split);
+        const int ii[3] = {ix, iy, iz};
+        for (int d = 0; d < 3; ++d)
+            out[3 * k + d] = __dadd_rn(centres[3 * r + d], __dmul_rn(__dadd_rn((double)ii[d], -mid), hh));
+        if (parent) parent[k] = (int32_t)r;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_roi_refine(Ctx* c, const float* S, float kappa, double spacing, int split, double* out,
+                              int32_t* parent, int64_t cap, int64_t* n_qualified) {
+    const int64_t nroi = c->nroi;
+    float* peak = nullptr;
+    unsigned* gmax = nullptr;
+    int64_t *flag = nullptr, *off = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (dev_alloc(c, (void**)&peak, (size_t)nroi * sizeof(float)) ||
+        dev_alloc(c, (void**)&gmax, sizeof(unsigned)) || dev_alloc(c, (void**)&flag, (size_t)nroi * sizeof(int64_t)) ||
+        dev_alloc(c, (void**)&off, (size_t)(nroi + 1) * sizeof(int64_t)))
+        e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMemsetAsync(gmax, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) {
+        k_roi_peak<<<(unsigned)tmin<int64_t>(nroi, (int64_t)c->sm_count * 16), 256, 0, c->stream>>>(S, nroi, c->nv,
+                                                                                                     peak, gmax);
+        k_roi_qualify<<<(unsigned)tmin<int64_t>((nroi + 255) / 256, 4096), 256, 0, c->stream>>>(peak, nroi, kappa,
+                                                                                                gmax, flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_scan_i64(flag, off, nroi, c->d_scan_tmp, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n_qualified, off + nroi, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && cap > 0 && out) {
+        const int64_t s3 = (int64_t)split * split * split;
+        k_roi_split<<<(unsigned)tmin<int64_t>((nroi * s3 + 255) / 256, 65535), 256, 0, c->stream>>>(
+            c->d_centres, flag, off, nroi, spacing, split, out, parent, cap);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(peak);
+    dev_free(gmax);
+    dev_free(flag);
+    dev_free(off);
+    return e;
+}
+
 }  // namespace aptidx

@@ -183,6 +183,8 @@ size_t scan_tmp_elems(int64_t n);
 cudaError_t launch_gather_count(Ctx* c);
 cudaError_t launch_gather_fill(Ctx* c);
 cudaError_t launch_roi_order(Ctx* c);
+cudaError_t launch_roi_refine(Ctx* c, const float* S, float kappa, double spacing, int split, double* out,
+                              int32_t* parent, int64_t cap, int64_t* n_qualified);
 cudaError_t launch_twiddles(float2* tw, int m, cudaStream_t s);
 
 // signature kernels

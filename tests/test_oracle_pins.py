@@ -452,6 +452,25 @@ def test_match_topk_orders_solutions():
     assert list(g[1]) == list(range(7))
 
 
+def test_refine_roi_grid_geometry_and_threshold():
+    """Grid refinement: peaks 1.0, 0.8, 0.5 and kappa = 0.75 keep the first two
+    ROIs; each gets 125 new centres on a 5 x 5 x 5 lattice of pitch
+    spacing / 5 centred on it, filling its cell (extent spacing - pitch), the
+    x index running fastest."""
+    S = np.array([[0.2, 1.0, 0.3], [0.8, 0.1, 0.0], [0.5, 0.5, 0.4]])
+    centres = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [4.0, 0.0, 0.0]])
+    c, par = oracle.refine_roi_grid(S, centres, 0.75, 2.0, 5)
+    assert c.shape == (250, 3) and list(np.unique(par)) == [0, 1]
+    for r in (0, 1):
+        sub = c[par == r]
+        assert np.allclose(sub.mean(axis=0), centres[r])
+        assert np.allclose(sub.max(axis=0) - sub.min(axis=0), 2.0 - 0.4)
+        assert np.allclose(np.unique(np.round(sub[:, 0] - centres[r, 0], 12)), [-0.8, -0.4, 0.0, 0.4, 0.8])
+    assert np.allclose(c[1] - c[0], [0.4, 0.0, 0.0]) and np.allclose(c[5] - c[0], [0.0, 0.4, 0.0])
+    c2, _ = oracle.refine_roi_grid(S, centres, 0.5, 2.0, 2)     # 0.5 * 1.0: the third ROI just qualifies
+    assert c2.shape == (24, 3)
+
+
 def test_match_indexes_rotated_crystal_end_to_end():
     """Signatures of a rotated perfect f.c.c. ROI, matched against the
     unrotated reference over a test-orientation set that contains the true
