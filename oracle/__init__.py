@@ -88,6 +88,8 @@ def _declare(L):
     L.orc_lut.argtypes = [_p, _i64, _p, C.c_int, _p, _i64, _p, C.c_int]
     L.orc_match.restype = None
     L.orc_match.argtypes = [_p, _i64, _i64, _p, _p, C.c_int, _p, _i64, _p, _p, _p, C.c_int]
+    L.orc_fsp.restype = None
+    L.orc_fsp.argtypes = [_p, _i64, C.c_int, _d, _p, _i64, _p]
     L.orc_bilinear.restype = C.c_int
     L.orc_bilinear.argtypes = [_p, _p, _p, _p, _p]
     L.orc_refine_eval.restype = None
@@ -241,6 +243,17 @@ def lut(dirs, top, quats, threads=0):
     q = _c(quats, np.float64).reshape(-1, 4)
     out = np.empty((q.shape[0], top.shape[0]), np.int32)
     lib().orc_lut(_ptr(u), u.shape[0], _ptr(top), top.shape[0], _ptr(q), q.shape[0], _ptr(out), threads)
+    return out
+
+
+def fsp(xc, L, kmax=2 * np.pi, points=None):
+    """|F(k)| of Eq. 2 for centred positions xc on the L^3 grid over
+    [-kmax, kmax]^3 (nm^-1), FP64 direct sum.  points: flat indices
+    (ix * L + iy) * L + iz (default: all L^3).  Returns float64 [npts]."""
+    xc = _c(xc, np.float32).reshape(-1, 3)
+    pts = np.arange(L ** 3, dtype=np.int64) if points is None else _c(points, np.int64)
+    out = np.empty(pts.shape[0], np.float64)
+    lib().orc_fsp(_ptr(xc), xc.shape[0], int(L), float(kmax), _ptr(pts), pts.shape[0], _ptr(out))
     return out
 
 

@@ -614,3 +614,29 @@ int orc_openmp_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reciprocal-space signature (Eq. 2, the FSP method after Vurpillot et al.) */
+/* F(k) = sum_w exp(-2 pi i k . x_w) over the centred positions x_w of a ROI */
+/* on the cubic grid k_a = -k_max + i_a dk, i_a < L, dk = 2 k_max / (L - 1)   */
+/* (the reciprocal-space cube [-k_max, k_max]^3 of the supplement's cost     */
+/* section, L_D points per axis).  out[p] = |F(k_p)| for the grid points     */
+/* given as flat indices (ix L + iy) L + iz; FP64 throughout.                */
+/* ------------------------------------------------------------------------ */
+void orc_fsp(const float* xc, int64_t nw, int L, double kmax, const int64_t* pts, int64_t npts, double* out)
+{
+    const double dk = 2.0 * kmax / (double)(L - 1);
+    for (int64_t p = 0; p < npts; ++p) {
+        const int64_t f = pts[p];
+        const int iz = (int)(f % L), iy = (int)((f / L) % L), ix = (int)(f / ((int64_t)L * L));
+        const double kx = -kmax + ix * dk, ky = -kmax + iy * dk, kz = -kmax + iz * dk;
+        double re = 0.0, im = 0.0;
+        for (int64_t w = 0; w < nw; ++w) {
+            const double ph = 2.0 * ORC_PI * (kx * (double)xc[3 * w] + ky * (double)xc[3 * w + 1] +
+                                               kz * (double)xc[3 * w + 2]);
+            re += cos(ph);
+            im -= sin(ph);
+        }
+        out[p] = sqrt(re * re + im * im);
+    }
+}

@@ -471,6 +471,45 @@ def test_refine_roi_grid_geometry_and_threshold():
     assert c2.shape == (24, 3)
 
 
+def test_fsp_closed_forms():
+    """Eq. 2 closed forms: one atom anywhere gives |F| = 1 on the whole grid;
+    at k = 0 (odd L puts it at the centre) |F| = N_w; two atoms d apart along
+    x give |F| = |2 cos(pi k_x d)|; grid points follow k = -kmax + i dk."""
+    L = 5
+    one = oracle.fsp(np.array([[0.3, -0.7, 1.1]], np.float32), L)
+    assert np.allclose(one, 1.0, atol=1e-12)
+    rng = np.random.default_rng(1)
+    xc = rng.uniform(-2, 2, (37, 3)).astype(np.float32)
+    c = ((L // 2) * L + L // 2) * L + L // 2
+    assert oracle.fsp(xc, L, points=[c])[0] == pytest.approx(37.0, abs=1e-9)
+    d = 0.25
+    two = np.array([[-d / 2, 0.0, 0.0], [d / 2, 0.0, 0.0]], np.float32)
+    F = oracle.fsp(two, L).reshape(L, L, L)
+    kx = -2 * np.pi + np.arange(L) * (4 * np.pi / (L - 1))
+    assert np.allclose(F[:, 1, 3], np.abs(2 * np.cos(np.pi * kx * np.float64(np.float32(d)))), atol=1e-9)
+
+
+def test_fsp_matches_brute_force_and_lattice_peaks():
+    """Eq. 2 against a numpy evaluation of the same sum on random points, and a
+    simple cubic lattice of pitch 0.5 nm peaking at its reciprocal lattice
+    points k = (h, k, l) / 0.5 with |F| = N_w."""
+    rng = np.random.default_rng(2)
+    xc = rng.uniform(-1.5, 1.5, (50, 3)).astype(np.float32)
+    L = 7
+    F = oracle.fsp(xc, L)
+    k = -np.pi * 2 + np.arange(L) * (4 * np.pi / (L - 1))
+    K = np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
+    ref = np.abs(np.exp(-2j * np.pi * (K @ xc.astype(np.float64).T)).sum(axis=1))
+    assert np.allclose(F, ref, rtol=1e-10, atol=1e-9)
+    g = np.arange(-3, 4) * 0.5
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    # kmax = 2 per nm, L = 9: dk = 0.5, k = 2 per nm (= 1 / 0.5) is grid index 8
+    F2 = oracle.fsp(lat, 9, kmax=2.0).reshape(9, 9, 9)
+    assert F2[8, 4, 4] == pytest.approx(lat.shape[0], rel=1e-9)
+    assert F2[4, 4, 4] == pytest.approx(lat.shape[0], rel=1e-9)
+    assert F2[6, 4, 4] < 0.2 * lat.shape[0]
+
+
 def test_match_indexes_rotated_crystal_end_to_end():
     """Signatures of a rotated perfect f.c.c. ROI, matched against the
     unrotated reference over a test-orientation set that contains the true
