@@ -207,6 +207,20 @@ int aptidx_refine_roi_grid(aptidx_ctx* ctx, const float* S, int64_t nroi, float 
                            int32_t split, double* centres_out, int32_t* parent_out, int64_t cap, int64_t* n_out,
                            int mem);
 
+/* Reciprocal-space signature (Eq. 2, the FSP method of Section 2.2 after
+ * Vurpillot et al.): for every ROI of the current set (and type mask),
+ * |F(k)| with F(k) = sum_w exp(-2 pi i k . (p_w - p_c)) over the ROI's
+ * atoms (centred FP32 coordinates of the gather, nm), on the cubic grid
+ * k = (k_x, k_y, k_z), k_a = -k_max + i_a dk, i_a < APTIDX_FSP_L,
+ * dk = 2 k_max / (APTIDX_FSP_L - 1), k in nm^-1 (the supplement's grid over
+ * [-2 pi, 2 pi]^3 gives k_max = 2 pi).  amp: nroi x L x L x L FP32,
+ * amp[((roi * L + ix) * L + iy) * L + iz], in `mem`.  Computed as tensor-core
+ * GEMMs with fp16 operands and FP32 accumulation (sm_103 only).
+ * 0 < k_max <= 64.  Errors: INVALID_ARG (no tensor cores, bad k_max), STATE,
+ * OOM, CUDA, TIMEOUT. */
+#define APTIDX_FSP_L 64
+int aptidx_compute_fsp(aptidx_ctx* ctx, double k_max, float* amp, int mem);
+
 /* ---- indexing (supplement "Indexing algorithm", Eq. 3) ---------------------- */
 
 /* Reference of crystal-structure candidate `cand` (0 <= cand < 8):

@@ -22,7 +22,7 @@ __all__ = [
     "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
-    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_refine_loss", "aptidx_refine",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_compute_fsp", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
@@ -32,6 +32,7 @@ __all__ = [
 APTIDX_OK = 0
 APTIDX_MAX_TOPK = 1024
 APTIDX_MAX_BANDS = 4
+APTIDX_FSP_L = 64
 APTIDX_E_INVALID_ARG = 1
 APTIDX_E_CUDA = 2
 APTIDX_E_OOM = 3
@@ -77,6 +78,7 @@ _SIGS = {
     "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_match_topk": (C.c_int, [_vp, _i32, _vp, _i64, _i32, _vp, _vp, C.c_int]),
+    "aptidx_compute_fsp": (C.c_int, [_vp, C.c_double, _vp, C.c_int]),
     "aptidx_refine_roi_grid": (C.c_int, [_vp, _vp, _i64, C.c_float, C.c_double, _i32, _vp, _vp, _i64, _vp,
                                          C.c_int]),
     "aptidx_compute_signatures_multi": (C.c_int, [_vp, C.c_int, C.c_uint, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -293,6 +295,13 @@ def aptidx_refine_roi_grid(ctx, S, kappa: float, spacing: float, split: int = 5)
                                                   cen.ctypes.data_as(_vp), par.ctypes.data_as(_vp), n.value,
                                                   C.byref(_i64(0)), mS))
     return cen, par
+
+
+def aptidx_compute_fsp(ctx, amp, k_max: float = 2 * 3.141592653589793):
+    """|F(k)| of Eq. 2 on the 64^3 grid over [-k_max, k_max]^3 (nm^-1) for
+    every ROI: amp [nroi, 64, 64, 64] float32 (ix, iy, iz)."""
+    pA, mA = _out(amp, np.float32)
+    _check(ctx, load().aptidx_compute_fsp(ctx, C.c_double(k_max), pA, mA))
 
 
 def aptidx_get_histograms(ctx, roi: int, path: int, h):

@@ -1,0 +1,317 @@
+// fsp_tc.cu -- the reciprocal-space signature (Eq. 2, the FSP method of
+// Section 2.2 after Vurpillot et al.): |F(k)| with
+//   F(k) = sum_w exp(-2 pi i k . x_w)
+// over the centred positions x_w of a ROI, on the cubic grid
+// k_a = -k_max + i_a dk (i_a < L, dk = 2 k_max / (L - 1)), as tensor-core
+// GEMMs.  The exponential factorises per axis, E_a[i, w] = exp(-2 pi i k_i a_w),
+// so with P[(ix, iy), w] = E_x[ix, w] E_y[iy, w]:
+//   F[(ix, iy), iz] = sum_w P[(ix, iy), w] E_z[iz, w],
+// a complex GEMM of M = L^2 rows, N = L columns and K = N_w.  It runs as the
+// real GEMM [P_r | P_i] x [[E_r, E_i], [-E_i, E_r]] (K = 2 N_w, N = 2 L)
+// whose two column halves are Re F and Im F, on tcgen05 with fp16 operands
+// and FP32 accumulators in tensor memory.
+//
+// Work item = (ROI, 8 consecutive ix) = 512 rows = 4 M tiles of 128, their
+// accumulators filling the 512 tensor-memory columns.  Per chunk of 32 atoms
+// (K = 64: the 32 real parts, then the 32 imaginary parts) 448 producer
+// threads tabulate E_x (8 rows), E_y and E_z (64 rows each; E_y, E_z by
+// recurrence E[i + 1] = E[i] exp(-2 pi i dk a) from an exact start every 16
+// rows), build the A chunk (P, 4 tiles) and the B chunk in the K-major
+// 128-byte-swizzled layout, and hand the stage to two issuer threads, which
+// run 16 MMAs (M = 128, N = 128, K = 16) while the next stage is built.
+#include <cuda_fp16.h>
+
+#include "tcgen05.cuh"
+
+namespace aptidx {
+
+namespace {
+
+constexpr int kL = APTIDX_FSP_L;                    // grid points per axis
+constexpr int kN = 2 * kL;                          // MMA N: [Re F | Im F] over iz
+constexpr int kTileRows = 128;                      // MMA M
+constexpr int kTiles = 4;                           // M tiles per item
+constexpr int kIxItem = kTiles * kTileRows / kL;    // 8 values of ix per item
+constexpr int kItemsRoi = kL / kIxItem;             // 8 items per ROI
+constexpr int kWc = 32;                             // atoms per chunk (K = 64)
+constexpr int kThreadsF = 512;
+constexpr int kIss = 2;                             // issuer warps: tiles 0-1 and 2-3
+constexpr int kProd0 = kIss * 32;                   // first producer thread
+constexpr int kProd = kThreadsF - kProd0;           // 448 producer threads
+constexpr int kStageA = kTiles * kTileRows * 128;   // 64 KB
+constexpr int kStageB = kN * 128;                   // 16 KB
+constexpr int kStage = kStageA + kStageB;           // 80 KB
+constexpr int kTabBytes = (kIxItem + 2 * kL) * kWc * 8;
+constexpr int kSeg = 16;                            // recurrence segment (rows)
+
+static_assert(kL == 64, "the tiling assumes L = 64");
+
+struct FspParams {
+    const float4* atoms;   // centred ROI atoms, CSR by off
+    const int64_t* off;
+    const int32_t* nw;
+    int64_t nroi;
+    float kmax, dk;
+    float* out;            // nroi x L^3 amplitudes, iz fastest
+    int32_t* counter;
+    int* status;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void prod_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory");
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// exp(-2 pi i t) for t = k a given as 2 k a in units of pi
+__device__ __forceinline__ float2 cexp_m2pi(float two_ka) {
+    float s, c;
+    sincospif(two_ka, &s, &c);
+    return make_float2(c, -s);
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// byte offset of 16-byte chunk j of row r in a K-major 128-byte-swizzled
+// operand (rows of 64 fp16, atoms of 8 rows x 128 bytes)
+__device__ __forceinline__ uint32_t sw128_off(int r, int j) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    float2* Ex = reinterpret_cast<float2*>(smem + 2 * kStage);
+    float2* Ey = Ex + kIxItem * kWc;
+    float2* Ez = Ey + kL * kWc;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage + kTabBytes);
+    uint64_t* full = bars;          // [2]: producers -> issuers
+    uint64_t* empty = bars + 2;     // [2]: MMA completion -> producers
+    uint64_t* accum = bars + 4;     // all MMAs of the item completed
+    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 5);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 6);
+    int* fail_s = reinterpret_cast<int*>(bars + 7);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], kIss);
+        mbar_init(&empty[1], kIss);
+        mbar_init(accum, kIss);
+        *fail_s = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_s, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_s;
+    const uint32_t st_addr = smem_u32(smem);
+    const uint32_t idesc = idesc_f16_mk(kTileRows, kN, false);
+
+    uint32_t cg = 0;      // chunks issued so far by this CTA (stage ring position)
+    uint32_t nitem = 0;   // items finished so far (accumulator barrier phase)
+    const int64_t n_items = p.nroi * kItemsRoi;
+    for (;;) {
+        if (tid == 0) *item_s = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int64_t item = *item_s;
+        const int failed = *fail_s;
+        __syncthreads();
+        if (item >= n_items || failed) break;
+        const int64_t roi = item / kItemsRoi;
+        const int g = (int)(item % kItemsRoi);
+        const int nw = p.nw[roi];
+        const float4* A = p.atoms + p.off[roi];
+        const int nch = max(1, (nw + kWc - 1) / kWc);
+
+        if (warp < kIss) {
+            // ---- issuers: warp 0 tiles 0-1, warp 1 tiles 2-3 ----
+            if (lane == 0) {
+                bool ok = true;
+                for (int c = 0; c < nch && ok; ++c) {
+                    const uint32_t s = (cg + c) & 1u, u = (cg + c) >> 1;
+                    ok = mbar_wait_bounded(&full[s], u & 1u, p.status);
+                    if (!ok) {
+                        *fail_s = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_base = st_addr + s * kStage;
+                    const uint32_t b_base = a_base + kStageA;
+#pragma unroll
+                    for (int tt = 0; tt < 2; ++tt) {
+                        const int t = warp * 2 + tt;
+                        const uint64_t ad = sdesc_sw128(a_base + (uint32_t)t * (kTileRows * 128), 16u, 1024u);
+                        const uint64_t bd = sdesc_sw128(b_base, 16u, 1024u);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)   // K = 16 per MMA: +32 bytes along the row
+                            mma_f16(tmem + (uint32_t)t * 128u, ad + 2u * kk, bd + 2u * kk, idesc,
+                                    (c > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(accum);   // also after a failure: the epilogue then waits on what was issued
+            }
+            __syncwarp();
+        } else {
+            // ---- producers ----
+            const int pt = tid - kProd0;
+            for (int c = 0; c < nch; ++c) {
+                const uint32_t s = (cg + c) & 1u, u = (cg + c) >> 1;
+                if (pt == 0 && u >= 1 && !mbar_wait_bounded(&empty[s], (u - 1) & 1u, p.status)) *fail_s = 1;
+                prod_sync();
+                const int w0 = c * kWc;
+                // tables: E_y, E_z by recurrence in segments of 16 rows ...
+                if (pt < 2 * kWc * (kL / kSeg)) {
+                    const int axis = pt / (kWc * (kL / kSeg));   // 0: y, 1: z
+                    const int rem = pt % (kWc * (kL / kSeg));
+                    const int wl = rem / (kL / kSeg), seg = rem % (kL / kSeg);
+                    const bool valid = w0 + wl < nw;
+                    const float a = valid ? (axis ? A[w0 + wl].z : A[w0 + wl].y) : 0.f;
+                    const int i0 = seg * kSeg;
+                    float2 e = cexp_m2pi(2.f * fmaf((float)i0, p.dk, -p.kmax) * a);
+                    const float2 d = cexp_m2pi(2.f * p.dk * a);
+                    float2* tab = axis ? Ez : Ey;
+                    for (int j = 0; j < kSeg; ++j) {
+                        tab[(i0 + j) * kWc + wl] = valid ? e : make_float2(0.f, 0.f);
+                        e = cmul(e, d);
+                    }
+                } else {
+                    // ... and E_x for the item's 8 values of ix, directly
+                    for (int e = pt - 2 * kWc * (kL / kSeg); e < kIxItem * kWc; e += kProd - 2 * kWc * (kL / kSeg)) {
+                        const int ixl = e / kWc, wl = e % kWc;
+                        const bool valid = w0 + wl < nw;
+                        const float x = valid ? A[w0 + wl].x : 0.f;
+                        const float k = fmaf((float)(g * kIxItem + ixl), p.dk, -p.kmax);
+                        Ex[ixl * kWc + wl] = valid ? cexp_m2pi(2.f * k * x) : make_float2(0.f, 0.f);
+                    }
+                }
+                prod_sync();
+                unsigned char* stA = smem + s * kStage;
+                unsigned char* stB = stA + kStageA;
+                // A: row m = ixl * 64 + iy, K = [Re P of the 32 atoms | Im P]; unit
+                // (iy, q, half): atoms 8q .. 8q+7, ixl in half * 4 .. + 3
+                for (int e = pt; e < kL * 4 * 2; e += kProd) {
+                    const int iy = e & (kL - 1), q = (e / kL) & 3, half = e / (kL * 4);
+                    float2 ey[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) ey[j] = Ey[iy * kWc + 8 * q + j];
+#pragma unroll
+                    for (int il = 0; il < 4; ++il) {
+                        const int ixl = half * 4 + il;
+                        uint32_t re[4], im[4];
+#pragma unroll
+                        for (int j = 0; j < 8; j += 2) {
+                            const float2 p0 = cmul(Ex[ixl * kWc + 8 * q + j], ey[j]);
+                            const float2 p1 = cmul(Ex[ixl * kWc + 8 * q + j + 1], ey[j + 1]);
+                            re[j / 2] = pack_h2(p0.x, p1.x);
+                            im[j / 2] = pack_h2(p0.y, p1.y);
+                        }
+                        const int m = ixl * kL + iy, t = m >> 7, r = m & 127;
+                        unsigned char* rowt = stA + t * (kTileRows * 128);
+                        *reinterpret_cast<uint4*>(rowt + sw128_off(r, q)) = make_uint4(re[0], re[1], re[2], re[3]);
+                        *reinterpret_cast<uint4*>(rowt + sw128_off(r, q + 4)) = make_uint4(im[0], im[1], im[2], im[3]);
+                    }
+                }
+                // B: row n < L: [Re E_z | -Im E_z] of iz = n; n >= L: [Im E_z | Re E_z] of iz = n - L
+                for (int e = pt; e < kN * 4; e += kProd) {
+                    const int n = e >> 2, q = e & 3, z = n & (kL - 1);
+                    uint32_t v0[4], v1[4];
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) {
+                        const float2 a0 = Ez[z * kWc + 8 * q + j], a1 = Ez[z * kWc + 8 * q + j + 1];
+                        if (n < kL) {
+                            v0[j / 2] = pack_h2(a0.x, a1.x);
+                            v1[j / 2] = pack_h2(-a0.y, -a1.y);
+                        } else {
+                            v0[j / 2] = pack_h2(a0.y, a1.y);
+                            v1[j / 2] = pack_h2(a0.x, a1.x);
+                        }
+                    }
+                    *reinterpret_cast<uint4*>(stB + sw128_off(n, q)) = make_uint4(v0[0], v0[1], v0[2], v0[3]);
+                    *reinterpret_cast<uint4*>(stB + sw128_off(n, q + 4)) = make_uint4(v1[0], v1[1], v1[2], v1[3]);
+                }
+                fence_proxy_async_smem();
+                prod_sync();
+                if (pt == 0) mbar_arrive(&full[s]);
+            }
+        }
+        cg += (uint32_t)nch;
+
+        // ---- epilogue: |F| = sqrt(Re^2 + Im^2); warp w reads TMEM lane
+        // quadrant w % 4 of tile w / 4 ----
+        if (tid == 0 && !mbar_wait_bounded(accum, nitem & 1u, p.status)) *fail_s = 1;
+        ++nitem;
+        __syncthreads();
+        tc_fence_after();
+        if (!*fail_s) {
+            const int qd = warp & 3, t = warp >> 2;
+            const int m = t * kTileRows + qd * 32 + lane;
+            const int ix = g * kIxItem + (m >> 6), iy = m & (kL - 1);
+            float* dst = p.out + (((int64_t)roi * kL + ix) * kL + iy) * kL;
+            const uint32_t tb = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)t * 128u;
+            for (int h = 0; h < 2; ++h) {
+                float re[32], im[32];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    tmem_ld8(tb + (uint32_t)(h * 32 + 8 * i), re + 8 * i);
+                    tmem_ld8(tb + (uint32_t)(kL + h * 32 + 8 * i), im + 8 * i);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 32; i += 4) {
+                    float4 v;
+                    v.x = sqrtf(re[i] * re[i] + im[i] * im[i]);
+                    v.y = sqrtf(re[i + 1] * re[i + 1] + im[i + 1] * im[i + 1]);
+                    v.z = sqrtf(re[i + 2] * re[i + 2] + im[i + 2] * im[i + 2]);
+                    v.w = sqrtf(re[i + 3] * re[i + 3] + im[i + 3] * im[i + 3]);
+                    *reinterpret_cast<float4*>(dst + h * 32 + i) = v;
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+size_t fsp_smem_bytes() { return 1024 + 2 * (size_t)kStage + kTabBytes + 128; }
+
+cudaError_t launch_fsp_tc(Ctx* c, double kmax, float* out) {
+    const size_t smem = fsp_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_fsp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    FspParams p;
+    p.atoms = c->d_atoms;
+    p.off = c->d_off;
+    p.nw = c->d_nw;
+    p.nroi = c->nroi;
+    p.kmax = (float)kmax;
+    p.dk = (float)(2.0 * kmax / (double)(kL - 1));
+    p.out = out;
+    p.counter = c->d_counter + 2;
+    p.status = c->d_status;
+    if ((e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count, c->nroi * kItemsRoi);
+    if (grid < 1) return cudaSuccess;
+    k_fsp_tc<<<(unsigned)grid, kThreadsF, smem, c->stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace aptidx
