@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-paper-index", action="store_true",
                     help="skip the paper-scale indexing measurement (618324 orientations, top-1000)")
+    ap.add_argument("--no-fsp", action="store_true",
+                    help="skip the reciprocal-space signature measurement (Eq. 2, 64^3 grid)")
     ap.add_argument("--rois", type=int, default=0,
                     help="use only the first N ROIs (a smaller case for profiling; 0: all 8192)")
     return ap.parse_args()
@@ -393,6 +395,39 @@ def run_gb300(args):
                        "rois_per_s": n_pi / (m_ms / 1e3),
                        "set": "Halton points through Shoemake's map, reduced to the cubic fundamental zone"}
 
+    # reciprocal-space signatures (Eq. 2) of the same ROIs on the 64^3 grid
+    # (not part of the step): tensor-core GEMMs, the paper's L_D = 64 case
+    fsp = None
+    if not args.no_fsp and tc_ok:
+        L = apt.APTIDX_FSP_L
+        n_f = min(nroi, 4096)
+        apt.aptidx_set_rois(h, torch.from_numpy(w.centres[:n_f]).cuda(), torch.from_numpy(w.radii[:n_f]).cuda())
+        amp = torch.empty((n_f, L, L, L), dtype=torch.float32, device="cuda")
+        apt.aptidx_compute_fsp(h, amp)            # warm-up
+        ef = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        apt.aptidx_set_profiling(h, True)
+        ef[0].record(stream)
+        for _ in range(2):
+            apt.aptidx_compute_fsp(h, amp)
+        ef[1].record(stream)
+        torch.cuda.synchronize()
+        fprof, _ = apt.aptidx_get_profile(h)
+        apt.aptidx_set_profiling(h, False)
+        f_ms = ef[0].elapsed_time(ef[1]) / 2
+        k_ms = fprof["signature"][0] / max(fprof["signature"][1], 1)
+        nw_f = n_atoms[:n_f]
+        kpad = 2 * ((nw_f + 31) // 32 * 32)                    # K = 2 N_w padded to the 32-atom chunks
+        flop = float(np.sum(2.0 * L * L * (2 * L) * kpad))     # executed, M = L^2, N = 2L
+        peaks = measured_peaks()
+        tp = peaks.get("bf16_tflops")
+        fsp = {"grid": f"{L}^3 over [-2pi, 2pi]^3 nm^-1", "rois": n_f, "ms_per_call": f_ms, "kernel_ms": k_ms,
+               "rois_per_s": n_f / (f_ms / 1e3),
+               "tensor": {"achieved": flop / (k_ms / 1e3) / 1e12, "peak": tp, "unit": "TFLOP/s",
+                          "frac": (flop / (k_ms / 1e3) / 1e12 / tp) if tp else None,
+                          "work": f"{flop:.3e} executed fp16 flop per launch (M = L^2, N = 2L, K = 2 N_w padded)"}}
+        apt.aptidx_set_rois(h, torch.from_numpy(w.centres).cuda(), torch.from_numpy(w.radii).cuda())
+        del amp
+
     # roofline of the dominant kernel (the signature kernel of the headline path)
     sig_ms = prof["signature"][0] / max(prof["signature"][1], 1)
     K = band[1] - band[0] + 1
@@ -485,6 +520,7 @@ def run_gb300(args):
                          "frac_below_0p5_deg": float((mis <= 0.5).mean()),
                          "median_coarse_match_deg": float(np.median(mis_coarse))},
             "paper_scale_indexing": paper_index,
+            "fsp": fsp,
             "roofline": roof,
             "clocks": clk,
             "gpu_launches": int(launches),

@@ -41,7 +41,8 @@ constexpr int kProd = kThreadsF - kProd0;           // 448 producer threads
 constexpr int kStageA = kTiles * kTileRows * 128;   // 64 KB
 constexpr int kStageB = kN * 128;                   // 16 KB
 constexpr int kStage = kStageA + kStageB;           // 80 KB
-constexpr int kTabBytes = (kIxItem + 2 * kL) * kWc * 8;
+constexpr int kTabRow = kWc + 2;                    // table row stride (float2): 16-byte reads, rows spread over banks
+constexpr int kTabBytes = (kIxItem + 2 * kL) * kTabRow * 8;
 constexpr int kSeg = 16;                            // recurrence segment (rows)
 
 static_assert(kL == 64, "the tiling assumes L = 64");
@@ -91,8 +92,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     float2* Ex = reinterpret_cast<float2*>(smem + 2 * kStage);
-    float2* Ey = Ex + kIxItem * kWc;
-    float2* Ez = Ey + kL * kWc;
+    float2* Ey = Ex + kIxItem * kTabRow;
+    float2* Ez = Ey + kL * kTabRow;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage + kTabBytes);
     uint64_t* full = bars;          // [2]: producers -> issuers
     uint64_t* empty = bars + 2;     // [2]: MMA completion -> producers
@@ -172,75 +173,81 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                 if (pt == 0 && u >= 1 && !mbar_wait_bounded(&empty[s], (u - 1) & 1u, p.status)) *fail_s = 1;
                 prod_sync();
                 const int w0 = c * kWc;
-                // tables: E_y, E_z by recurrence in segments of 16 rows ...
-                if (pt < 2 * kWc * (kL / kSeg)) {
-                    const int axis = pt / (kWc * (kL / kSeg));   // 0: y, 1: z
-                    const int rem = pt % (kWc * (kL / kSeg));
-                    const int wl = rem / (kL / kSeg), seg = rem % (kL / kSeg);
-                    const bool valid = w0 + wl < nw;
+                // tables: E_y, E_z by recurrence E[i + 1] = E[i] exp(-2 pi i dk a)
+                // in segments of 16 rows from an exact start; lane = atom, so
+                // every store writes whole table rows
+                const int wl = pt & 31;
+                const bool valid = w0 + wl < nw;
+                if (pt < 8 * 32) {
+                    const int axis = pt >> 7, seg = (pt >> 5) & 3;   // 0: y, 1: z
                     const float a = valid ? (axis ? A[w0 + wl].z : A[w0 + wl].y) : 0.f;
                     const int i0 = seg * kSeg;
                     float2 e = cexp_m2pi(2.f * fmaf((float)i0, p.dk, -p.kmax) * a);
                     const float2 d = cexp_m2pi(2.f * p.dk * a);
                     float2* tab = axis ? Ez : Ey;
                     for (int j = 0; j < kSeg; ++j) {
-                        tab[(i0 + j) * kWc + wl] = valid ? e : make_float2(0.f, 0.f);
+                        tab[(i0 + j) * kTabRow + wl] = valid ? e : make_float2(0.f, 0.f);
                         e = cmul(e, d);
                     }
                 } else {
-                    // ... and E_x for the item's 8 values of ix, directly
-                    for (int e = pt - 2 * kWc * (kL / kSeg); e < kIxItem * kWc; e += kProd - 2 * kWc * (kL / kSeg)) {
-                        const int ixl = e / kWc, wl = e % kWc;
-                        const bool valid = w0 + wl < nw;
-                        const float x = valid ? A[w0 + wl].x : 0.f;
+                    // E_x for the item's 8 values of ix, directly
+                    const float x = valid ? A[w0 + wl].x : 0.f;
+                    for (int ixl = (pt >> 5) - 8; ixl < kIxItem; ixl += kProd / 32 - 8) {
                         const float k = fmaf((float)(g * kIxItem + ixl), p.dk, -p.kmax);
-                        Ex[ixl * kWc + wl] = valid ? cexp_m2pi(2.f * k * x) : make_float2(0.f, 0.f);
+                        Ex[ixl * kTabRow + wl] = valid ? cexp_m2pi(2.f * k * x) : make_float2(0.f, 0.f);
                     }
                 }
                 prod_sync();
                 unsigned char* stA = smem + s * kStage;
                 unsigned char* stB = stA + kStageA;
-                // A: row m = ixl * 64 + iy, K = [Re P of the 32 atoms | Im P]; unit
-                // (iy, q, half): atoms 8q .. 8q+7, ixl in half * 4 .. + 3
-                for (int e = pt; e < kL * 4 * 2; e += kProd) {
-                    const int iy = e & (kL - 1), q = (e / kL) & 3, half = e / (kL * 4);
-                    float2 ey[8];
+                // A: row m = ixl * 64 + iy, K = [Re P of the 32 atoms | Im P].
+                // Threads 0..255 take unit (iy, q): E_y of atoms 8q .. 8q+7 in
+                // registers, all 8 values of ix (E_x reads are broadcasts).
+                if (pt < kL * 4) {
+                    const int iy = pt & (kL - 1), q = pt / kL;
+                    const float4* ey4 = reinterpret_cast<const float4*>(Ey + iy * kTabRow + 8 * q);
+                    float4 y[4];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) ey[j] = Ey[iy * kWc + 8 * q + j];
-#pragma unroll
-                    for (int il = 0; il < 4; ++il) {
-                        const int ixl = half * 4 + il;
+                    for (int j = 0; j < 4; ++j) y[j] = ey4[j];   // two atoms each: (re, im, re, im)
+#pragma unroll 2
+                    for (int ixl = 0; ixl < kIxItem; ++ixl) {
+                        const float4* ex4 = reinterpret_cast<const float4*>(Ex + ixl * kTabRow + 8 * q);
                         uint32_t re[4], im[4];
 #pragma unroll
-                        for (int j = 0; j < 8; j += 2) {
-                            const float2 p0 = cmul(Ex[ixl * kWc + 8 * q + j], ey[j]);
-                            const float2 p1 = cmul(Ex[ixl * kWc + 8 * q + j + 1], ey[j + 1]);
-                            re[j / 2] = pack_h2(p0.x, p1.x);
-                            im[j / 2] = pack_h2(p0.y, p1.y);
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 x = ex4[j];
+                            const float2 p0 = cmul(make_float2(x.x, x.y), make_float2(y[j].x, y[j].y));
+                            const float2 p1 = cmul(make_float2(x.z, x.w), make_float2(y[j].z, y[j].w));
+                            re[j] = pack_h2(p0.x, p1.x);
+                            im[j] = pack_h2(p0.y, p1.y);
                         }
                         const int m = ixl * kL + iy, t = m >> 7, r = m & 127;
                         unsigned char* rowt = stA + t * (kTileRows * 128);
                         *reinterpret_cast<uint4*>(rowt + sw128_off(r, q)) = make_uint4(re[0], re[1], re[2], re[3]);
-                        *reinterpret_cast<uint4*>(rowt + sw128_off(r, q + 4)) = make_uint4(im[0], im[1], im[2], im[3]);
+                        *reinterpret_cast<uint4*>(rowt + sw128_off(r, q + 4)) =
+                            make_uint4(im[0], im[1], im[2], im[3]);
                     }
-                }
-                // B: row n < L: [Re E_z | -Im E_z] of iz = n; n >= L: [Im E_z | Re E_z] of iz = n - L
-                for (int e = pt; e < kN * 4; e += kProd) {
-                    const int n = e >> 2, q = e & 3, z = n & (kL - 1);
-                    uint32_t v0[4], v1[4];
+                } else {
+                    // B (threads 256..447): row n < L: [Re E_z | -Im E_z] of
+                    // iz = n; n >= L: [Im E_z | Re E_z] of iz = n - L
+                    for (int e = pt - kL * 4; e < kN * 4; e += kProd - kL * 4) {
+                        const int n = e >> 2, q = e & 3, z = n & (kL - 1);
+                        uint32_t v0[4], v1[4];
+                        const float4* ez4 = reinterpret_cast<const float4*>(Ez + z * kTabRow + 8 * q);
 #pragma unroll
-                    for (int j = 0; j < 8; j += 2) {
-                        const float2 a0 = Ez[z * kWc + 8 * q + j], a1 = Ez[z * kWc + 8 * q + j + 1];
-                        if (n < kL) {
-                            v0[j / 2] = pack_h2(a0.x, a1.x);
-                            v1[j / 2] = pack_h2(-a0.y, -a1.y);
-                        } else {
-                            v0[j / 2] = pack_h2(a0.y, a1.y);
-                            v1[j / 2] = pack_h2(a0.x, a1.x);
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 a = ez4[j];   // atoms 2j, 2j + 1: (re, im, re, im)
+                            if (n < kL) {
+                                v0[j] = pack_h2(a.x, a.z);
+                                v1[j] = pack_h2(-a.y, -a.w);
+                            } else {
+                                v0[j] = pack_h2(a.y, a.w);
+                                v1[j] = pack_h2(a.x, a.z);
+                            }
                         }
+                        *reinterpret_cast<uint4*>(stB + sw128_off(n, q)) = make_uint4(v0[0], v0[1], v0[2], v0[3]);
+                        *reinterpret_cast<uint4*>(stB + sw128_off(n, q + 4)) = make_uint4(v1[0], v1[1], v1[2], v1[3]);
                     }
-                    *reinterpret_cast<uint4*>(stB + sw128_off(n, q)) = make_uint4(v0[0], v0[1], v0[2], v0[3]);
-                    *reinterpret_cast<uint4*>(stB + sw128_off(n, q + 4)) = make_uint4(v1[0], v1[1], v1[2], v1[3]);
                 }
                 fence_proxy_async_smem();
                 prod_sync();
