@@ -16,7 +16,8 @@
 // (K = 64: the 32 real parts, then the 32 imaginary parts) 448 producer
 // threads tabulate E_x (8 rows), E_y and E_z (64 rows each; E_y, E_z by
 // recurrence E[i + 1] = E[i] exp(-2 pi i dk a) from an exact start every 16
-// rows), build the A chunk (P, 4 tiles) and the B chunk in the K-major
+// rows; segment starts from the hardware sine and cosine after an exact
+// range reduction), build the A chunk (P, 4 tiles) and the B chunk in the K-major
 // 128-byte-swizzled layout, and hand the stage to two issuer threads, which
 // run 16 MMAs (M = 128, N = 128, K = 16) while the next stage is built.
 #include <cuda_fp16.h>
@@ -70,10 +71,13 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// exp(-2 pi i t) for t = k a given as 2 k a in units of pi
+// exp(-i pi x) for x = 2 k a (so exp(-2 pi i k a)): x reduced exactly to
+// [-1, 1] (x - 2 rint(x / 2) is exact in FP32 for |x| < 2^22), then the
+// hardware sine and cosine of pi x_r, absolute error a few 1e-7 on [-pi, pi]
 __device__ __forceinline__ float2 cexp_m2pi(float two_ka) {
+    const float xr = two_ka - 2.f * rintf(0.5f * two_ka);
     float s, c;
-    sincospif(two_ka, &s, &c);
+    __sincosf(3.14159265358979324f * xr, &s, &c);
     return make_float2(c, -s);
 }
 
