@@ -153,6 +153,37 @@ __device__ __forceinline__ void band_update(const BandSet& bs, int klo, int khi,
     }
 }
 
+// The same with the slot count fixed at compile time: kNB == 1 is the
+// single-band kernel (the ROI's band [klo, khi]; the BandSet is not read).
+template <int kNB>
+__device__ __forceinline__ void band_init_t(const BandSet& bs, int klo, float* best, int* bk) {
+    if (kNB == 1) {
+        best[0] = -1.f;
+        bk[0] = klo;
+    } else {
+        band_init(bs, klo, best, bk);
+    }
+}
+
+template <int kNB>
+__device__ __forceinline__ void band_update_t(const BandSet& bs, int klo, int khi, int f, float a, float* best,
+                                              int* bk) {
+    if (kNB == 1) {
+        if (f >= klo && f <= khi && a > best[0]) {
+            best[0] = a;
+            bk[0] = f;
+        }
+    } else {
+        band_update(bs, klo, khi, f, a, best, bk);
+    }
+}
+
+template <int kNB>
+__device__ __forceinline__ int band_count_t(const BandSet& bs) { return kNB == 1 ? 1 : band_count(bs); }
+
+template <int kNB>
+__device__ __forceinline__ int64_t band_off_t(const BandSet& bs, int b) { return kNB == 1 ? 0 : bs.off[b]; }
+
 // ROI rank ranges of a signature launch (ranks index the longest-first order)
 constexpr int kRanksAll = 0;       // [0, nroi)
 constexpr int kRanksBig = 1;       // [0, n_big): ROIs above 2048 atoms

@@ -56,6 +56,9 @@ struct SigParams {
     BandSet bands;
 };
 
+// kNB: band slots of the epilogue (1: the ROI's own band; APTIDX_MAX_BANDS:
+// the pass's BandSet)
+template <int kNB>
 __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int NB = 1 << p.m;
@@ -161,9 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                 __syncthreads();
                 if (tid < kDirs) {
                     const int64_t v = (int64_t)tile * kDirs + tid;
-                    float best[APTIDX_MAX_BANDS];
-                    int bk[APTIDX_MAX_BANDS];
-                    band_init(p.bands, klo, best, bk);
+                    float best[kNB];
+                    int bk[kNB];
+                    band_init_t<kNB>(p.bands, klo, best, bk);
                     for (int kk = 0; kk < K; ++kk) {
                         const int g = kk / kKpw, q = kk % kKpw;
                         float sr = 0.f, si = 0.f;
@@ -172,23 +175,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                             sr += t.x;
                             si += t.y;
                         }
-                        band_update(p.bands, klo, khi, klo + kk, sqrtf(sr * sr + si * si), best, bk);
+                        band_update_t<kNB>(p.bands, klo, khi, klo + kk, sqrtf(sr * sr + si * si), best, bk);
                     }
                     if (v < p.nv) {
 #pragma unroll
-                        for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
-                            if (b < band_count(p.bands)) {
-                                p.S[p.bands.off[b] + out_base + tid] = best[b];
-                                if (p.argk) p.argk[p.bands.off[b] + out_base + tid] = (uint16_t)bk[b];
+                        for (int b = 0; b < kNB; ++b) {
+                            if (b < band_count_t<kNB>(p.bands)) {
+                                p.S[band_off_t<kNB>(p.bands, b) + out_base + tid] = best[b];
+                                if (p.argk) p.argk[band_off_t<kNB>(p.bands, b) + out_base + tid] = (uint16_t)bk[b];
                             }
                         }
                     }
                 }
             } else {
-                float b0[APTIDX_MAX_BANDS], b1[APTIDX_MAX_BANDS];
-                int bk0[APTIDX_MAX_BANDS], bk1[APTIDX_MAX_BANDS];
-                band_init(p.bands, klo, b0, bk0);
-                band_init(p.bands, klo, b1, bk1);
+                float b0[kNB], b1[kNB];
+                int bk0[kNB], bk1[kNB];
+                band_init_t<kNB>(p.bands, klo, b0, bk0);
+                band_init_t<kNB>(p.bands, klo, b1, bk1);
                 for (int g = warp; g < G; g += kWarps) {
                     const int k0 = klo + g * kKpw;
                     float re[kKpw][2], im[kKpw][2];
@@ -216,15 +219,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                         if (k0 + q > khi) break;
                         const float a0 = sqrtf(re[q][0] * re[q][0] + im[q][0] * im[q][0]);
                         const float a1 = sqrtf(re[q][1] * re[q][1] + im[q][1] * im[q][1]);
-                        band_update(p.bands, klo, khi, k0 + q, a0, b0, bk0);
-                        band_update(p.bands, klo, khi, k0 + q, a1, b1, bk1);
+                        band_update_t<kNB>(p.bands, klo, khi, k0 + q, a0, b0, bk0);
+                        band_update_t<kNB>(p.bands, klo, khi, k0 + q, a1, b1, bk1);
                     }
                 }
                 // per band, each warp's best over its frequency groups; the
                 // band's slab of PART holds kWarps x kDirs (value, k) pairs
 #pragma unroll
-                for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
-                    if (b < band_count(p.bands)) {
+                for (int b = 0; b < kNB; ++b) {
+                    if (b < band_count_t<kNB>(p.bands)) {
                         PART[((size_t)b * kWarps + warp) * kDirs + 2 * lane] = make_float2(b0[b], __int_as_float(bk0[b]));
                         PART[((size_t)b * kWarps + warp) * kDirs + 2 * lane + 1] =
                             make_float2(b1[b], __int_as_float(bk1[b]));
@@ -233,9 +236,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                 __syncthreads();
                 if (tid < kDirs) {
                     const int64_t v = (int64_t)tile * kDirs + tid;
-                    for (int b = 0; b < band_count(p.bands); ++b) {
+                    for (int b = 0; b < band_count_t<kNB>(p.bands); ++b) {
                         float best = -1.f;
-                        int bk = p.bands.n == 0 ? klo : p.bands.lo[b];
+                        int bk = kNB == 1 ? klo : p.bands.lo[b];
                         for (int w = 0; w < kWarps; ++w) {
                             const float2 t = PART[((size_t)b * kWarps + w) * kDirs + tid];
                             const int k = __float_as_int(t.y);
@@ -245,8 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
                             }
                         }
                         if (v < p.nv) {
-                            p.S[p.bands.off[b] + out_base + tid] = best;
-                            if (p.argk) p.argk[p.bands.off[b] + out_base + tid] = (uint16_t)bk;
+                            p.S[band_off_t<kNB>(p.bands, b) + out_base + tid] = best;
+                            if (p.argk) p.argk[band_off_t<kNB>(p.bands, b) + out_base + tid] = (uint16_t)bk;
                         }
                     }
                 }
@@ -296,7 +299,9 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     cap = min(cap, 4096) & ~15;
     if (cap < 256) return cudaErrorInvalidConfiguration;
     const size_t smem = plain_smem_bytes(c->m, cap);
-    cudaError_t e = cudaFuncSetAttribute(k_sig_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool multi = !hist_out && c->multi.n > 0;
+    auto kern = multi ? k_sig_plain<APTIDX_MAX_BANDS> : k_sig_plain<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
 
     SigParams p;
@@ -329,12 +334,12 @@ cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* 
     p.bands = hist_out ? BandSet() : c->multi;
     if ((e = cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     per_sm = max(per_sm, 1);
     int64_t grid = tmin<int64_t>((int64_t)c->sm_count * per_sm, p.n_items);
     if (rank_mode == kRanksBig && !hist_out) grid = tmin<int64_t>(grid, (int64_t)c->sm_count);
     if (grid < 1) return cudaSuccess;
-    k_sig_plain<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
+    kern<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -465,7 +470,7 @@ extern "C" int aptidx_signatures_noalloc(const float* xc4, const int64_t* off, c
     cap = std::min(cap, 4096) & ~15;
     if (cap < 256) return APTIDX_E_CUDA;
     const size_t smem = plain_smem_bytes(m, cap);
-    if (cudaFuncSetAttribute(k_sig_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_sig_plain<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return APTIDX_E_CUDA;
     }
@@ -495,9 +500,9 @@ extern "C" int aptidx_signatures_noalloc(const float* xc4, const int64_t* off, c
     p.rank_mode = kRanksAll;
     p.nroi = nroi;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_plain<1>, kThreads, smem);
     per_sm = std::max(per_sm, 1);
     const int64_t grid = std::min<int64_t>((int64_t)sm_count * per_sm, p.n_items);
-    k_sig_plain<<<(unsigned)grid, kThreads, smem, s>>>(p);
+    k_sig_plain<1><<<(unsigned)grid, kThreads, smem, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? APTIDX_OK : APTIDX_E_CUDA;
 }

@@ -79,6 +79,9 @@ __device__ __forceinline__ uint32_t idesc_f16(int n) { return idesc_f16_mk(kRows
 
 // ---- the kernel ----------------------------------------------------------------
 
+// kNB: band slots of the epilogue (1: the ROI's own band; APTIDX_MAX_BANDS:
+// the pass's BandSet, aptidx_compute_signatures_multi)
+template <int kNB>
 __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled operands; offset arithmetic on the
@@ -293,9 +296,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 // warps 0, 1 hold rows 0-63 (bins of the first half), warps
                 // 2, 3 rows 64-127; per frequency group the second-half warps
                 // hand their sums over through shared memory
-                float best[APTIDX_MAX_BANDS];
-                int bk[APTIDX_MAX_BANDS];
-                band_init(p.bands, klo, best, bk);
+                float best[kNB];
+                int bk[kNB];
+                band_init_t<kNB>(p.bands, klo, best, bk);
                 const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
                 const int n_iss = nbatch == 1 ? p.n_iss : 1;
                 const uint32_t cols_b = (uint32_t)(16 * p.gb);
@@ -332,7 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                                 const float sg = (f & 1) ? -1.f : 1.f;
                                 const float xr = re[q] + sg * EX[dir * 8 + 2 * q];
                                 const float xi = im[q] + sg * EX[dir * 8 + 2 * q + 1];
-                                band_update(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f, best, bk);
+                                band_update_t<kNB>(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f, best,
+                                                   bk);
                             }
                         }
                         asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -343,10 +347,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     if (v < p.nv) {
                         const int64_t o = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv + v;
 #pragma unroll
-                        for (int b = 0; b < APTIDX_MAX_BANDS; ++b) {
-                            if (b < band_count(p.bands)) {
-                                p.S[p.bands.off[b] + o] = best[b];
-                                if (p.argk) p.argk[p.bands.off[b] + o] = (uint16_t)bk[b];
+                        for (int b = 0; b < kNB; ++b) {
+                            if (b < band_count_t<kNB>(p.bands)) {
+                                p.S[band_off_t<kNB>(p.bands, b) + o] = best[b];
+                                if (p.argk) p.argk[band_off_t<kNB>(p.bands, b) + o] = (uint16_t)bk[b];
                             }
                         }
                     }
@@ -465,7 +469,9 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     cap = std::min(cap, kTcMaxAtoms) & ~15;
     if (cap < 256) return cudaErrorInvalidConfiguration;
     const size_t smem = tc_smem_bytes(c->m, cap);
-    if ((e = cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    const bool multi = !hist_out && c->multi.n > 0;
+    auto kern = multi ? k_sig_tc<APTIDX_MAX_BANDS> : k_sig_tc<1>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     TcParams p;
     p.atoms = c->d_atoms;
@@ -498,12 +504,12 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     p.bands = hist_out ? BandSet() : c->multi;
     if ((e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sig_tc, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     per_sm = std::max(1, std::min(per_sm, (int)(512 / p.tmem_cols)));
     const int64_t items = (hist_out ? 1 : p.nroi) * (int64_t)p.items_per_roi;
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, items);
     if (grid < 1) return cudaSuccess;
-    k_sig_tc<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
+    kern<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
     c->launches += hist_out ? 0 : 1;   // the FP32 launch above is counted by the caller's phase count
     return cudaGetLastError();
 }
