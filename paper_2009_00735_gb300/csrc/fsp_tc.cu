@@ -13,13 +13,14 @@
 //
 // Work item = (ROI, 8 consecutive ix) = 512 rows = 4 M tiles of 128, their
 // accumulators filling the 512 tensor-memory columns.  Per chunk of 32 atoms
-// (K = 64: the 32 real parts, then the 32 imaginary parts) 448 producer
-// threads tabulate E_x (8 rows), E_y and E_z (64 rows each; E_y, E_z by
-// recurrence E[i + 1] = E[i] exp(-2 pi i dk a) from an exact start every 16
-// rows; segment starts from the hardware sine and cosine after an exact
-// range reduction), build the A chunk (P, 4 tiles) and the B chunk in the K-major
-// 128-byte-swizzled layout, and hand the stage to two issuer threads, which
-// run 16 MMAs (M = 128, N = 128, K = 16) while the next stage is built.
+// (K = 64: the 32 real parts, then the 32 imaginary parts) four table warps
+// tabulate E_x (8 rows, FP32), E_y and E_z (64 rows each, fp16; by
+// recurrence E[i + 1] = E[i] exp(-2 pi i dk a) over 16-row segments whose
+// starts come from the hardware sine and cosine after an exact range
+// reduction) into one of two table sets, ten builder warps turn the other
+// set into the A stage (P, 4 tiles) and the B stage in the K-major
+// 128-byte-swizzled layout, and two issuer threads run the 16 MMAs
+// (M = 128, N = 128, K = 16) of the previous stage.
 #include <cuda_fp16.h>
 
 #include "tcgen05.cuh"
@@ -36,14 +37,18 @@ constexpr int kIxItem = kTiles * kTileRows / kL;    // 8 values of ix per item
 constexpr int kItemsRoi = kL / kIxItem;             // 8 items per ROI
 constexpr int kWc = 32;                             // atoms per chunk (K = 64)
 constexpr int kThreadsF = 512;
-constexpr int kIss = 2;                             // issuer warps: tiles 0-1 and 2-3
-constexpr int kProd0 = kIss * 32;                   // first producer thread
-constexpr int kProd = kThreadsF - kProd0;           // 448 producer threads
+constexpr int kIss = 2;                             // issuer warps 0, 1: tiles 0-1 and 2-3
+constexpr int kTab0 = kIss * 32;                    // table warps 2..5
+constexpr int kTabThreads = 128;
+constexpr int kBld0 = kTab0 + kTabThreads;          // builder warps 6..15
+constexpr int kBld = kThreadsF - kBld0;             // 320 builder threads
 constexpr int kStageA = kTiles * kTileRows * 128;   // 64 KB
 constexpr int kStageB = kN * 128;                   // 16 KB
 constexpr int kStage = kStageA + kStageB;           // 80 KB
-constexpr int kTabRow = kWc + 2;                    // table row stride (float2): 16-byte reads, rows spread over banks
-constexpr int kTabBytes = (kIxItem + 2 * kL) * kTabRow * 8;
+constexpr int kTabRow = kWc + 2;                    // E_x row stride (float2): 16-byte reads, rows spread over banks
+constexpr int kTabRowH = kWc + 4;                   // E_y, E_z row stride (half2)
+constexpr int kTabSet = kIxItem * kTabRow * 8 + 2 * kL * kTabRowH * 4;   // one table set
+constexpr int kTabBytes = 2 * kTabSet;              // double buffered
 constexpr int kSeg = 16;                            // recurrence segment (rows)
 
 static_assert(kL == 64, "the tiling assumes L = 64");
@@ -63,9 +68,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void prod_sync() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory");
-}
+__device__ __forceinline__ void bld_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kBld) : "memory"); }
+__device__ __forceinline__ void tab_sync() { asm volatile("bar.sync 2, %0;" ::"r"(kTabThreads) : "memory"); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -95,23 +99,26 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int j) {
 __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    float2* Ex = reinterpret_cast<float2*>(smem + 2 * kStage);
-    float2* Ey = Ex + kIxItem * kTabRow;
-    float2* Ez = Ey + kL * kTabRow;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kStage + kTabBytes);
-    uint64_t* full = bars;          // [2]: producers -> issuers
-    uint64_t* empty = bars + 2;     // [2]: MMA completion -> producers
+    unsigned char* tabs = smem + 2 * kStage;   // two table sets: E_x (float2), E_y, E_z (half2)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tabs + kTabBytes);
+    uint64_t* full = bars;          // [2] stage built -> issuers
+    uint64_t* empty = bars + 2;     // [2] stage's MMAs completed -> builders
     uint64_t* accum = bars + 4;     // all MMAs of the item completed
-    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 5);
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 6);
-    int* fail_s = reinterpret_cast<int*>(bars + 7);
+    uint64_t* tfull = bars + 5;     // [2] table set filled -> builders
+    uint64_t* tempty = bars + 7;    // [2] table set consumed -> table warps
+    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 9);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 10);
+    int* fail_s = reinterpret_cast<int*>(bars + 11);
+    const volatile int* vfail = fail_s;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&empty[0], kIss);
-        mbar_init(&empty[1], kIss);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kIss);
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 1);
+        }
         mbar_init(accum, kIss);
         *fail_s = 0;
         fence_barrier_init();
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
     const uint32_t st_addr = smem_u32(smem);
     const uint32_t idesc = idesc_f16_mk(kTileRows, kN, false);
 
-    uint32_t cg = 0;      // chunks issued so far by this CTA (stage ring position)
+    uint32_t cg = 0;      // chunks handled so far by this CTA (stage and table-set ring position)
     uint32_t nitem = 0;   // items finished so far (accumulator barrier phase)
     const int64_t n_items = p.nroi * kItemsRoi;
     for (;;) {
@@ -169,59 +176,80 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                 mma_commit(accum);   // also after a failure: the epilogue then waits on what was issued
             }
             __syncwarp();
-        } else {
-            // ---- producers ----
-            const int pt = tid - kProd0;
+        } else if (warp < kBld0 / 32) {
+            // ---- table warps: E_x (8 rows), E_y, E_z (64 rows each) of the
+            // chunk's 32 atoms into table set (chunk & 1), running up to two
+            // chunks ahead of the builders.  E_y, E_z by recurrence
+            // E[i + 1] = E[i] exp(-2 pi i dk a) over 16-row segments; lane = atom ----
+            const int tt = tid - kTab0;
             for (int c = 0; c < nch; ++c) {
-                const uint32_t s = (cg + c) & 1u, u = (cg + c) >> 1;
-                if (pt == 0 && u >= 1 && !mbar_wait_bounded(&empty[s], (u - 1) & 1u, p.status)) *fail_s = 1;
-                prod_sync();
-                const int w0 = c * kWc;
-                // tables: E_y, E_z by recurrence E[i + 1] = E[i] exp(-2 pi i dk a)
-                // in segments of 16 rows from an exact start; lane = atom, so
-                // every store writes whole table rows
-                const int wl = pt & 31;
-                const bool valid = w0 + wl < nw;
-                if (pt < 8 * 32) {
-                    const int axis = pt >> 7, seg = (pt >> 5) & 3;   // 0: y, 1: z
-                    const float a = valid ? (axis ? A[w0 + wl].z : A[w0 + wl].y) : 0.f;
+                const uint32_t cc = cg + c, b = cc & 1u, u = cc >> 1;
+                if (tt == 0 && u >= 1 && !*vfail && !mbar_wait_bounded(&tempty[b], (u - 1) & 1u, p.status)) *fail_s = 1;
+                tab_sync();
+                float2* Ex = reinterpret_cast<float2*>(tabs + b * kTabSet);
+                uint32_t* Eyh = reinterpret_cast<uint32_t*>(Ex + kIxItem * kTabRow);
+                uint32_t* Ezh = Eyh + kL * kTabRowH;
+                const int wl = lane, w = c * kWc + wl;
+                const bool valid = w < nw;
+                const float4 at = valid ? A[w] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int rep = 0; rep < 2; ++rep) {
+                    const int unit = tt + rep * kTabThreads;          // (axis, segment, atom)
+                    const int axis = unit >> 7, seg = (unit >> 5) & 3;
+                    const float a = axis ? at.z : at.y;
                     const int i0 = seg * kSeg;
                     float2 e = cexp_m2pi(2.f * fmaf((float)i0, p.dk, -p.kmax) * a);
                     const float2 d = cexp_m2pi(2.f * p.dk * a);
-                    float2* tab = axis ? Ez : Ey;
+                    uint32_t* tab = axis ? Ezh : Eyh;
                     for (int j = 0; j < kSeg; ++j) {
-                        tab[(i0 + j) * kTabRow + wl] = valid ? e : make_float2(0.f, 0.f);
+                        tab[(i0 + j) * kTabRowH + wl] = valid ? pack_h2(e.x, e.y) : 0u;
                         e = cmul(e, d);
                     }
-                } else {
-                    // E_x for the item's 8 values of ix, directly
-                    const float x = valid ? A[w0 + wl].x : 0.f;
-                    for (int ixl = (pt >> 5) - 8; ixl < kIxItem; ixl += kProd / 32 - 8) {
-                        const float k = fmaf((float)(g * kIxItem + ixl), p.dk, -p.kmax);
-                        Ex[ixl * kTabRow + wl] = valid ? cexp_m2pi(2.f * k * x) : make_float2(0.f, 0.f);
-                    }
+                    const int ixl = (tt >> 5) + 4 * rep;               // E_x: rows 0..7
+                    const float k = fmaf((float)(g * kIxItem + ixl), p.dk, -p.kmax);
+                    Ex[ixl * kTabRow + wl] = valid ? cexp_m2pi(2.f * k * at.x) : make_float2(0.f, 0.f);
                 }
-                prod_sync();
+                tab_sync();
+                if (tt == 0) mbar_arrive(&tfull[b]);
+            }
+        } else {
+            // ---- builders: the A stage (P = E_x E_y, 4 tiles) and the B stage ----
+            const int bt = tid - kBld0;
+            for (int c = 0; c < nch; ++c) {
+                const uint32_t cc = cg + c, s = cc & 1u, u = cc >> 1;
+                if (bt == 0 && !*vfail) {   // after a timeout the rest of the item runs unsynchronised
+                    if (u >= 1 && !mbar_wait_bounded(&empty[s], (u - 1) & 1u, p.status)) *fail_s = 1;
+                    if (!*vfail && !mbar_wait_bounded(&tfull[s], u & 1u, p.status)) *fail_s = 1;
+                }
+                bld_sync();
+                const float2* Ex = reinterpret_cast<const float2*>(tabs + s * kTabSet);
+                const uint32_t* Eyh = reinterpret_cast<const uint32_t*>(Ex + kIxItem * kTabRow);
+                const uint32_t* Ezh = Eyh + kL * kTabRowH;
                 unsigned char* stA = smem + s * kStage;
                 unsigned char* stB = stA + kStageA;
-                // A: row m = ixl * 64 + iy, K = [Re P of the 32 atoms | Im P].
-                // Threads 0..255 take unit (iy, q): E_y of atoms 8q .. 8q+7 in
-                // registers, all 8 values of ix (E_x reads are broadcasts).
-                if (pt < kL * 4) {
-                    const int iy = pt & (kL - 1), q = pt / kL;
-                    const float4* ey4 = reinterpret_cast<const float4*>(Ey + iy * kTabRow + 8 * q);
-                    float4 y[4];
+                if (bt < kL * 4) {
+                    // A: row m = ixl * 64 + iy, K = [Re P of the 32 atoms | Im P];
+                    // unit (iy, q): E_y of atoms 8q .. 8q+7 in registers, all 8
+                    // values of ix (E_x reads are broadcasts)
+                    const int iy = bt & (kL - 1), q = bt / kL;
+                    const uint4* ey4 = reinterpret_cast<const uint4*>(Eyh + iy * kTabRowH + 8 * q);
+                    float2 y[8];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) y[j] = ey4[j];   // two atoms each: (re, im, re, im)
+                    for (int h = 0; h < 2; ++h) {
+                        const uint4 v = ey4[h];
+                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) y[4 * h + j] = __half22float2(*reinterpret_cast<const __half2*>(&vv[j]));
+                    }
 #pragma unroll 2
                     for (int ixl = 0; ixl < kIxItem; ++ixl) {
                         const float4* ex4 = reinterpret_cast<const float4*>(Ex + ixl * kTabRow + 8 * q);
                         uint32_t re[4], im[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float4 x = ex4[j];
-                            const float2 p0 = cmul(make_float2(x.x, x.y), make_float2(y[j].x, y[j].y));
-                            const float2 p1 = cmul(make_float2(x.z, x.w), make_float2(y[j].z, y[j].w));
+                            const float4 x = ex4[j];   // atoms 2j, 2j + 1: (re, im, re, im)
+                            const float2 p0 = cmul(make_float2(x.x, x.y), y[2 * j]);
+                            const float2 p1 = cmul(make_float2(x.z, x.w), y[2 * j + 1]);
                             re[j] = pack_h2(p0.x, p1.x);
                             im[j] = pack_h2(p0.y, p1.y);
                         }
@@ -232,30 +260,31 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                             make_uint4(im[0], im[1], im[2], im[3]);
                     }
                 } else {
-                    // B (threads 256..447): row n < L: [Re E_z | -Im E_z] of
-                    // iz = n; n >= L: [Im E_z | Re E_z] of iz = n - L
-                    for (int e = pt - kL * 4; e < kN * 4; e += kProd - kL * 4) {
-                        const int n = e >> 2, q = e & 3, z = n & (kL - 1);
+                    // B: row n < L: [Re E_z | -Im E_z] of iz = n; n >= L:
+                    // [Im E_z | Re E_z] of iz = n - L (fp16 pairs moved as bits)
+                    for (int e = bt - kL * 4; e < kN * 4; e += kBld - kL * 4) {
+                        const int n = e & (kN - 1), q = e / kN, z = n & (kL - 1);   // 8 lanes: 8 rows, one q
+                        const uint4* ez4 = reinterpret_cast<const uint4*>(Ezh + z * kTabRowH + 8 * q);
+                        const uint4 h0 = ez4[0], h1 = ez4[1];
+                        const uint32_t hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
                         uint32_t v0[4], v1[4];
-                        const float4* ez4 = reinterpret_cast<const float4*>(Ez + z * kTabRow + 8 * q);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float4 a = ez4[j];   // atoms 2j, 2j + 1: (re, im, re, im)
-                            if (n < kL) {
-                                v0[j] = pack_h2(a.x, a.z);
-                                v1[j] = pack_h2(-a.y, -a.w);
-                            } else {
-                                v0[j] = pack_h2(a.y, a.w);
-                                v1[j] = pack_h2(a.x, a.z);
-                            }
+                            const uint32_t re = __byte_perm(hv[2 * j], hv[2 * j + 1], 0x5410);
+                            const uint32_t im = __byte_perm(hv[2 * j], hv[2 * j + 1], 0x7632);
+                            v0[j] = n < kL ? re : im;
+                            v1[j] = n < kL ? (im ^ 0x80008000u) : re;
                         }
                         *reinterpret_cast<uint4*>(stB + sw128_off(n, q)) = make_uint4(v0[0], v0[1], v0[2], v0[3]);
                         *reinterpret_cast<uint4*>(stB + sw128_off(n, q + 4)) = make_uint4(v1[0], v1[1], v1[2], v1[3]);
                     }
                 }
                 fence_proxy_async_smem();
-                prod_sync();
-                if (pt == 0) mbar_arrive(&full[s]);
+                bld_sync();
+                if (bt == 0) {
+                    mbar_arrive(&full[s]);
+                    mbar_arrive(&tempty[s]);
+                }
             }
         }
         cg += (uint32_t)nch;
