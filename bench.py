@@ -77,7 +77,7 @@ def tc_traffic_per_launch(n_roi):
     if not m:
         return None
     h = hashlib.sha256()
-    for f in ("signature_tc.cu", "common.cuh"):
+    for f in ("signature_tc.cu", "common.cuh", "tcgen05.cuh"):
         with open(os.path.join(ROOT, "paper_2009_00735_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest()[:16] != m.group(3):

@@ -14,13 +14,13 @@
 // Work item = (ROI, 8 consecutive ix) = 512 rows = 4 M tiles of 128, their
 // accumulators filling the 512 tensor-memory columns.  Per chunk of 32 atoms
 // (K = 64: the 32 real parts, then the 32 imaginary parts) four table warps
-// tabulate E_x (8 rows, FP32), E_y and E_z (64 rows each, fp16; by
+// tabulate E_x (8 rows), E_y and E_z (64 rows each) in fp16 pairs (E_y, E_z by
 // recurrence E[i + 1] = E[i] exp(-2 pi i dk a) over 16-row segments whose
 // starts come from the hardware sine and cosine after an exact range
 // reduction) into one of two table sets, ten builder warps turn the other
-// set into the A stage (P, 4 tiles) and the B stage in the K-major
-// 128-byte-swizzled layout, and two issuer threads run the 16 MMAs
-// (M = 128, N = 128, K = 16) of the previous stage.
+// set into the A stage (P = E_x E_y in fp16 pair arithmetic, 4 tiles) and
+// the B stage in the K-major 128-byte-swizzled layout, and two issuer
+// threads run the 16 MMAs (M = 128, N = 128, K = 16) of the previous stage.
 #include <cuda_fp16.h>
 
 #include "tcgen05.cuh"
@@ -45,9 +45,10 @@ constexpr int kBld = kThreadsF - kBld0;             // 320 builder threads
 constexpr int kStageA = kTiles * kTileRows * 128;   // 64 KB
 constexpr int kStageB = kN * 128;                   // 16 KB
 constexpr int kStage = kStageA + kStageB;           // 80 KB
-constexpr int kTabRow = kWc + 2;                    // E_x row stride (float2): 16-byte reads, rows spread over banks
-constexpr int kTabRowH = kWc + 4;                   // E_y, E_z row stride (half2)
-constexpr int kTabSet = kIxItem * kTabRow * 8 + 2 * kL * kTabRowH * 4;   // one table set
+// table rows of 32 atoms as fp16 pairs: words 0..15 = (Re a_2j, Re a_2j+1),
+// words 16..31 = (Im a_2j, Im a_2j+1); 36-word stride spreads rows over banks
+constexpr int kTabRowH = kWc + 4;
+constexpr int kTabSet = (kIxItem + 2 * kL) * kTabRowH * 4;   // one table set: E_x, E_y, E_z
 constexpr int kTabBytes = 2 * kTabSet;              // double buffered
 constexpr int kSeg = 16;                            // recurrence segment (rows)
 
@@ -85,6 +86,9 @@ __device__ __forceinline__ float2 cexp_m2pi(float two_ka) {
     return make_float2(c, -s);
 }
 
+__device__ __forceinline__ __half2 u2h2(uint32_t v) { return *reinterpret_cast<const __half2*>(&v); }
+__device__ __forceinline__ uint32_t h22u(__half2 h) { return *reinterpret_cast<const uint32_t*>(&h); }
+
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
     const __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -99,7 +103,7 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int j) {
 __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char* tabs = smem + 2 * kStage;   // two table sets: E_x (float2), E_y, E_z (half2)
+    unsigned char* tabs = smem + 2 * kStage;   // two table sets: E_x, E_y, E_z as fp16 pairs
     uint64_t* bars = reinterpret_cast<uint64_t*>(tabs + kTabBytes);
     uint64_t* full = bars;          // [2] stage built -> issuers
     uint64_t* empty = bars + 2;     // [2] stage's MMAs completed -> builders
@@ -180,34 +184,43 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
             // ---- table warps: E_x (8 rows), E_y, E_z (64 rows each) of the
             // chunk's 32 atoms into table set (chunk & 1), running up to two
             // chunks ahead of the builders.  E_y, E_z by recurrence
-            // E[i + 1] = E[i] exp(-2 pi i dk a) over 16-row segments; lane = atom ----
+            // E[i + 1] = E[i] exp(-2 pi i dk a) over 16-row segments in FP32,
+            // stored as fp16 pairs; lane = atom, neighbouring lanes pair up ----
             const int tt = tid - kTab0;
+            const bool even = (lane & 1) == 0;
+            const uint32_t sel = even ? 0x5410u : 0x3276u;   // (own Re, other Re) | (other Im, own Im)
+            const int col = (lane >> 1) + (even ? 0 : kWc / 2);
             for (int c = 0; c < nch; ++c) {
                 const uint32_t cc = cg + c, b = cc & 1u, u = cc >> 1;
                 if (tt == 0 && u >= 1 && !*vfail && !mbar_wait_bounded(&tempty[b], (u - 1) & 1u, p.status)) *fail_s = 1;
                 tab_sync();
-                float2* Ex = reinterpret_cast<float2*>(tabs + b * kTabSet);
-                uint32_t* Eyh = reinterpret_cast<uint32_t*>(Ex + kIxItem * kTabRow);
+                uint32_t* Exh = reinterpret_cast<uint32_t*>(tabs + b * kTabSet);
+                uint32_t* Eyh = Exh + kIxItem * kTabRowH;
                 uint32_t* Ezh = Eyh + kL * kTabRowH;
-                const int wl = lane, w = c * kWc + wl;
+                const int w = c * kWc + lane;
                 const bool valid = w < nw;
                 const float4 at = valid ? A[w] : make_float4(0.f, 0.f, 0.f, 0.f);
+                auto put = [&](uint32_t* row, float2 e) {
+                    const uint32_t own = valid ? pack_h2(e.x, e.y) : 0u;
+                    const uint32_t oth = __shfl_xor_sync(0xffffffffu, own, 1);
+                    row[col] = __byte_perm(own, oth, sel);
+                };
+                const int i0 = (tt >> 5) * kSeg;
+                const float k0 = fmaf((float)i0, p.dk, -p.kmax);
+                float2 ey = cexp_m2pi(2.f * k0 * at.y), ez = cexp_m2pi(2.f * k0 * at.z);
+                const float2 dy = cexp_m2pi(2.f * p.dk * at.y), dz = cexp_m2pi(2.f * p.dk * at.z);
+#pragma unroll 4
+                for (int j = 0; j < kSeg; ++j) {
+                    put(Eyh + (i0 + j) * kTabRowH, ey);
+                    put(Ezh + (i0 + j) * kTabRowH, ez);
+                    ey = cmul(ey, dy);
+                    ez = cmul(ez, dz);
+                }
 #pragma unroll
                 for (int rep = 0; rep < 2; ++rep) {
-                    const int unit = tt + rep * kTabThreads;          // (axis, segment, atom)
-                    const int axis = unit >> 7, seg = (unit >> 5) & 3;
-                    const float a = axis ? at.z : at.y;
-                    const int i0 = seg * kSeg;
-                    float2 e = cexp_m2pi(2.f * fmaf((float)i0, p.dk, -p.kmax) * a);
-                    const float2 d = cexp_m2pi(2.f * p.dk * a);
-                    uint32_t* tab = axis ? Ezh : Eyh;
-                    for (int j = 0; j < kSeg; ++j) {
-                        tab[(i0 + j) * kTabRowH + wl] = valid ? pack_h2(e.x, e.y) : 0u;
-                        e = cmul(e, d);
-                    }
-                    const int ixl = (tt >> 5) + 4 * rep;               // E_x: rows 0..7
+                    const int ixl = (tt >> 5) + 4 * rep;
                     const float k = fmaf((float)(g * kIxItem + ixl), p.dk, -p.kmax);
-                    Ex[ixl * kTabRow + wl] = valid ? cexp_m2pi(2.f * k * at.x) : make_float2(0.f, 0.f);
+                    put(Exh + ixl * kTabRowH, cexp_m2pi(2.f * k * at.x));
                 }
                 tab_sync();
                 if (tt == 0) mbar_arrive(&tfull[b]);
@@ -222,36 +235,31 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                     if (!*vfail && !mbar_wait_bounded(&tfull[s], u & 1u, p.status)) *fail_s = 1;
                 }
                 bld_sync();
-                const float2* Ex = reinterpret_cast<const float2*>(tabs + s * kTabSet);
-                const uint32_t* Eyh = reinterpret_cast<const uint32_t*>(Ex + kIxItem * kTabRow);
+                const uint32_t* Exh = reinterpret_cast<const uint32_t*>(tabs + s * kTabSet);
+                const uint32_t* Eyh = Exh + kIxItem * kTabRowH;
                 const uint32_t* Ezh = Eyh + kL * kTabRowH;
                 unsigned char* stA = smem + s * kStage;
                 unsigned char* stB = stA + kStageA;
                 if (bt < kL * 4) {
                     // A: row m = ixl * 64 + iy, K = [Re P of the 32 atoms | Im P];
                     // unit (iy, q): E_y of atoms 8q .. 8q+7 in registers, all 8
-                    // values of ix (E_x reads are broadcasts)
+                    // values of ix (E_x reads are broadcasts); P in fp16 pairs
                     const int iy = bt & (kL - 1), q = bt / kL;
-                    const uint4* ey4 = reinterpret_cast<const uint4*>(Eyh + iy * kTabRowH + 8 * q);
-                    float2 y[8];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint4 v = ey4[h];
-                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) y[4 * h + j] = __half22float2(*reinterpret_cast<const __half2*>(&vv[j]));
-                    }
-#pragma unroll 2
+                    const uint4 yr4 = *reinterpret_cast<const uint4*>(Eyh + iy * kTabRowH + 4 * q);
+                    const uint4 yi4 = *reinterpret_cast<const uint4*>(Eyh + iy * kTabRowH + kWc / 2 + 4 * q);
+                    const __half2 yr[4] = {u2h2(yr4.x), u2h2(yr4.y), u2h2(yr4.z), u2h2(yr4.w)};
+                    const __half2 yi[4] = {u2h2(yi4.x), u2h2(yi4.y), u2h2(yi4.z), u2h2(yi4.w)};
+#pragma unroll 4
                     for (int ixl = 0; ixl < kIxItem; ++ixl) {
-                        const float4* ex4 = reinterpret_cast<const float4*>(Ex + ixl * kTabRow + 8 * q);
+                        const uint4 xr4 = *reinterpret_cast<const uint4*>(Exh + ixl * kTabRowH + 4 * q);
+                        const uint4 xi4 = *reinterpret_cast<const uint4*>(Exh + ixl * kTabRowH + kWc / 2 + 4 * q);
+                        const __half2 xr[4] = {u2h2(xr4.x), u2h2(xr4.y), u2h2(xr4.z), u2h2(xr4.w)};
+                        const __half2 xi[4] = {u2h2(xi4.x), u2h2(xi4.y), u2h2(xi4.z), u2h2(xi4.w)};
                         uint32_t re[4], im[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float4 x = ex4[j];   // atoms 2j, 2j + 1: (re, im, re, im)
-                            const float2 p0 = cmul(make_float2(x.x, x.y), y[2 * j]);
-                            const float2 p1 = cmul(make_float2(x.z, x.w), y[2 * j + 1]);
-                            re[j] = pack_h2(p0.x, p1.x);
-                            im[j] = pack_h2(p0.y, p1.y);
+                            re[j] = h22u(__hfma2(xr[j], yr[j], __hneg2(__hmul2(xi[j], yi[j]))));
+                            im[j] = h22u(__hfma2(xr[j], yi[j], __hmul2(xi[j], yr[j])));
                         }
                         const int m = ixl * kL + iy, t = m >> 7, r = m & 127;
                         unsigned char* rowt = stA + t * (kTileRows * 128);
@@ -261,22 +269,17 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                     }
                 } else {
                     // B: row n < L: [Re E_z | -Im E_z] of iz = n; n >= L:
-                    // [Im E_z | Re E_z] of iz = n - L (fp16 pairs moved as bits)
+                    // [Im E_z | Re E_z] of iz = n - L (fp16 pairs moved as bits,
+                    // the sign flipped in the bits)
                     for (int e = bt - kL * 4; e < kN * 4; e += kBld - kL * 4) {
                         const int n = e & (kN - 1), q = e / kN, z = n & (kL - 1);   // 8 lanes: 8 rows, one q
-                        const uint4* ez4 = reinterpret_cast<const uint4*>(Ezh + z * kTabRowH + 8 * q);
-                        const uint4 h0 = ez4[0], h1 = ez4[1];
-                        const uint32_t hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                        uint32_t v0[4], v1[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const uint32_t re = __byte_perm(hv[2 * j], hv[2 * j + 1], 0x5410);
-                            const uint32_t im = __byte_perm(hv[2 * j], hv[2 * j + 1], 0x7632);
-                            v0[j] = n < kL ? re : im;
-                            v1[j] = n < kL ? (im ^ 0x80008000u) : re;
-                        }
-                        *reinterpret_cast<uint4*>(stB + sw128_off(n, q)) = make_uint4(v0[0], v0[1], v0[2], v0[3]);
-                        *reinterpret_cast<uint4*>(stB + sw128_off(n, q + 4)) = make_uint4(v1[0], v1[1], v1[2], v1[3]);
+                        const uint4 zr = *reinterpret_cast<const uint4*>(Ezh + z * kTabRowH + 4 * q);
+                        const uint4 zi = *reinterpret_cast<const uint4*>(Ezh + z * kTabRowH + kWc / 2 + 4 * q);
+                        const uint32_t f = 0x80008000u;
+                        const uint4 v0 = n < kL ? zr : zi;
+                        const uint4 v1 = n < kL ? make_uint4(zi.x ^ f, zi.y ^ f, zi.z ^ f, zi.w ^ f) : zr;
+                        *reinterpret_cast<uint4*>(stB + sw128_off(n, q)) = v0;
+                        *reinterpret_cast<uint4*>(stB + sw128_off(n, q + 4)) = v1;
                     }
                 }
                 fence_proxy_async_smem();
