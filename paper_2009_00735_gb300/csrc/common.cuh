@@ -115,6 +115,113 @@ __device__ __forceinline__ void hist_tile(uint32_t* H, const float4* A, int cn, 
     for (; j < cn; j += W) hist_add_atom<kMasked>(hbase, A[j], d0, d1, scale, magic, nbm1);
 }
 
+// Packed FP32 pairs (f32x2): each half is one IEEE FP32 operation with the
+// stated rounding, so a pair gives bit for bit the two scalar results.
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma_rd(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_dup(float v) {
+    return ((uint64_t)__float_as_uint(v) << 32) | (uint64_t)__float_as_uint(v);
+}
+
+// Rearranges staged atoms in place for the paired histogram loop: the
+// 32-byte block of atoms 2p, 2p + 1 becomes (x_a, x_b, y_a, y_b | z_a, z_b,
+// w_a, w_b), so that one 16-byte and one 8-byte load give the coordinates
+// of both atoms as FP32 pairs.  A trailing odd atom keeps its layout.
+__device__ __forceinline__ void pair_atoms(float4* A, int n, int tid, int nthreads) {
+    for (int q = tid; q < (n >> 1); q += nthreads) {
+        const float4 a = A[2 * q], b = A[2 * q + 1];
+        A[2 * q] = make_float4(a.x, b.x, a.y, b.y);
+        A[2 * q + 1] = make_float4(a.z, b.z, a.w, b.w);
+    }
+}
+
+// Per-lane constants of the paired loop: the lane's two directions and the
+// binning scale and magic, each duplicated into both halves of a pair.
+struct PairDirs {
+    uint64_t x0, y0, z0, x1, y1, z1, sc, mg;
+};
+
+__device__ __forceinline__ PairDirs pair_dirs(float4 d0, float4 d1, float scale, float magic) {
+    PairDirs q;
+    q.x0 = f2_dup(d0.x);
+    q.y0 = f2_dup(d0.y);
+    q.z0 = f2_dup(d0.z);
+    q.x1 = f2_dup(d1.x);
+    q.y1 = f2_dup(d1.y);
+    q.z1 = f2_dup(d1.z);
+    q.sc = f2_dup(scale);
+    q.mg = f2_dup(magic);
+    return q;
+}
+
+// Two atoms (one paired block) into the histograms of a 64-direction tile:
+// the projections and the binning of Eq. 1 in the scalar order (x, then
+// y, then z; fma rounding down for the bin) on FP32 pairs, then the four
+// increments of hist_add_atom's unmasked form.
+__device__ __forceinline__ void hist_add_pair(uint32_t hbase, ulonglong2 xy, uint64_t zz, const PairDirs& q) {
+    const uint64_t s0 = f2_fma(zz, q.z0, f2_fma(xy.y, q.y0, f2_mul(xy.x, q.x0)));
+    const uint64_t s1 = f2_fma(zz, q.z1, f2_fma(xy.y, q.y1, f2_mul(xy.x, q.x1)));
+    const uint64_t t0 = f2_fma_rd(s0, q.sc, q.mg);
+    const uint64_t t1 = f2_fma_rd(s1, q.sc, q.mg);
+    const uint32_t base = hbase - 0x80000000u;   // (t - 0x4B000000) * 128 + hbase, wrapping
+    const uint32_t wa0 = (uint32_t)t0 * 128u + base, wb0 = (uint32_t)(t0 >> 32) * 128u + base;
+    const uint32_t wa1 = (uint32_t)t1 * 128u + base, wb1 = (uint32_t)(t1 >> 32) * 128u + base;
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wa0), "r"(1u) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wb0), "r"(1u) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wa1), "r"(0x10000u) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wb1), "r"(0x10000u) : "memory");
+}
+
+// hist_tile<W, false> over atoms staged by pair_atoms: warp w takes the
+// pairs w, w + W, w + 2W, ...; the odd trailing atom goes to warp
+// (cn / 2) % W.
+template <int W>
+__device__ __forceinline__ void hist_tile_pairs(uint32_t* H, const float4* A, int cn, int warp, int lane,
+                                                float4 d0, float4 d1, float scale, float magic) {
+    const uint32_t hbase = smem_u32(H) + 4u * (uint32_t)lane;
+    const PairDirs q = pair_dirs(d0, d1, scale, magic);
+    const int np = cn >> 1;
+    int j = warp;
+    auto ld_xy = [&](int i) { return *reinterpret_cast<const ulonglong2*>(A + 2 * i); };
+    auto ld_z = [&](int i) { return *reinterpret_cast<const uint64_t*>(A + 2 * i + 1); };
+    if (j + W < np) {
+        // two pairs at a time, the next two pairs' loads issued first
+        ulonglong2 xa = ld_xy(j), xb = ld_xy(j + W);
+        uint64_t za = ld_z(j), zb = ld_z(j + W);
+        for (; j + 3 * W < np; j += 2 * W) {
+            const ulonglong2 nxa = ld_xy(j + 2 * W), nxb = ld_xy(j + 3 * W);
+            const uint64_t nza = ld_z(j + 2 * W), nzb = ld_z(j + 3 * W);
+            hist_add_pair(hbase, xa, za, q);
+            hist_add_pair(hbase, xb, zb, q);
+            xa = nxa;
+            xb = nxb;
+            za = nza;
+            zb = nzb;
+        }
+        hist_add_pair(hbase, xa, za, q);
+        hist_add_pair(hbase, xb, zb, q);
+        j += 2 * W;
+    }
+    for (; j < np; j += W) hist_add_pair(hbase, ld_xy(j), ld_z(j), q);
+    if ((cn & 1) && warp == np % W) {
+        const float4 d0s = d0, d1s = d1;
+        hist_add_atom<false>(hbase, A[cn - 1], d0s, d1s, scale, magic, 0);
+    }
+}
+
 // Debug export of a tile's histograms: h_out[v * 2^m + b] for v < nv.
 __device__ __forceinline__ void hist_export(const uint32_t* H, int NB, int tile, int nv, uint16_t* h_out, int tid,
                                             int nthreads) {

@@ -88,7 +88,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     // shared array keeps the pointers in the shared address space
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int NB = 1 << p.m;
-    const int nbm1 = NB - 1;
     const int KB = NB / 128;   // 1 KB K-blocks of the B operand (K = 2^m / 2 rows)
     uint32_t* H = reinterpret_cast<uint32_t*>(smem);
     unsigned char* BT = smem + (size_t)NB * 128;
@@ -151,9 +150,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         const int t0 = grp * p.tiles_per_item;
         const int t1 = min(t0 + p.tiles_per_item, p.tiles_per_roi);
         const bool one_chunk = nw <= p.atom_cap;
-        if (one_chunk && !stage_atoms(A, p.atoms + abase, nw, &bars[0], ph_atoms, p.status, flag)) {
-            failed = true;
-            break;
+        if (one_chunk) {
+            if (!stage_atoms(A, p.atoms + abase, nw, &bars[0], ph_atoms, p.status, flag)) {
+                failed = true;
+                break;
+            }
+            pair_atoms(A, nw, tid, kThreads);
+            __syncthreads();
         }
 
         for (int tile = t0; tile < t1 && !failed; ++tile) {
@@ -162,11 +165,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
             const float4 d1 = p.dirs[(int64_t)tile * kDirs + 2 * lane + 1];
             for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
                 const int cn = min(p.atom_cap, nw - c0);
-                if (!one_chunk && !stage_atoms(A, p.atoms + abase + c0, cn, &bars[0], ph_atoms, p.status, flag)) {
-                    failed = true;
-                    break;
+                if (!one_chunk) {
+                    if (!stage_atoms(A, p.atoms + abase + c0, cn, &bars[0], ph_atoms, p.status, flag)) {
+                        failed = true;
+                        break;
+                    }
+                    pair_atoms(A, cn, tid, kThreads);
+                    __syncthreads();
                 }
-                hist_tile<kWarps, false>(H, A, cn, warp, lane, d0, d1, scale, magic, nbm1);
+                hist_tile_pairs<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic);
                 if (!one_chunk) __syncthreads();
             }
             if (failed) break;
