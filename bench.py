@@ -395,38 +395,45 @@ def run_gb300(args):
                        "rois_per_s": n_pi / (m_ms / 1e3),
                        "set": "Halton points through Shoemake's map, reduced to the cubic fundamental zone"}
 
-    # reciprocal-space signatures (Eq. 2) of the same ROIs on the 64^3 grid
-    # (not part of the step): tensor-core GEMMs, the paper's L_D = 64 case
+    # reciprocal-space signatures (Eq. 2) of the same ROIs (not part of the
+    # step): tensor-core GEMMs on the paper's L_D = 64 and L_D = 512 grids
     fsp = None
     if not args.no_fsp and tc_ok:
-        L = apt.APTIDX_FSP_L
-        n_f = min(nroi, 4096)
-        apt.aptidx_set_rois(h, torch.from_numpy(w.centres[:n_f]).cuda(), torch.from_numpy(w.radii[:n_f]).cuda())
-        amp = torch.empty((n_f, L, L, L), dtype=torch.float32, device="cuda")
-        apt.aptidx_compute_fsp(h, amp)            # warm-up
-        ef = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        apt.aptidx_set_profiling(h, True)
-        ef[0].record(stream)
-        for _ in range(2):
-            apt.aptidx_compute_fsp(h, amp)
-        ef[1].record(stream)
-        torch.cuda.synchronize()
-        fprof, _ = apt.aptidx_get_profile(h)
-        apt.aptidx_set_profiling(h, False)
-        f_ms = ef[0].elapsed_time(ef[1]) / 2
-        k_ms = fprof["signature"][0] / max(fprof["signature"][1], 1)
-        nw_f = n_atoms[:n_f]
-        kpad = 2 * ((nw_f + 31) // 32 * 32)                    # K = 2 N_w padded to the 32-atom chunks
-        flop = float(np.sum(2.0 * L * L * (2 * L) * kpad))     # executed, M = L^2, N = 2L
         peaks = measured_peaks()
         tp = peaks.get("bf16_tflops")
-        fsp = {"grid": f"{L}^3 over [-2pi, 2pi]^3 nm^-1", "rois": n_f, "ms_per_call": f_ms, "kernel_ms": k_ms,
-               "rois_per_s": n_f / (f_ms / 1e3),
-               "tensor": {"achieved": flop / (k_ms / 1e3) / 1e12, "peak": tp, "unit": "TFLOP/s",
-                          "frac": (flop / (k_ms / 1e3) / 1e12 / tp) if tp else None,
-                          "work": f"{flop:.3e} executed fp16 flop per launch (M = L^2, N = 2L, K = 2 N_w padded)"}}
+
+        def fsp_run(L, n_f, calls):
+            apt.aptidx_set_rois(h, torch.from_numpy(w.centres[:n_f]).cuda(), torch.from_numpy(w.radii[:n_f]).cuda())
+            amp = torch.empty((n_f, L, L, L), dtype=torch.float32, device="cuda")
+            apt.aptidx_compute_fsp(h, amp)            # warm-up
+            ef = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            apt.aptidx_set_profiling(h, True)
+            ef[0].record(stream)
+            for _ in range(calls):
+                apt.aptidx_compute_fsp(h, amp)
+            ef[1].record(stream)
+            torch.cuda.synchronize()
+            fprof, _ = apt.aptidx_get_profile(h)
+            apt.aptidx_set_profiling(h, False)
+            del amp
+            f_ms = ef[0].elapsed_time(ef[1]) / calls
+            k_ms = fprof["signature"][0] / max(fprof["signature"][1], 1)
+            nw_f = n_atoms[:n_f]
+            kpad = 2 * ((nw_f + 31) // 32 * 32)                    # K = 2 N_w padded to the 32-atom chunks
+            flop = float(np.sum(2.0 * L * L * (2 * L) * kpad))     # executed: L^2 columns x 2L rows
+            return {"grid": f"{L}^3 over [-2pi, 2pi]^3 nm^-1", "rois": n_f, "ms_per_call": f_ms, "kernel_ms": k_ms,
+                    "rois_per_s": n_f / (f_ms / 1e3),
+                    "tensor": {"achieved": flop / (k_ms / 1e3) / 1e12, "peak": tp, "unit": "TFLOP/s",
+                               "frac": (flop / (k_ms / 1e3) / 1e12 / tp) if tp else None,
+                               "work": f"{flop:.3e} executed fp16 flop per launch (L^2 x 2L x K, K = 2 N_w padded)"}}
+
+        # the paper's two benchmark grids: L_D = 64 (4096 ROIs) and L_D = 512
+        # (8 ROIs per call: 4 GiB of amplitudes)
+        fsp = fsp_run(64, min(nroi, 4096), 2)
+        l512 = fsp_run(512, min(nroi, 8), 2)
+        l512["s_per_1e4_rois"] = 1e4 / l512["rois_per_s"]
+        fsp["l512"] = l512
         apt.aptidx_set_rois(h, torch.from_numpy(w.centres).cuda(), torch.from_numpy(w.radii).cuda())
-        del amp
 
     # roofline of the dominant kernel (the signature kernel of the headline path)
     sig_ms = prof["signature"][0] / max(prof["signature"][1], 1)

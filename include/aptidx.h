@@ -211,15 +211,18 @@ int aptidx_refine_roi_grid(aptidx_ctx* ctx, const float* S, int64_t nroi, float 
  * Vurpillot et al.): for every ROI of the current set (and type mask),
  * |F(k)| with F(k) = sum_w exp(-2 pi i k . (p_w - p_c)) over the ROI's
  * atoms (centred FP32 coordinates of the gather, nm), on the cubic grid
- * k = (k_x, k_y, k_z), k_a = -k_max + i_a dk, i_a < APTIDX_FSP_L,
- * dk = 2 k_max / (APTIDX_FSP_L - 1), k in nm^-1 (the supplement's grid over
- * [-2 pi, 2 pi]^3 gives k_max = 2 pi).  amp: nroi x L x L x L FP32,
- * amp[((roi * L + ix) * L + iy) * L + iz], in `mem`.  Computed as tensor-core
- * GEMMs with fp16 operands and FP32 accumulation (sm_103 only).
- * 0 < k_max <= 64.  Errors: INVALID_ARG (no tensor cores, bad k_max), STATE,
- * OOM, CUDA, TIMEOUT. */
-#define APTIDX_FSP_L 64
-int aptidx_compute_fsp(aptidx_ctx* ctx, double k_max, float* amp, int mem);
+ * k = (k_x, k_y, k_z), k_a = -k_max + i_a dk, i_a < L, dk = 2 k_max / (L - 1),
+ * k in nm^-1 (the supplement's grid over [-2 pi, 2 pi]^3 gives k_max = 2 pi;
+ * its benchmarks use L = 64 and L = 512).  grid_l = L: a multiple of 64 in
+ * [APTIDX_FSP_L_MIN, APTIDX_FSP_L_MAX].  amp: nroi x L x L x L FP32,
+ * amp[((roi * L + ix) * L + iy) * L + iz], in `mem` (L = 512 is 512 MiB per
+ * ROI: pass ROI sets that fit).  Computed as tensor-core GEMMs with fp16
+ * operands and FP32 accumulation (sm_103 only).  0 < k_max <= 64.
+ * Errors: INVALID_ARG (no tensor cores, bad grid_l or k_max, more than 2^31
+ * work items), STATE, OOM, CUDA, TIMEOUT. */
+#define APTIDX_FSP_L_MIN 64
+#define APTIDX_FSP_L_MAX 512
+int aptidx_compute_fsp(aptidx_ctx* ctx, int32_t grid_l, double k_max, float* amp, int mem);
 
 /* ---- indexing (supplement "Indexing algorithm", Eq. 3) ---------------------- */
 

@@ -32,7 +32,8 @@ __all__ = [
 APTIDX_OK = 0
 APTIDX_MAX_TOPK = 1024
 APTIDX_MAX_BANDS = 4
-APTIDX_FSP_L = 64
+APTIDX_FSP_L_MIN = 64
+APTIDX_FSP_L_MAX = 512
 APTIDX_E_INVALID_ARG = 1
 APTIDX_E_CUDA = 2
 APTIDX_E_OOM = 3
@@ -78,7 +79,7 @@ _SIGS = {
     "aptidx_get_lut": (C.c_int, [_vp, _i32, _vp, _vp, C.c_int]),
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_match_topk": (C.c_int, [_vp, _i32, _vp, _i64, _i32, _vp, _vp, C.c_int]),
-    "aptidx_compute_fsp": (C.c_int, [_vp, C.c_double, _vp, C.c_int]),
+    "aptidx_compute_fsp": (C.c_int, [_vp, C.c_int32, C.c_double, _vp, C.c_int]),
     "aptidx_refine_roi_grid": (C.c_int, [_vp, _vp, _i64, C.c_float, C.c_double, _i32, _vp, _vp, _i64, _vp,
                                          C.c_int]),
     "aptidx_compute_signatures_multi": (C.c_int, [_vp, C.c_int, C.c_uint, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -298,10 +299,12 @@ def aptidx_refine_roi_grid(ctx, S, kappa: float, spacing: float, split: int = 5)
 
 
 def aptidx_compute_fsp(ctx, amp, k_max: float = 2 * 3.141592653589793):
-    """|F(k)| of Eq. 2 on the 64^3 grid over [-k_max, k_max]^3 (nm^-1) for
-    every ROI: amp [nroi, 64, 64, 64] float32 (ix, iy, iz)."""
+    """|F(k)| of Eq. 2 on the L^3 grid over [-k_max, k_max]^3 (nm^-1) for
+    every ROI: amp [nroi, L, L, L] float32 (ix, iy, iz); L (a multiple of 64
+    up to 512) is taken from amp's shape."""
+    L = int(amp.shape[1])
     pA, mA = _out(amp, np.float32)
-    _check(ctx, load().aptidx_compute_fsp(ctx, C.c_double(k_max), pA, mA))
+    _check(ctx, load().aptidx_compute_fsp(ctx, C.c_int32(L), C.c_double(k_max), pA, mA))
 
 
 def aptidx_get_histograms(ctx, roi: int, path: int, h):

@@ -1270,15 +1270,20 @@ int aptidx_refine_roi_grid(aptidx_ctx* ctx, const float* S, int64_t nroi, float 
     return read_status(c);
 }
 
-int aptidx_compute_fsp(aptidx_ctx* ctx, double k_max, float* amp, int mem) {
+int aptidx_compute_fsp(aptidx_ctx* ctx, int32_t grid_l, double k_max, float* amp, int mem) {
     CTX_OR_FAIL(ctx);
     int rc;
     if ((rc = check_mem(c, mem))) return rc;
     if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "compute_fsp: set ROIs first");
     if (!amp) return set_error(c, APTIDX_E_INVALID_ARG, "compute_fsp: need amp");
+    if (grid_l < APTIDX_FSP_L_MIN || grid_l > APTIDX_FSP_L_MAX || grid_l % APTIDX_FSP_L_MIN != 0)
+        return set_error(c, APTIDX_E_INVALID_ARG, "compute_fsp: grid_l = %d", grid_l);
     if (!(k_max > 0.0 && k_max <= 64.0)) return set_error(c, APTIDX_E_INVALID_ARG, "compute_fsp: k_max = %g", k_max);
     if (!tc_supported(c)) return set_error(c, APTIDX_E_INVALID_ARG, "compute_fsp: needs the sm_103 tensor cores");
-    const int64_t L = APTIDX_FSP_L;
+    const int64_t L = grid_l;
+    if (c->nroi * (L * L * L / 32768) >= ((int64_t)1 << 31))
+        return set_error(c, APTIDX_E_INVALID_ARG, "compute_fsp: %lld ROIs at L = %d exceed 2^31 work items",
+                         (long long)c->nroi, grid_l);
     const size_t n = (size_t)c->nroi * L * L * L;
     DevTmp t;
     float* d;
@@ -1287,7 +1292,7 @@ int aptidx_compute_fsp(aptidx_ctx* ctx, double k_max, float* amp, int mem) {
     if ((rc = run_gather(c))) return rc;
     prof_end(c, APTIDX_PHASE_GATHER, 6);
     prof_begin(c, APTIDX_PHASE_SIGNATURE);
-    cudaError_t e = launch_fsp_tc(c, k_max, d);
+    cudaError_t e = launch_fsp_tc(c, grid_l, k_max, d);
     if (e != cudaSuccess) return cuda_check(c, e, "reciprocal-space signature");
     prof_end(c, APTIDX_PHASE_SIGNATURE, 1);
     if ((rc = copy_back(c, amp, d, n, mem))) return rc;

@@ -9,19 +9,20 @@
 // a complex GEMM of M = L^2 rows, N = L columns and K = N_w.  It runs
 // transposed as the real GEMM
 //   [[Re F^T], [Im F^T]] = [[E_r, -E_i], [E_i, E_r]] x [P_r | P_i]^T
-// (M = 2 L rows: Re F then Im F over iz; N = L^2 columns (ix, iy);
-// K = 2 N_w), on tcgen05 with fp16 operands and FP32 accumulators in tensor
-// memory.
+// (rows: Re F then Im F over iz; columns (ix, iy); K = 2 N_w), on tcgen05
+// with fp16 operands and FP32 accumulators in tensor memory.
 //
-// Work item = (ROI, 8 consecutive ix) = 512 columns, two MMAs of N = 256
-// per K step, the accumulators filling the 512 tensor-memory columns.  Per
-// chunk of 32 atoms (K = 64: the 32 real parts, then the 32 imaginary
-// parts):
+// Work item = (ROI, 64 values of iz, 8 of ix, 64 of iy): M = 128 rows of
+// the E_z block matrix times 512 columns of P, two MMAs of N = 256 per K
+// step, the accumulators filling the 512 tensor-memory columns; L is any
+// multiple of 64 up to 512 (L^3 / 32768 items per ROI).  Per chunk of 32
+// atoms (K = 64: the 32 real parts, then the 32 imaginary parts):
 //   four table warps tabulate E_x (8 rows) and E_y (64 rows) as fp16 pairs
-//     into one of two table sets (E_y by recurrence
-//     E[i + 1] = E[i] exp(-2 pi i dk a) over 8-row segments whose starts
-//     come from the hardware sine and cosine after an exact range reduction);
-//   two warps compute E_z the same way and write the A operand (the E_z
+//     into one of two table sets (E_y by the recurrence
+//     E[i + 2] = E[i] exp(-2 pi i 2 dk a) over 8 rows per half warp, whose
+//     starts come from the hardware sine and cosine after an exact range
+//     reduction);
+//   four warps compute E_z the same way and write the A operand (the E_z
 //     block matrix, 16 KB) straight into the stage;
 //   eight builder warps form the B operand P = E_x E_y in fp16 pair
 //     arithmetic (512 rows, 64 KB);
@@ -37,12 +38,11 @@ namespace aptidx {
 
 namespace {
 
-constexpr int kL = APTIDX_FSP_L;                    // grid points per axis
-constexpr int kN = 2 * kL;                          // MMA N: [Re F | Im F] over iz
-constexpr int kTileRows = 128;                      // MMA M
-constexpr int kTiles = 4;                           // M tiles per item
+constexpr int kL = 64;                              // grid points per block of iy and of iz
+constexpr int kN = 2 * kL;                          // rows of the E_z block matrix: Re F, Im F over iz
+constexpr int kTileRows = 128;
+constexpr int kTiles = 4;                           // 512 (ix, iy) columns per item
 constexpr int kIxItem = kTiles * kTileRows / kL;    // 8 values of ix per item
-constexpr int kItemsRoi = kL / kIxItem;             // 8 items per ROI
 constexpr int kWc = 32;                             // atoms per chunk (K = 64)
 constexpr int kThreadsF = 576;                      // 18 warps, every role spread over the 4 SM sub-partitions
 constexpr int kIss = 2;                             // issuer warps 0, 1: N halves 0 and 1
@@ -63,7 +63,7 @@ constexpr int kTabSet = (kIxItem + kL) * kTabRowH * 4;   // one table set: E_x, 
 constexpr int kTabBytes = 2 * kTabSet;              // double buffered
 constexpr int kRowsHw = 8;   // E_y / E_z rows per half warp and chunk (recurrence length)
 
-static_assert(kL == 64, "the tiling assumes L = 64");
+static_assert(kL == 64 && APTIDX_FSP_L_MIN == kL && APTIDX_FSP_L_MAX % kL == 0, "the tiling assumes 64-blocks");
 
 struct FspParams {
     const float4* atoms;   // centred ROI atoms, CSR by off
@@ -71,6 +71,9 @@ struct FspParams {
     const int32_t* nw;
     int64_t nroi;
     float kmax, dk;
+    int L;                 // grid points per axis, a multiple of 64
+    int nxb, nyb;          // blocks of 8 ix and of 64 iy per axis
+    int items_roi;         // (L / 64) blocks of iz x nxb x nyb
     float* out;            // nroi x L^3 amplitudes, iz fastest
     int32_t* counter;
     int* status;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
 
     uint32_t cg = 0;      // chunks handled so far by this CTA (stage and table-set ring position)
     uint32_t nitem = 0;   // items finished so far (accumulator barrier phase)
-    const int64_t n_items = p.nroi * kItemsRoi;
+    const int64_t n_items = p.nroi * p.items_roi;
     for (;;) {
         if (tid == 0) *item_s = atomicAdd(p.counter, 1);
         __syncthreads();
@@ -164,8 +167,13 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
         const int failed = *fail_s;
         __syncthreads();
         if (item >= n_items || failed) break;
-        const int64_t roi = item / kItemsRoi;
-        const int g = (int)(item % kItemsRoi);
+        // item = (ROI, 64-block of iz, 8-block of ix, 64-block of iy)
+        const int64_t roi = item / p.items_roi;
+        int rest = (int)(item % p.items_roi);
+        const int iy0 = (rest % p.nyb) * kL;
+        rest /= p.nyb;
+        const int ix0 = (rest % p.nxb) * kIxItem;
+        const int iz0 = (rest / p.nxb) * kL;
         const int nw = p.nw[roi];
         const float4* A = p.atoms + p.off[roi];
         const int nch = max(1, (nw + kWc - 1) / kWc);
@@ -204,8 +212,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
             // 2 tw + hw ----
             const int tw = (tid - kTab0) >> 5, hw = lane >> 4, pl = lane & 15;
             const int r0 = 16 * tw + hw, ixl = 2 * tw + hw;
-            const float kx = fmaf((float)(g * kIxItem + ixl), p.dk, -p.kmax);
-            const float ky0 = fmaf((float)r0, p.dk, -p.kmax);
+            const float kx = fmaf((float)(ix0 + ixl), p.dk, -p.kmax);
+            const float ky0 = fmaf((float)(iy0 + r0), p.dk, -p.kmax);
             float4 na = atom_or_zero(A, 2 * pl, nw), nb = atom_or_zero(A, 2 * pl + 1, nw);
             for (int c = 0; c < nch; ++c) {
                 const uint32_t cc = cg + c, b = cc & 1u, u = cc >> 1;
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
             // opposite order, so a store touches 32 distinct banks ----
             const int zw = (tid - kZ0) >> 5, hw = lane >> 4, pl = lane & 15;
             const int n0 = 16 * zw + hw;
-            const float kz0 = fmaf((float)n0, p.dk, -p.kmax);
+            const float kz0 = fmaf((float)(iz0 + n0), p.dk, -p.kmax);
             const uint32_t wofs_lo = (uint32_t)(pl & 3) * 4u, c_lo = (uint32_t)(pl >> 2), c_hi = c_lo + 4u;
             const uint32_t c0 = hw ? c_hi : c_lo, c1 = hw ? c_lo : c_hi;   // this half's first and second word
             float4 na = atom_or_zero(A, 2 * pl, nw), nb = atom_or_zero(A, 2 * pl + 1, nw);
@@ -333,8 +341,9 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
         }
         cg += (uint32_t)nch;
 
-        // ---- epilogue: tensor-memory lane n holds Re F (n < L) or Im F
-        // (n >= L) of iz = n mod L, column j the grid point (ix, iy) = j.
+        // ---- epilogue: tensor-memory lane n holds Re F (n < 64) or Im F
+        // (n >= 64) of iz = iz0 + n mod 64, column j the grid point
+        // (ix0 + j / 64, iy0 + j % 64).
         // Warp w reads lane quadrant qd = w % 4 of column group w / 4; the
         // Re and Im quadrants of the same iz (qd, qd ^ 2) meet in shared
         // memory (the idle stage), taking turns at forming |F| ----
@@ -347,7 +356,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
             const bool is_im = qd >= 2;
             float* slab = reinterpret_cast<float*>(smem) + (grp * 2 + pair) * 32 * 32;
             const uint32_t tl = tmem + ((uint32_t)(qd * 32) << 16);
-            float* dst = p.out + ((int64_t)roi * kL + g * kIxItem) * kL * kL + pair * 32 + lane;
+            const int64_t L = p.L;
+            float* dst = p.out + ((roi * L + ix0) * L + iy0) * L + iz0 + pair * 32 + lane;
             for (int bb = 0; bb < 4; ++bb) {
                 const int c0 = grp * 128 + bb * 32;
                 float v[32];
@@ -365,7 +375,8 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                     for (int j = 0; j < 32; ++j) {
                         const float o = slab[j * 32 + lane];
                         const float a2 = fmaf(v[j], v[j], o * o);
-                        dst[(int64_t)(c0 + j) * kL] = a2 * rsqrtf(fmaxf(a2, 1e-30f));   // |F|, 0 at a2 = 0
+                        const int m = c0 + j;   // (ix, iy) = (ix0 + m / 64, iy0 + m % 64)
+                        dst[((m >> 6) * L + (m & (kL - 1))) * L] = a2 * rsqrtf(fmaxf(a2, 1e-30f));   // |F|, 0 at a2 = 0
                     }
                 }
                 grp_sync(grp);
@@ -384,7 +395,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
 
 size_t fsp_smem_bytes() { return 1024 + 2 * (size_t)kStage + kTabBytes + 128; }
 
-cudaError_t launch_fsp_tc(Ctx* c, double kmax, float* out) {
+cudaError_t launch_fsp_tc(Ctx* c, int L, double kmax, float* out) {
     const size_t smem = fsp_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_fsp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -394,12 +405,16 @@ cudaError_t launch_fsp_tc(Ctx* c, double kmax, float* out) {
     p.nw = c->d_nw;
     p.nroi = c->nroi;
     p.kmax = (float)kmax;
-    p.dk = (float)(2.0 * kmax / (double)(kL - 1));
+    p.dk = (float)(2.0 * kmax / (double)(L - 1));
+    p.L = L;
+    p.nxb = L / kIxItem;
+    p.nyb = L / kL;
+    p.items_roi = (L / kL) * p.nxb * p.nyb;
     p.out = out;
     p.counter = c->d_counter + 2;
     p.status = c->d_status;
     if ((e = cudaMemsetAsync(p.counter, 0, sizeof(int32_t), c->stream)) != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count, c->nroi * kItemsRoi);
+    const int64_t grid = std::min<int64_t>((int64_t)c->sm_count, c->nroi * p.items_roi);
     if (grid < 1) return cudaSuccess;
     k_fsp_tc<<<(unsigned)grid, kThreadsF, smem, c->stream>>>(p);
     return cudaGetLastError();

@@ -194,7 +194,7 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
                                  int64_t hist_roi);
 int prepare_tc(Ctx* c);
 bool tc_supported(Ctx* c);
-cudaError_t launch_fsp_tc(Ctx* c, double kmax, float* out);
+cudaError_t launch_fsp_tc(Ctx* c, int L, double kmax, float* out);
 bool tc_supported(Ctx* c);
 cudaError_t launch_normalise(Ctx* c, float* S, int64_t rows = -1);   // rows of nv values; -1: nroi
 size_t plain_smem_bytes(int m, int atom_cap);

@@ -1,7 +1,8 @@
 """GPU parity of the reciprocal-space signature (Eq. 2) on tcgen05 against the
-FP64 oracle: |F(k)| on the 64^3 grid over [-2 pi, 2 pi]^3 nm^-1, fp16
-operands with FP32 accumulation; per ROI
-e = max_k |F_gpu - F_oracle| / max_k F_oracle <= 5e-3.
+FP64 oracle: |F(k)| on the L^3 grid over [-2 pi, 2 pi]^3 nm^-1 (L = 64, and
+the larger grids of the paper's benchmark up to L = 512), fp16 operands with
+FP32 accumulation; per ROI e = max_k |F_gpu - F_oracle| / max_k F_oracle
+<= 5e-3.
 """
 import numpy as np
 import pytest
@@ -18,7 +19,7 @@ TOL = 5e-3
 L = 64
 
 
-def fsp_gpu(torch, xyz, centres, radii, types=None, mask=0xFFFFFFFF, kmax=2 * np.pi):
+def fsp_gpu(torch, xyz, centres, radii, types=None, mask=0xFFFFFFFF, kmax=2 * np.pi, L=L):
     ctx = apt.Context(0)
     h = ctx.handle
     apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda(), None if types is None else torch.from_numpy(types).cuda())
@@ -74,3 +75,27 @@ def test_fsp_single_crystal_rois_and_type_mask(torch_cuda):
     _, xc = oracle.gather(w.xyz, centres[0], radii[0], types=types, type_mask=0b10)
     Fo = oracle.fsp(xc, L, kmax=5.0, points=pts)
     assert np.abs(Fm[0].reshape(-1)[pts] - Fo).max() / Fo.max() <= TOL
+
+
+def edge_points(L, n, seed):
+    """n random flat grid indices plus every combination of the 64-block
+    edges (first and last index of each block) along the three axes."""
+    rng = np.random.default_rng(seed)
+    edge = np.unique(np.concatenate([np.arange(0, L, 64), np.arange(63, L, 64)]))
+    ijk = np.stack(np.meshgrid(edge, edge, edge, indexing="ij"), -1).reshape(-1, 3)
+    return np.unique(np.concatenate([rng.choice(L ** 3, n, replace=False), (ijk[:, 0] * L + ijk[:, 1]) * L + ijk[:, 2]]))
+
+
+@pytest.mark.parametrize("Lg", [128, 512])
+def test_fsp_larger_grids(torch_cuda, Lg):
+    """The larger grids of the paper's benchmark (L_D up to 512): a b.c.c. ROI
+    and a small f.c.c. ROI at sampled points, among them every block edge."""
+    b = synth.single_crystal_bcc()
+    w = synth.tiny_fcc()
+    for xyz, centre, radius in [(b.xyz, b.centres[:1], b.radii[:1]), (w.xyz, w.centres[1:2], w.radii[1:2])]:
+        F = fsp_gpu(torch_cuda, xyz, centre, radius, L=Lg).reshape(-1)
+        pts = edge_points(Lg, 4000, 11)
+        _, xc = oracle.gather(xyz, centre[0], radius[0])
+        Fo = oracle.fsp(xc, Lg, points=pts)
+        assert np.abs(F[pts] - Fo).max() / xc.shape[0] <= TOL, Lg
+        del F
