@@ -367,6 +367,45 @@ def run_gb300(args):
                        "gather_ms": pprof["gather"][0] / max(pprof["gather"][1], 1),
                        "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
 
+    # end to end through the C ABI: host inputs copied in, results copied out, every step
+    e2e = None
+    if not args.no_e2e:
+        xyz_h = torch.from_numpy(w.xyz).pin_memory()
+        cen_h = torch.from_numpy(w.centres).pin_memory()
+        rad_h = torch.from_numpy(w.radii).pin_memory()
+        S_h = torch.empty((nroi, nv), dtype=torch.float32).pin_memory()
+        q_h = torch.empty((nroi, 4), dtype=torch.float64).pin_memory()
+
+        copy_stream = torch.cuda.Stream()
+
+        def e2e_step():
+            # the signature array streams to the host while Eq. 3 and the
+            # refinement (which only read it) run on the library's stream
+            apt.aptidx_load_positions(h, xyz_h)
+            apt.aptidx_set_rois(h, cen_h, rad_h)
+            apt.aptidx_compute_signatures(h, code[headline], apt.APTIDX_NORMALISE_MAX | tuned, S, None, None)
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            copy_stream.wait_event(ready)
+            with torch.cuda.stream(copy_stream):
+                S_h.copy_(S, non_blocking=True)
+            apt.aptidx_match(h, 0, S, best, score)
+            apt.aptidx_refine(h, 0, S, None, iters, q_out, rloss, best=best)
+            q_h.copy_(q_out, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        dt = ranks.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
+        e2e = {"value": world * nroi * nv / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(w.xyz.nbytes + w.centres.nbytes + w.radii.nbytes),
+               "d2h_bytes_per_step": int(nroi * nv * 4 + nroi * 4 * 8),
+               "ms_per_step": 1e3 * dt}
+
     # paper-scale indexing (not part of the step): the 1-degree-sized set of
     # 618324 orientations, n_hat = 1000, the 1000 best solutions per ROI
     paper_index = None
@@ -464,45 +503,6 @@ def run_gb300(args):
             "work": f"{flop:.3e} algorithmic FP32 flop per launch"}
     if tensor:
         roof["tensor"] = tensor
-
-    # end to end through the C ABI: host inputs copied in, results copied out, every step
-    e2e = None
-    if not args.no_e2e:
-        xyz_h = torch.from_numpy(w.xyz).pin_memory()
-        cen_h = torch.from_numpy(w.centres).pin_memory()
-        rad_h = torch.from_numpy(w.radii).pin_memory()
-        S_h = torch.empty((nroi, nv), dtype=torch.float32).pin_memory()
-        q_h = torch.empty((nroi, 4), dtype=torch.float64).pin_memory()
-
-        copy_stream = torch.cuda.Stream()
-
-        def e2e_step():
-            # the signature array streams to the host while Eq. 3 and the
-            # refinement (which only read it) run on the library's stream
-            apt.aptidx_load_positions(h, xyz_h)
-            apt.aptidx_set_rois(h, cen_h, rad_h)
-            apt.aptidx_compute_signatures(h, code[headline], apt.APTIDX_NORMALISE_MAX | tuned, S, None, None)
-            ready = torch.cuda.Event()
-            ready.record(stream)
-            copy_stream.wait_event(ready)
-            with torch.cuda.stream(copy_stream):
-                S_h.copy_(S, non_blocking=True)
-            apt.aptidx_match(h, 0, S, best, score)
-            apt.aptidx_refine(h, 0, S, None, iters, q_out, rloss, best=best)
-            q_h.copy_(q_out, non_blocking=True)
-            torch.cuda.synchronize()
-
-        e2e_step()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        barrier()
-        dt = ranks.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
-        e2e = {"value": world * nroi * nv / dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(w.xyz.nbytes + w.centres.nbytes + w.radii.nbytes),
-               "d2h_bytes_per_step": int(nroi * nv * 4 + nroi * 4 * 8),
-               "ms_per_step": 1e3 * dt}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

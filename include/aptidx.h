@@ -108,8 +108,9 @@ int aptidx_version(void);
 
 /* Atom positions of the reconstruction (Section 2.2: p_i).  xyz: n x 3 FP32
  * (x, y, z) in nm; types: n atom-type ids (NULL: all type 0).  Copies the
- * data and invalidates any previous ROI set.  Errors: INVALID_ARG (n <= 0,
- * n >= 2^31, NULL xyz, non-finite coordinate), OOM, CUDA. */
+ * data and invalidates any previous ROI set; a set of the same n reuses the
+ * device buffers.  Errors: INVALID_ARG (n <= 0, n >= 2^31, NULL xyz,
+ * non-finite coordinate: the context then holds no positions), OOM, CUDA. */
 int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const uint8_t* types,
                           int mem);
 

@@ -449,26 +449,34 @@ int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const ui
     if ((rc = check_mem(c, mem))) return rc;
     if (!xyz || n <= 0 || n >= ((int64_t)1 << 31))
         return set_error(c, APTIDX_E_INVALID_ARG, "positions: need 0 < n < 2^31 and a non-NULL pointer");
-    HostView<float> hx;
-    if ((rc = to_host(c, xyz, (size_t)n * 3, mem, hx))) return rc;
-    for (size_t i = 0; i < (size_t)n * 3; ++i)
-        if (!isfinite(hx[i])) return set_error(c, APTIDX_E_INVALID_ARG, "positions: non-finite coordinate at %zu", i / 3);
     free_rois(c);
     free_grid(c);
     clear_graphs(c);
-    free_ptr(c->d_pos);
-    free_ptr(c->d_types);
     c->n_atoms = 0;
-    if ((rc = dev_alloc(c, (void**)&c->d_pos, (size_t)n * 3 * sizeof(float)))) return rc;
-    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_pos, xyz, (size_t)n * 3 * sizeof(float),
-                                   mem == APTIDX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                                   c->stream));
-    if (types) {
-        if ((rc = dev_alloc(c, (void**)&c->d_types, (size_t)n))) return rc;
-        APTIDX_CUDA(c, cudaMemcpyAsync(c->d_types, types, (size_t)n,
-                                       mem == APTIDX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                                       c->stream));
+    // a set of the same size reuses the device buffers (a reload per step
+    // then costs the copy and the bounding box only)
+    if (c->pos_cap != n) {
+        free_ptr(c->d_pos);
+        c->pos_cap = 0;
+        if ((rc = dev_alloc(c, (void**)&c->d_pos, (size_t)n * 3 * sizeof(float)))) return rc;
+        c->pos_cap = n;
     }
+    const cudaMemcpyKind kind = mem == APTIDX_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    APTIDX_CUDA(c, cudaMemcpyAsync(c->d_pos, xyz, (size_t)n * 3 * sizeof(float), kind, c->stream));
+    if (types) {
+        if (c->types_cap != n) {
+            free_ptr(c->d_types);
+            c->types_cap = 0;
+            if ((rc = dev_alloc(c, (void**)&c->d_types, (size_t)n))) return rc;
+            c->types_cap = n;
+        }
+        APTIDX_CUDA(c, cudaMemcpyAsync(c->d_types, types, (size_t)n, kind, c->stream));
+    } else {
+        free_ptr(c->d_types);
+        c->types_cap = 0;
+    }
+    // bounding box on the device; a NaN or infinite coordinate shows up as
+    // a non-finite extreme (NaN patterns order beyond the infinities)
     float* mm = nullptr;
     if ((rc = dev_alloc(c, (void**)&mm, 12 * sizeof(float)))) return rc;
     cudaError_t e = launch_bbox(c->d_pos, n, mm, c->stream);
@@ -477,6 +485,8 @@ int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const ui
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(mm);
     if (e != cudaSuccess) return cuda_check(c, e, "bounding box");
+    for (int d = 0; d < 6; ++d)
+        if (!isfinite(hmm[d])) return set_error(c, APTIDX_E_INVALID_ARG, "positions: a coordinate is NaN or infinite");
     for (int d = 0; d < 3; ++d) {
         c->lo[d] = hmm[d];
         c->hi[d] = hmm[3 + d];

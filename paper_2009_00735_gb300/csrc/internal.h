@@ -55,6 +55,8 @@ struct Ctx {
     int64_t n_atoms = 0;
     float* d_pos = nullptr;        // [n x 3]
     uint8_t* d_types = nullptr;    // [n] or null
+    int64_t pos_cap = 0;           // atoms d_pos holds room for (reused by a same-sized load)
+    int64_t types_cap = 0;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 
     // uniform cell grid over the positions

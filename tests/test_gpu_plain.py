@@ -206,6 +206,20 @@ def test_invalid_arguments(torch_cuda, tiny):
         apt.aptidx_load_positions(h, bad)
     assert ei.value.code == apt.APTIDX_E_INVALID_ARG
     apt.aptidx_load_positions(h, tiny.xyz)
+    # every non-finite form, also into the buffers of a same-sized set; the
+    # context then holds no positions until a good set is loaded
+    for i, v in [(0, np.inf), (tiny.xyz.shape[0] - 1, -np.inf), (7, -np.nan)]:
+        bad = tiny.xyz.copy()
+        bad[i, 2] = v
+        with pytest.raises(apt.AptidxError) as ei:
+            apt.aptidx_load_positions(h, bad)
+        assert ei.value.code == apt.APTIDX_E_INVALID_ARG
+        apt.aptidx_set_directions(h, tiny.dirs)
+        apt.aptidx_set_binning(h, 8, 10, 11)
+        with pytest.raises(apt.AptidxError) as ei:
+            apt.aptidx_set_rois(h, tiny.centres, tiny.radii)
+        assert ei.value.code == apt.APTIDX_E_STATE
+    apt.aptidx_load_positions(h, tiny.xyz)
     with pytest.raises(apt.AptidxError):
         apt.aptidx_set_directions(h, tiny.dirs * 1.01)
     apt.aptidx_set_directions(h, tiny.dirs)
