@@ -356,6 +356,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (no L1 allocation); completion
+// by cp_async_wait_all of the issuing thread.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stage `n` float4 atoms from global into shared memory with one bulk copy
 // issued by thread 0, then make them visible to the whole CTA.  `phase` is
 // the barrier's parity bit, toggled per use.  Returns false on a timeout

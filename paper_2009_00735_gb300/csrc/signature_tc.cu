@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     unsigned char* BT = smem + (size_t)NB * 128;
     float* EX = reinterpret_cast<float*>(BT + kBtBytes);   // [kDirs][8]
     float4* A = reinterpret_cast<float4*>(BT + kBtBytes + kExBytes);
+    float4* DB = A + p.atom_cap;   // [2][kDirs]: this tile's directions and the next tile's
     // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per issuer
-    uint64_t* bars = reinterpret_cast<uint64_t*>(A + p.atom_cap);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(DB + 2 * kDirs);
     int* flag = reinterpret_cast<int*>(bars + 2 + kIssuers);
     int64_t* item_s = reinterpret_cast<int64_t*>(bars + 3 + kIssuers);
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 4 + kIssuers);
@@ -156,13 +157,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 break;
             }
             pair_atoms(A, nw, tid, kThreads);
-            __syncthreads();
         }
+        // the first tile's directions (later tiles' arrive while the tile
+        // before them runs)
+        if (tid < kDirs) cp_async16(DB + (t0 & 1) * kDirs + tid, p.dirs + (int64_t)t0 * kDirs + tid);
+        cp_async_wait_all();
+        __syncthreads();
 
         for (int tile = t0; tile < t1 && !failed; ++tile) {
             // ---- 1. histograms (H is zero here) ----
-            const float4 d0 = p.dirs[(int64_t)tile * kDirs + 2 * lane];
-            const float4 d1 = p.dirs[(int64_t)tile * kDirs + 2 * lane + 1];
+            const float4 d0 = DB[(tile & 1) * kDirs + 2 * lane];
+            const float4 d1 = DB[(tile & 1) * kDirs + 2 * lane + 1];
+            if (tile + 1 < t1 && tid < kDirs)
+                cp_async16(DB + ((tile + 1) & 1) * kDirs + tid, p.dirs + (int64_t)(tile + 1) * kDirs + tid);
             for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
                 const int cn = min(p.atom_cap, nw - c0);
                 if (!one_chunk) {
@@ -214,13 +221,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 }
                 *flag = ok;
             }
-            for (int r0 = warp * 4; r0 < NB; r0 += kWarps * 4) {
+            // two groups of four rows per pass, 64 rows apart (same k & 7;
+            // NB is a multiple of 128), both loaded before either is stored
+            for (int r0 = warp * 4; r0 < NB; r0 += kWarps * 8) {
                 const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
                 uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
-                uint4 x;
-                if (sw) x = row[c];
+                uint4* row2 = row + kWarps * 4 * 8;   // row k + 64
+                uint4 x, x2;
+                if (sw) {
+                    x = row[c];
+                    x2 = row2[c];
+                }
                 __syncwarp();
-                if (sw) row[c ^ sw] = x;
+                if (sw) {
+                    row[c ^ sw] = x;
+                    row2[c ^ sw] = x2;
+                }
             }
             fence_proxy_async_smem();
             tc_fence_before();
@@ -363,6 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     }
                 }
             }
+            cp_async_wait_all();   // the next tile's directions have landed
             tc_fence_before();
             __syncthreads();
         }
@@ -416,7 +433,7 @@ bool tc_supported(Ctx* c) {
 }
 
 static size_t tc_smem_bytes(int m, int atom_cap) {
-    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 256;
+    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 256;
 }
 
 // Build the B operand for the current ROI bands and pick the TMEM size.
