@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                 const uint4 yi4 = *reinterpret_cast<const uint4*>(Eyh + iy * kTabRowH + kWc / 2 + 4 * q);
                 const __half2 yr[4] = {u2h2(yr4.x), u2h2(yr4.y), u2h2(yr4.z), u2h2(yr4.w)};
                 const __half2 yi[4] = {u2h2(yi4.x), u2h2(yi4.y), u2h2(yi4.z), u2h2(yi4.w)};
-#pragma unroll 4
+#pragma unroll
                 for (int ixl = 0; ixl < kIxItem; ++ixl) {
                     const uint4 xr4 = *reinterpret_cast<const uint4*>(Exh + ixl * kTabRowH + 4 * q);
                     const uint4 xi4 = *reinterpret_cast<const uint4*>(Exh + ixl * kTabRowH + kWc / 2 + 4 * q);
