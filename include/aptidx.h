@@ -121,7 +121,7 @@ int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem);
 
 /* Histogram resolution 2^m bins (Eq. 1; APTIDX_MIN_M <= m <= APTIDX_MAX_M)
  * and the default signature band of frequency bins [k_lo, k_hi]
- * (supplement, Al bicrystal: the highest amplitude in a fixed bin interval),
+ * (supplement, Al bicrystal: the largest amplitude over a fixed band of bins),
  * 0 <= k_lo <= k_hi <= 2^(m-1).  flags: reserved, 0. */
 int aptidx_set_binning(aptidx_ctx* ctx, int m, int32_t k_lo, int32_t k_hi, int flags);
 
