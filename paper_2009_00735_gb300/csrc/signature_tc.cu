@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     float* EX = reinterpret_cast<float*>(BT + kBtBytes);   // [kDirs][8]
     float4* A = reinterpret_cast<float4*>(BT + kBtBytes + kExBytes);
     float4* DB = A + p.atom_cap;   // [2][kDirs]: this tile's directions and the next tile's
+    float* EX2 = reinterpret_cast<float*>(DB + 2 * kDirs);   // [128 TMEM lanes][8]: partials 2, 3
     // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per issuer
-    uint64_t* bars = reinterpret_cast<uint64_t*>(DB + 2 * kDirs);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(EX2 + 128 * 8);
     int* flag = reinterpret_cast<int*>(bars + 2 + kIssuers);
     int64_t* item_s = reinterpret_cast<int64_t*>(bars + 3 + kIssuers);
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 4 + kIssuers);
@@ -311,10 +312,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
             tc_fence_after();
 
             // ---- 4. epilogue: |X(k)| and the band maximum (warps 0-3, one per
-            // TMEM lane quadrant); the other warps zero H for the next tile ----
-            if (warp >= 4) {
-                for (int i = tid - 128; i < NB * 8; i += kThreads - 128)
+            // TMEM lane quadrant); the other warps zero H for the next tile.
+            // With four partial accumulators and one frequency group, warps
+            // 4-7 sum partials 2 and 3 of the same quadrants meanwhile, so
+            // that each warp waits on two tensor-memory round trips, not four ----
+            const bool split = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
+            const int zw0 = split ? 8 : 4;   // first zeroing warp
+            if (warp >= zw0) {
+                for (int i = tid - zw0 * 32; i < NB * 8; i += kThreads - zw0 * 32)
                     reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+            } else if (warp >= 4) {
+                const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
+                const uint32_t cols_b = (uint32_t)(16 * p.gb);
+                float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int i = kIssuers / 2; i < kIssuers; ++i) {
+                    const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
+                    float hi[8], lo[8];
+                    tmem_ld8(dcol, hi);
+                    tmem_ld8(dcol + 8u, lo);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        re[q] += hi[2 * q] + lo[2 * q];
+                        im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                    }
+                }
+                float* e2 = EX2 + (size_t)(tid - 128) * 8;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    e2[2 * q] = re[q];
+                    e2[2 * q + 1] = im[q];
+                }
+                asm volatile("bar.sync 2, 256;" ::: "memory");
             } else {
                 // warps 0, 1 hold rows 0-63 (bins of the first half), warps
                 // 2, 3 rows 64-127; per frequency group the second-half warps
@@ -331,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     const int nb = min(p.gb, fg1 + 1 - g0);
                     for (int j = 0; j < nb; ++j) {
                         float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-                        for (int i = 0; i < n_iss; ++i) {
+                        for (int i = 0; i < (split ? kIssuers / 2 : n_iss); ++i) {
                             const uint32_t dcol = lane_base + (uint32_t)(b + i) * cols_b;
                             float hi[8], lo[8];
                             tmem_ld8(dcol + (uint32_t)(8 * j), hi);
@@ -341,6 +370,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             for (int q = 0; q < 4; ++q) {
                                 re[q] += hi[2 * q] + lo[2 * q];
                                 im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                            }
+                        }
+                        if (split) {   // partials 2, 3 from warp + 4 (one group: j = 0)
+                            asm volatile("bar.sync 2, 256;" ::: "memory");
+                            const float* e2 = EX2 + (size_t)tid * 8;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                re[q] += e2[2 * q];
+                                im[q] += e2[2 * q + 1];
                             }
                         }
                         if (warp >= 2) {
@@ -433,7 +471,8 @@ bool tc_supported(Ctx* c) {
 }
 
 static size_t tc_smem_bytes(int m, int atom_cap) {
-    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 256;
+    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 128 * 8 * 4 +
+           256;
 }
 
 // Build the B operand for the current ROI bands and pick the TMEM size.
