@@ -19,11 +19,11 @@
 // atoms (K = 64: the 32 real parts, then the 32 imaginary parts):
 //   four table warps tabulate E_x (8 rows) and E_y (64 rows) as fp16 pairs
 //     into one of two table sets (E_y by the recurrence
-//     E[i + 2] = E[i] exp(-2 pi i 2 dk a) over 8 rows per half warp, whose
-//     starts come from the hardware sine and cosine after an exact range
+//     E[i + 1] = E[i] exp(-2 pi i dk a) over runs of 4 rows, whose starts
+//     come from the hardware sine and cosine after an exact range
 //     reduction);
-//   four warps compute E_z the same way and write the A operand (the E_z
-//     block matrix, 16 KB) straight into the stage;
+//   four warps compute E_z (recurrence of step 2 dk over 8 rows) and write
+//     the A operand (the E_z block matrix, 16 KB) straight into the stage;
 //   eight builder warps form the B operand P = E_x E_y in fp16 pair
 //     arithmetic (512 rows, 64 KB);
 //   two issuer threads run the 8 MMAs (M = 128, N = 256, K = 16) of the
@@ -208,12 +208,15 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
             // 32 atoms into table set (chunk & 1), up to two chunks ahead of
             // the builders.  Lane (hw, pl) = (lane / 16, lane % 16) holds
             // atoms 2 pl, 2 pl + 1; warp tw, half hw: E_y rows
-            // 16 tw + hw + 2 j (j < 8, one recurrence of step 2 dk), E_x row
-            // 2 tw + hw ----
+            // 16 tw + 4 hw + {0..3} and 16 tw + 4 hw + 8 + {0..3} (two
+            // recurrences of step dk), E_x row tw + 4 hw.  The halves' rows
+            // are 4 apart, so a store's two 16-word halves fall in disjoint
+            // banks (36-word rows) ----
             const int tw = (tid - kTab0) >> 5, hw = lane >> 4, pl = lane & 15;
-            const int r0 = 16 * tw + hw, ixl = 2 * tw + hw;
+            const int r0 = 16 * tw + 4 * hw, ixl = tw + 4 * hw;
             const float kx = fmaf((float)(ix0 + ixl), p.dk, -p.kmax);
             const float ky0 = fmaf((float)(iy0 + r0), p.dk, -p.kmax);
+            const float ky1 = fmaf((float)(iy0 + r0 + 8), p.dk, -p.kmax);
             float4 na = atom_or_zero(A, 2 * pl, nw), nb = atom_or_zero(A, 2 * pl + 1, nw);
             for (int c = 0; c < nch; ++c) {
                 const uint32_t cc = cg + c, b = cc & 1u, u = cc >> 1;
@@ -235,14 +238,20 @@ __global__ void __launch_bounds__(kThreadsF, 1) k_fsp_tc(FspParams p) {
                     Exh[ixl * kTabRowH + kWc / 2 + pl] = pack_h2(ea.y, eb.y);
                 }
                 float2 ea = cexp_m2pi(2.f * ky0 * xa.y), eb = cexp_m2pi(2.f * ky0 * xb.y);
-                const float2 da = cexp_m2pi(4.f * p.dk * xa.y), db = cexp_m2pi(4.f * p.dk * xb.y);
+                float2 fa = cexp_m2pi(2.f * ky1 * xa.y), fb = cexp_m2pi(2.f * ky1 * xb.y);
+                const float2 da = cexp_m2pi(2.f * p.dk * xa.y), db = cexp_m2pi(2.f * p.dk * xb.y);
 #pragma unroll
-                for (int j = 0; j < kRowsHw; ++j) {
-                    uint32_t* row = Eyh + (r0 + 2 * j) * kTabRowH;
+                for (int j = 0; j < kRowsHw / 2; ++j) {
+                    uint32_t* row = Eyh + (r0 + j) * kTabRowH;
                     row[pl] = pack_h2(ea.x, eb.x);
                     row[kWc / 2 + pl] = pack_h2(ea.y, eb.y);
+                    row += 8 * kTabRowH;
+                    row[pl] = pack_h2(fa.x, fb.x);
+                    row[kWc / 2 + pl] = pack_h2(fa.y, fb.y);
                     ea = cmul(ea, da);
                     eb = cmul(eb, db);
+                    fa = cmul(fa, da);
+                    fb = cmul(fb, db);
                 }
                 tab_sync();
                 if (tid == kTab0) mbar_arrive(&tfull[b]);
