@@ -1,0 +1,72 @@
+"""Host logic of bench.py, on the CPU: the clock sampler's parsing and
+rejection reasons (against a fake nvidia-smi), the committed ncu traffic
+figure matching the committed kernel sources, and the reference arm's JSON
+line (the FP64 oracle on two host threads, one short step).
+"""
+import json
+import os
+import stat
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def fake_smi(tmp_path, rows):
+    script = tmp_path / "nvidia-smi"
+    body = "".join(f"echo '{r}'\n" for r in rows)
+    script.write_text("#!/bin/sh\n" + body + "sleep 5\n")
+    script.chmod(script.stat().st_mode | stat.S_IEXEC)
+    return str(tmp_path)
+
+
+def test_clock_sampler_median_under_load_and_reasons(tmp_path, monkeypatch):
+    rows = ["0, 2070, 2070, 450.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2070, 2070, 460.0, 0x0, Not Active, Not Active, Not Active, Active",
+            "0, 2055, 2070, 455.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 345, 2070, 90.0, 0x0, Not Active, Not Active, Not Active, Not Active"]   # idle sample
+    monkeypatch.setenv("PATH", fake_smi(tmp_path, rows) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    c = s.stop()
+    assert c["samples"] == 4
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["sm_mhz"] == 2070.0            # median of the samples above half the maximum
+    assert c["reasons"] == ["sw_power_cap"]
+    assert c["power_w_max"] == 460.0
+
+
+def test_clock_sampler_reports_thermal_slowdown(tmp_path, monkeypatch):
+    rows = ["0, 1500, 2070, 700.0, 0x0, Active, Not Active, Active, Not Active"]
+    monkeypatch.setenv("PATH", fake_smi(tmp_path, rows) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    c = s.stop()
+    assert c["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_committed_traffic_matches_kernel_sources():
+    """profiles/k_sig_tc_bcc1024.md carries the DRAM traffic of the committed
+    tensor-core kernel (its source fingerprint matches), scaled by ROIs."""
+    t8 = bench.tc_traffic_per_launch(8192)
+    t1 = bench.tc_traffic_per_launch(1024)
+    assert t8 is not None and t8 > 0
+    assert np.isclose(t8, 8 * t1)
+
+
+def test_reference_arm_json_line():
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([x for x in out.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["unit"] == line["cpu_baseline"]["unit"] == line["e2e"]["unit"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 2
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["higher_is_better"] is True and line["dtype"] == "f64"
