@@ -170,7 +170,10 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
  * (NULL to skip); n_atoms: n_sig x nroi int32 (NULL to skip); these three
  * in `mem`.
  * flags: APTIDX_NORMALISE_MAX or 0.  The context's ROI bands and type mask
- * are left as they were.  Errors: INVALID_ARG, STATE, OOM, CUDA, TIMEOUT. */
+ * are left as they were; masks that select atom types beyond the context's
+ * mask grow the gather buffer to the union of the masks.  Errors:
+ * INVALID_ARG, STATE, OOM, CUDA, TIMEOUT, OVERFLOW (a ROI above
+ * APTIDX_MAX_ATOMS_PER_ROI atoms of the requested types). */
 #define APTIDX_MAX_BANDS 4
 int aptidx_compute_signatures_multi(aptidx_ctx* ctx, int path, unsigned flags, int32_t n_sig,
                                     const uint32_t* type_mask, const int32_t* k_lo, const int32_t* k_hi, float* S,

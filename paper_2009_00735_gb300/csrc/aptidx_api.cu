@@ -1172,6 +1172,42 @@ int aptidx_compute_signatures_multi(aptidx_ctx* ctx, int path, unsigned flags, i
                 passes.emplace_back(grp.begin() + i, grp.begin() + std::min(grp.size(), i + APTIDX_MAX_BANDS));
         }
     }
+    // the gather buffer was sized for the context's type mask; a pass that
+    // selects further atom types needs it sized for the union of the masks
+    {
+        uint32_t umask = 0;
+        for (int s = 0; s < n_sig; ++s) umask |= type_mask[s];
+        if (umask & ~c->type_mask) {
+            const uint32_t m0 = c->type_mask;
+            c->type_mask = umask;
+            APTIDX_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+            cudaError_t e = launch_gather_count(c);
+            c->type_mask = m0;
+            if (e != cudaSuccess) return cuda_check(c, e, "ROI count");
+            std::vector<int32_t> hnw((size_t)c->nroi);
+            APTIDX_CUDA(c, cudaMemcpyAsync(hnw.data(), c->d_nw, (size_t)c->nroi * sizeof(int32_t),
+                                           cudaMemcpyDeviceToHost, c->stream));
+            APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
+            int64_t total = 0;
+            int32_t nwmax = 0;
+            for (int64_t r = 0; r < c->nroi; ++r) {
+                total += hnw[(size_t)r];
+                nwmax = std::max(nwmax, hnw[(size_t)r]);
+            }
+            if (nwmax > APTIDX_MAX_ATOMS_PER_ROI) {
+                APTIDX_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+                return set_error(c, APTIDX_E_OVERFLOW, "a ROI holds %d atoms of the requested types (limit %d)",
+                                 nwmax, APTIDX_MAX_ATOMS_PER_ROI);
+            }
+            if (total > c->atoms_cap) {
+                free_ptr(c->d_atoms);
+                c->atoms_cap = 0;
+                if ((rc = dev_alloc(c, (void**)&c->d_atoms, (size_t)total * sizeof(float4)))) return rc;
+                c->atoms_cap = total;
+            }
+            if ((rc = read_status(c))) return rc;
+        }
+    }
     // the context's ROI bands and type mask are restored afterwards; cached
     // graphs may hold the B operand of other bands, so they are dropped
     clear_graphs(c);

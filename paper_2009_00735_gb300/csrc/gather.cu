@@ -269,6 +269,7 @@ struct GatherParams {
     int32_t* nw;           // count pass output
     const int64_t* off;    // fill pass input
     float4* atoms;         // fill pass output
+    int64_t atoms_cap;     // entries of atoms (a fill past it records OVERFLOW and writes nothing)
     int* status;
 };
 
@@ -329,8 +330,11 @@ __global__ void __launch_bounds__(256) k_gather(GatherParams p) {
                         unsigned bal = __ballot_sync(0xffffffffu, in);
                         if (kFill && in) {
                             int64_t o = base + count + __popc(bal & lt_mask);
-                            p.atoms[o] = make_float4(__double2float_rn(dx), __double2float_rn(dy),
-                                                     __double2float_rn(dz), 0.0f);
+                            if (o < p.atoms_cap)
+                                p.atoms[o] = make_float4(__double2float_rn(dx), __double2float_rn(dy),
+                                                         __double2float_rn(dz), 0.0f);
+                            else
+                                raise_status(p.status, kStatusOverflow);
                         }
                         count += __popc(bal);
                     }
@@ -356,6 +360,7 @@ static GatherParams gather_params(Ctx* c) {
     p.nw = c->d_nw;
     p.off = c->d_off;
     p.atoms = c->d_atoms;
+    p.atoms_cap = c->d_atoms ? c->atoms_cap : 0;
     p.status = c->d_status;
     return p;
 }

@@ -82,3 +82,42 @@ def test_multi_signatures(torch_cuda, l12, path):
     apt.aptidx_compute_signatures_multi(h, path, apt.APTIDX_NORMALISE_MAX, masks, lo, hi, Sn)
     assert np.allclose(Sn.cpu().numpy().max(axis=2), 1.0)
     ctx.close()
+
+
+@pytest.mark.parametrize("path", [apt.APTIDX_PATH_PLAIN_FP32, apt.APTIDX_PATH_TC_FP16])
+def test_multi_masks_wider_than_the_context(torch_cuda, l12, path):
+    """The ROI set gathers the Sc sub-lattice only; a multi call that also
+    asks for all atoms sizes its gather buffer for the union of the masks
+    and matches the oracle; afterwards the context still gathers Sc only."""
+    torch = torch_cuda
+    xyz, types, centres, radii = l12
+    m = 9
+    a = 0.410
+    masks = [ALL, SC, ALL]
+    bands = [spacing_band(a / 2, 1.5, m), spacing_band(a, 1.5, m), spacing_band(a / np.sqrt(3), 1.5, m)]
+    lo = [b[0] for b in bands]
+    hi = [b[1] for b in bands]
+    dirs = np.ascontiguousarray(synth.icosphere(4))
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda(), torch.from_numpy(types).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(dirs).cuda())
+    apt.aptidx_set_binning(h, m, lo[1], hi[1])
+    apt.aptidx_set_rois(h, centres, radii, type_mask=SC)
+    nroi, nv = centres.shape[0], dirs.shape[0]
+    S = torch.empty((len(masks), nroi, nv), dtype=torch.float32, device="cuda")
+    N = torch.empty((len(masks), nroi), dtype=torch.int32, device="cuda")
+    apt.aptidx_compute_signatures_multi(h, path, 0, masks, lo, hi, S, None, N)
+    S, N = S.cpu().numpy(), N.cpu().numpy()
+    tol = TOL_PLAIN if path == apt.APTIDX_PATH_PLAIN_FP32 else TOL_TC
+    for s in range(len(masks)):
+        So, _, No = oracle.signatures(xyz, centres, radii, lo[s], hi[s], dirs, m, types=types, type_mask=masks[s])
+        assert np.array_equal(N[s], No), s
+        keep = No > 0
+        assert roi_error(S[s][keep], So[keep]).max() <= tol, s
+    S1 = torch.empty((nroi, nv), dtype=torch.float32, device="cuda")
+    N1 = torch.empty(nroi, dtype=torch.int32, device="cuda")
+    apt.aptidx_compute_signatures(h, path, 0, S1, None, N1)
+    assert np.array_equal(N1.cpu().numpy(), N[1])
+    assert np.allclose(S1.cpu().numpy(), S[1], rtol=1e-6, atol=0)
+    ctx.close()
