@@ -330,7 +330,8 @@ static void orc_cubic_symmetry(double q[24][4])
 
 /* Disorientation angle (degrees) between two cubic orientations: the
  * smallest rotation angle of q1^-1 q2 s over the 24 proper cubic rotations s
- * (supplement: "disorientation ... smallest rotation angle"). */
+ * (the supplement defines the disorientation as the symmetry-equivalent
+ * misorientation of least rotation angle). */
 double orc_disorientation_deg(const double* q1, const double* q2)
 {
     double sym[24][4];
