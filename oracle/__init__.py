@@ -42,6 +42,29 @@ def lib():
     return _lib
 
 
+def build_mutant(k: int) -> str:
+    """Test-only: the oracle compiled with planted mistake k (the
+    ORC_MUTATION points of the C source), for checking that the pins catch
+    it.  Returns the library path."""
+    path = os.path.join(os.path.dirname(_LIB), f"liboracle_mut{int(k)}.so")
+    if os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                    f"-DORC_MUTATION={int(k)}", "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, path)
+    return path
+
+
+def use_library(path=None):
+    """Test-only: route every wrapper to the library at `path` (None: the
+    default build)."""
+    global _lib
+    _lib = C.CDLL(path if path else build())
+    _declare(_lib)
+
+
 _p = C.c_void_p
 _i64 = C.c_int64
 _i32 = C.c_int32

@@ -38,6 +38,15 @@
 
 #define ORC_PI 3.14159265358979323846264338327950288
 
+/* Test-only mutation points.  A build with -DORC_MUTATION=k plants the k-th
+ * plausible mistake listed in tests/test_oracle_mutations.py (a dropped term,
+ * an off-by-one, a transposed operand, ...), so that the test can check that
+ * the pins of tests/test_oracle_pins.py catch it.  The default build
+ * (ORC_MUTATION = 0) contains none of them. */
+#ifndef ORC_MUTATION
+#define ORC_MUTATION 0
+#endif
+
 /* ------------------------------------------------------------------------ */
 /* Section 2.2 / SI cost O_Proj: atoms of the ROI                            */
 /* ------------------------------------------------------------------------ */
@@ -60,7 +69,7 @@ int64_t orc_gather(const float* xyz, int64_t n, const uint8_t* types, uint32_t t
     const double R2 = R * R;
     for (int64_t i = 0; i < n; ++i) {
         if (!orc_selected(types, i, type_mask)) continue;
-        double dx = (double)xyz[3 * i + 0] - c[0];
+        double dx = (double)xyz[3 * i + (ORC_MUTATION == 6 ? 1 : 0)] - c[0];
         double dy = (double)xyz[3 * i + 1] - c[1];
         double dz = (double)xyz[3 * i + 2] - c[2];
         double xx = dx * dx;
@@ -99,7 +108,8 @@ int orc_bin_eq1(const double* u, const double* x, int m, double R)
 {
     const double dR = R / (double)((1 << (m - 1)) - 1);
     const double s = (u[0] * x[0] + u[1] * x[1]) + u[2] * x[2];
-    const double t = (s + R + dR) * (double)(1 << m) / (dR + 2.0 * R + dR);
+    const double t = ORC_MUTATION == 4 ? (s + R) * (double)(1 << m) / (2.0 * R)
+                                       : (s + R + dR) * (double)(1 << m) / (dR + 2.0 * R + dR);
     return (int)orc_clamp_bin(floor(t), m);
 }
 
@@ -120,6 +130,7 @@ float orc_project_f32(const float* u, const float* x)
 {
     float p = u[0] * x[0];
     float a = fmaf(u[1], x[1], p);
+    if (ORC_MUTATION == 1) return a;
     return fmaf(u[2], x[2], a);
 }
 
@@ -128,7 +139,7 @@ int orc_bin_contract(const float* u, const float* x, int m, double R)
     const float s = orc_project_f32(u, x);
     const float scale = orc_bin_scale(m, R);
     const double prod = (double)s * (double)scale;   /* exact */
-    const double f = (double)(1 << (m - 1)) + floor(prod);
+    const double f = (double)((1 << (m - 1)) - (ORC_MUTATION == 2)) + floor(prod);
     return (int)orc_clamp_bin(f, m);
 }
 
@@ -186,7 +197,7 @@ static void orc_band_amplitudes_tw(const int32_t* h, int m, int k_lo, int k_hi,
         double re = 0.0, im = 0.0;
         for (int64_t n = 0; n < nb; ++n) {
             if (!h[n]) continue;
-            int64_t j = ((int64_t)k * n) % nb;
+            int64_t j = ((int64_t)(k + (ORC_MUTATION == 3)) * n) % nb;
             re += (double)h[n] * cs[j];
             im -= (double)h[n] * sn[j];
         }
@@ -228,7 +239,7 @@ void orc_roi_signature(const float* xc, int64_t nw, const float* u, int64_t nv, 
         double best = -1.0;
         int bk = k_lo;
         for (int k = 0; k < nk; ++k)
-            if (amp[k] > best) { best = amp[k]; bk = k_lo + k; }
+            if (ORC_MUTATION == 8 ? amp[k] >= best : amp[k] > best) { best = amp[k]; bk = k_lo + k; }
         S[v] = nk > 0 ? best : 0.0;
         if (argk) argk[v] = bk;
     }
@@ -265,7 +276,9 @@ void orc_normalise(double* S, int64_t nroi, int64_t nv)
 {
     for (int64_t r = 0; r < nroi; ++r) {
         double mx = 0.0;
-        for (int64_t v = 0; v < nv; ++v) if (S[r * nv + v] > mx) mx = S[r * nv + v];
+        for (int64_t v = 0; v < nv; ++v)
+            if (ORC_MUTATION == 13) mx += S[r * nv + v];
+            else if (S[r * nv + v] > mx) mx = S[r * nv + v];
         for (int64_t v = 0; v < nv; ++v) S[r * nv + v] = mx > 0.0 ? S[r * nv + v] / mx : 0.0;
     }
 }
@@ -340,7 +353,7 @@ double orc_disorientation_deg(const double* q1, const double* q2)
     double d[4];
     orc_quat_mul(inv, q2, d);
     double best = 0.0;
-    for (int s = 0; s < 24; ++s) {
+    for (int s = 0; s < 24 - (ORC_MUTATION == 12); ++s) {
         double e[4];
         orc_quat_mul(d, sym[s], e);
         double w = fabs(e[0]) / sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + e[3] * e[3]);
@@ -363,7 +376,7 @@ static int orc_vi_cmp(const void* a, const void* b)
     const orc_vi* y = (const orc_vi*)b;
     if (x->v > y->v) return -1;
     if (x->v < y->v) return 1;
-    return (x->i > y->i) - (x->i < y->i);
+    return ORC_MUTATION == 10 ? (x->i < y->i) - (x->i > y->i) : (x->i > y->i) - (x->i < y->i);
 }
 
 void orc_top_nodes(const float* sig, int64_t nv, int n_hat, int32_t* out)
@@ -394,10 +407,10 @@ void orc_rotate_node(const double* q, const float* nrm, float* r)
 int32_t orc_nearest_node(const float* u, int64_t nv, const float* r)
 {
     int32_t best = 0;
-    float bd = -INFINITY;
+    float bd = ORC_MUTATION == 11 ? INFINITY : -INFINITY;
     for (int64_t p = 0; p < nv; ++p) {
         float d = orc_project_f32(u + 3 * p, r);
-        if (d > bd) { bd = d; best = (int32_t)p; }
+        if (ORC_MUTATION == 11 ? d < bd : d > bd) { bd = d; best = (int32_t)p; }
     }
     return best;
 }
@@ -435,7 +448,7 @@ void orc_match(const float* S_msr, int64_t nroi, int64_t nv, const float* S_ref,
             double acc = 0.0;
             for (int k = 0; k < n_hat; ++k) {
                 double d = (double)s[lut[g * n_hat + k]] - (double)S_ref[top[k]];
-                acc += d * d;
+                acc += ORC_MUTATION == 5 ? fabs(d) : d * d;
             }
             if (scores) scores[r * ng + g] = acc;
             if (acc < bs) { bs = acc; bg = (int32_t)g; }
@@ -532,6 +545,8 @@ void orc_refine_eval(const float* img, const float* S_msr, const float* u, int64
         J[0] = -(a[1] * uz - a[2] * uy);
         J[1] = -(a[2] * ux - a[0] * uz);
         J[2] = -(a[0] * uy - a[1] * ux);
+        if (ORC_MUTATION == 9)
+            for (int i = 0; i < 3; ++i) J[i] = -J[i];
         L += wv * r * r;
         for (int i = 0; i < 3; ++i) {
             g[i] += wv * 2.0 * r * J[i];
@@ -633,7 +648,8 @@ void orc_fsp(const float* xc, int64_t nw, int L, double kmax, const int64_t* pts
         const double kx = -kmax + ix * dk, ky = -kmax + iy * dk, kz = -kmax + iz * dk;
         double re = 0.0, im = 0.0;
         for (int64_t w = 0; w < nw; ++w) {
-            const double ph = 2.0 * ORC_PI * (kx * (double)xc[3 * w] + ky * (double)xc[3 * w + 1] +
+            const double ka = ORC_MUTATION == 7 ? ky : kx, kb = ORC_MUTATION == 7 ? kx : ky;
+            const double ph = 2.0 * ORC_PI * (ka * (double)xc[3 * w] + kb * (double)xc[3 * w + 1] +
                                                kz * (double)xc[3 * w + 2]);
             re += cos(ph);
             im -= sin(ph);

@@ -227,6 +227,10 @@ def test_signature_is_band_max_with_lowest_argk():
     # X(0) = N_w: the peak at the origin counts the atoms (Section 3.1)
     S0, _ = oracle.roi_signature(xc, u, 8, 1.0, 0, 0)
     assert np.allclose(S0, xc.shape[0])
+    # exact ties: one atom at the centre sits in bin 2^(m-1), so
+    # X(k) = (-1)^k and |X(k)| = 1 at every k; the lowest k of the band wins
+    S1, ak1 = oracle.roi_signature(np.zeros((1, 3), np.float32), u[:4], 8, 1.0, 6, 14)
+    assert np.all(S1 == 1.0) and np.all(ak1 == 6)
 
 
 # --------------------------------------------------------------------------
@@ -396,6 +400,13 @@ def test_lut_is_nearest_node():
             r = M @ u[v].astype(np.float64)
             dots = u.astype(np.float64) @ r
             assert dots[L[g, k]] >= dots.max() - 1e-6
+
+
+def test_normalise_divides_each_row_by_its_maximum():
+    """Normalisation S / max_v S per row (values exact in binary); an
+    all-zero row stays zero."""
+    S = np.array([[0.5, 2.0, 1.0], [0.0, 0.0, 0.0], [3.0, 3.0, 1.5]])
+    assert np.array_equal(oracle.normalise(S), [[0.25, 1.0, 0.5], [0.0, 0.0, 0.0], [1.0, 1.0, 0.5]])
 
 
 def test_top_nodes_order_and_ties():
