@@ -291,8 +291,8 @@ void orc_band_for_spacing(double d_min, double d_max, double R, int m, int32_t* 
 {
     const double dR = R / (double)((1 << (m - 1)) - 1);
     const double W = 2.0 * (R + dR);
-    *k_lo = (int32_t)ceil(W / d_max);
-    *k_hi = (int32_t)floor(W / d_min);
+    *k_lo = (int32_t)(ORC_MUTATION == 16 ? floor(W / d_max) : ceil(W / d_max));
+    *k_hi = (int32_t)(ORC_MUTATION == 16 ? ceil(W / d_min) : floor(W / d_min));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -310,6 +310,12 @@ void orc_quat_to_matrix(const double* q, double* M)
     M[0] = 1.0 - 2.0 * (yy + zz); M[1] = 2.0 * (xy - wz);       M[2] = 2.0 * (xz + wy);
     M[3] = 2.0 * (xy + wz);       M[4] = 1.0 - 2.0 * (xx + zz); M[5] = 2.0 * (yz - wx);
     M[6] = 2.0 * (xz - wy);       M[7] = 2.0 * (yz + wx);       M[8] = 1.0 - 2.0 * (xx + yy);
+    if (ORC_MUTATION == 14) {
+        double t;
+        t = M[1]; M[1] = M[3]; M[3] = t;
+        t = M[2]; M[2] = M[6]; M[6] = t;
+        t = M[5]; M[5] = M[7]; M[7] = t;
+    }
 }
 
 static void orc_quat_mul(const double* a, const double* b, double* o)
@@ -494,6 +500,7 @@ int orc_bilinear(const float* img, const double* c, double* val, double* grad, i
     int j0 = (int)floor(fj);
     double ti = fi - (double)i0;
     double tj = fj - (double)j0;
+    if (ORC_MUTATION == 15) tj = 1.0 - tj;
     j0 %= ORC_IMG_NB;
     int j1 = (j0 + 1) % ORC_IMG_NB;
     const double I00 = img[i0 * ORC_IMG_NB + j0], I01 = img[i0 * ORC_IMG_NB + j1];
@@ -597,7 +604,8 @@ void orc_refine(const float* img, const float* S_msr, const float* u, int64_t nv
         const double lam = 1e-6 * (H[0] + H[4] + H[8]);
         H[0] += lam; H[4] += lam; H[8] += lam;
         double d[3];
-        double nb[3] = {-b[0], -b[1], -b[2]};
+        const double sg = ORC_MUTATION == 18 ? 1.0 : -1.0;
+        double nb[3] = {sg * b[0], sg * b[1], sg * b[2]};
         orc_solve3(H, nb, d);
         double e[4], qn[4];
         orc_exp_quat(d, e);
@@ -641,7 +649,7 @@ int orc_openmp_threads(void)
 /* ------------------------------------------------------------------------ */
 void orc_fsp(const float* xc, int64_t nw, int L, double kmax, const int64_t* pts, int64_t npts, double* out)
 {
-    const double dk = 2.0 * kmax / (double)(L - 1);
+    const double dk = 2.0 * kmax / (double)(ORC_MUTATION == 17 ? L : L - 1);
     for (int64_t p = 0; p < npts; ++p) {
         const int64_t f = pts[p];
         const int iz = (int)(f % L), iy = (int)((f / L) % L), ix = (int)(f / ((int64_t)L * L));

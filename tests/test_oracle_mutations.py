@@ -25,6 +25,12 @@ MUTANTS = {
     12: ("disorientation over 23 of the 24 proper cubic rotations", "test_disorientation_textbook_values", {}),
     13: ("normalisation by the row sum instead of the row maximum",
          "test_normalise_divides_each_row_by_its_maximum", {}),
+    14: ("rotation matrix transposed", "test_quat_to_matrix_matches_axis_angle_rodrigues", {}),
+    15: ("bilinear weights of the two image columns swapped",
+         "test_bilinear_reproduces_grid_values_and_is_linear_inside_cells", {}),
+    16: ("band edges rounded outwards", "test_band_interval_reproduces_paper_al_200", {}),
+    17: ("Eq. 2 grid spacing 2 k_max / L instead of 2 k_max / (L - 1)", "test_fsp_closed_forms", {}),
+    18: ("Gauss-Newton step with the wrong sign", "test_refine_converges_to_truth", {}),
 }
 
 
