@@ -114,6 +114,45 @@ def test_bin_contract_brute_force_rational():
             assert h[v].sum() == 10
 
 
+def bin_edge_positions(m, R, n=40, seed=0):
+    """float32 coordinates on and one ulp either side of bin edges: for
+    integers j across the histogram, x0 = the float32 nearest to j / scale
+    (s * scale = j is a bin edge of the contract when s = x0), then its two
+    float32 neighbours.  |x| <= R except possibly one ulp past it."""
+    scale = Fraction(float(np.float32(float(Fraction((1 << (m - 1)) - 1) / Fraction(R)))))
+    half = (1 << (m - 1)) - 1
+    rng = np.random.default_rng(seed)
+    js = np.concatenate([[0, 1, -1, half - 1, -(half - 1)], rng.integers(-half + 1, half, n)])
+    xs = []
+    for j in js:
+        x0 = np.float32(float(Fraction(int(j)) / scale))
+        xs += [np.nextafter(x0, np.float32(-np.inf)), x0, np.nextafter(x0, np.float32(np.inf))]
+    return np.array(xs, np.float32)
+
+
+@pytest.mark.parametrize("m, R", [(8, 1.0), (10, 2.0), (10, 2.37)])
+def test_bin_contract_at_bin_edges(m, R):
+    """Atoms on and one ulp around bin edges (projection along a coordinate
+    axis, so s is the coordinate itself): the oracle's contract equals the
+    exact-rational contract, and the bins of x0 - ulp, x0, x0 + ulp never
+    decrease and step by at most one."""
+    xs = bin_edge_positions(m, R)
+    rng = np.random.default_rng(1)
+    for axis in range(3):
+        u = np.zeros(3, np.float32)
+        u[axis] = 1.0
+        for t in range(0, xs.shape[0], 3):
+            bins = []
+            for d in range(3):
+                x = (rng.random(3).astype(np.float32) - np.float32(0.5)) * np.float32(0.1)
+                x[axis] = xs[t + d]
+                b = oracle.bin_contract(u, x, m, R)
+                assert b == contract_bin_exact(u, x, m, R)
+                bins.append(b)
+            # every triple straddles exactly one edge
+            assert bins[0] <= bins[1] <= bins[2] and bins[2] - bins[0] == 1
+
+
 def test_bin_eq1_matches_exact_eq1_and_contract_moves_only_boundary_atoms():
     """The FP64 Eq. 1 oracle equals exact-rational Eq. 1, and the FP32
     contract differs from Eq. 1 only for atoms within a few float ulps of a
