@@ -54,7 +54,7 @@
 static int orc_selected(const uint8_t* types, int64_t i, uint32_t type_mask)
 {
     if (!types) return 1;
-    unsigned t = types[i];
+    unsigned t = types[i] + (ORC_MUTATION == 19);
     return t < 32u && ((type_mask >> t) & 1u);
 }
 
@@ -181,7 +181,7 @@ static void orc_twiddles(int m, double* cs, double* sn)
 {
     const int64_t nb = (int64_t)1 << m;
     for (int64_t j = 0; j < nb; ++j) {
-        double th = 2.0 * ORC_PI * (double)j / (double)nb;
+        double th = 2.0 * ORC_PI * (double)j / (double)(nb - (ORC_MUTATION == 21));
         cs[j] = cos(th);
         sn[j] = sin(th);
     }
@@ -401,9 +401,10 @@ void orc_rotate_node(const double* q, const float* nrm, float* r)
     double M[9];
     orc_quat_to_matrix(q, M);
     for (int i = 0; i < 3; ++i) {
-        double a = M[3 * i + 0] * (double)nrm[0];
-        double b = M[3 * i + 1] * (double)nrm[1];
-        double c = M[3 * i + 2] * (double)nrm[2];
+        const int st = ORC_MUTATION == 20 ? 3 : 1, rs = ORC_MUTATION == 20 ? 1 : 3;
+        double a = M[rs * i + 0 * st] * (double)nrm[0];
+        double b = M[rs * i + 1 * st] * (double)nrm[1];
+        double c = M[rs * i + 2 * st] * (double)nrm[2];
         r[i] = (float)((a + b) + c);
     }
 }

@@ -31,6 +31,9 @@ MUTANTS = {
     16: ("band edges rounded outwards", "test_band_interval_reproduces_paper_al_200", {}),
     17: ("Eq. 2 grid spacing 2 k_max / L instead of 2 k_max / (L - 1)", "test_fsp_closed_forms", {}),
     18: ("Gauss-Newton step with the wrong sign", "test_refine_converges_to_truth", {}),
+    19: ("atom type bits read one position off", "test_gather_type_mask", {}),
+    20: ("reference nodes rotated by the transposed matrix", "test_lut_is_nearest_node", {}),
+    21: ("DFT twiddle angles over N_b - 1 instead of N_b", "test_spectrum_matches_numpy_rfft", {"m": 8}),
 }
 
 
