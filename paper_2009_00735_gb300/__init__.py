@@ -188,6 +188,7 @@ def _check(ctx, rc):
 # ---------------------------------------------------------------------------
 
 def aptidx_version() -> int:
+    """Library version, major * 10000 + minor * 100 + patch."""
     return load().aptidx_version()
 
 
@@ -208,18 +209,23 @@ def aptidx_create(device: int = 0, stream=None):
 
 
 def aptidx_destroy(ctx):
+    """Synchronise and free the context and every buffer it owns."""
     _check(None, load().aptidx_destroy(ctx))
 
 
 def aptidx_last_error(ctx) -> str:
+    """Message of the context's last failing call ("" if none)."""
     return load().aptidx_last_error(ctx).decode()
 
 
 def aptidx_sync(ctx):
+    """Synchronise the context's stream; raises on a device status (TIMEOUT, OVERFLOW)."""
     _check(ctx, load().aptidx_sync(ctx))
 
 
 def aptidx_load_positions(ctx, xyz, types=None):
+    """Atom positions p_i: xyz [n, 3] float32 (nm), types [n] uint8 or None;
+    host (numpy) or device (torch) arrays, copied by the library."""
     p, m, k1 = _arg(xyz, np.float32)
     t, mt, k2 = _arg(types, np.uint8)
     n = (k1.numel() if _is_torch(k1) else k1.size) // 3
@@ -227,16 +233,21 @@ def aptidx_load_positions(ctx, xyz, types=None):
 
 
 def aptidx_set_directions(ctx, u):
+    """Projection directions: u [nv, 3] float32 unit vectors."""
     p, m, k = _arg(u, np.float32)
     nv = (k.numel() if _is_torch(k) else k.size) // 3
     _check(ctx, load().aptidx_set_directions(ctx, p, nv, m))
 
 
 def aptidx_set_binning(ctx, m: int, k_lo: int, k_hi: int, flags: int = 0):
+    """2^m histogram bins (Eq. 1) and the default band [k_lo, k_hi] of
+    frequency bins whose amplitude maximum is the signature."""
     _check(ctx, load().aptidx_set_binning(ctx, m, k_lo, k_hi, flags))
 
 
 def aptidx_set_rois(ctx, centres, radii, band_lo=None, band_hi=None, type_mask=0xFFFFFFFF):
+    """ROIs: centres [nroi, 3] float64 (nm), radii [nroi] float64, optional
+    per-ROI bands (int32 arrays or scalars), atom-type bit mask."""
     pc, mc, kc = _arg(centres, np.float64)
     pr, mr, kr = _arg(radii, np.float64)
     nroi = (kr.numel() if _is_torch(kr) else kr.size)
@@ -250,6 +261,10 @@ def aptidx_set_rois(ctx, centres, radii, band_lo=None, band_hi=None, type_mask=0
 
 
 def aptidx_compute_signatures(ctx, path: int, flags: int, S=None, argk=None, n_atoms=None):
+    """Signatures of every ROI on `path` (APTIDX_PATH_PLAIN_FP32 or
+    APTIDX_PATH_TC_FP16): S [nroi, nv] float32, argk [nroi, nv] uint16 and
+    n_atoms [nroi] int32 (each optional, host or device); flags:
+    APTIDX_NORMALISE_MAX | APTIDX_AUTOTUNE | APTIDX_GRAPH."""
     pS, mS = _out(S, np.float32)
     pA, mA = _out(argk, np.uint16)
     pN, mN = _out(n_atoms, np.int32)
@@ -308,11 +323,15 @@ def aptidx_compute_fsp(ctx, amp, k_max: float = 2 * 3.141592653589793):
 
 
 def aptidx_get_histograms(ctx, roi: int, path: int, h):
+    """Debug/parity: the 2^m-bin histograms of ROI `roi` as `path`'s
+    histogram stage computes them, h [nv, 2^m] uint16."""
     p, m = _out(h, np.uint16)
     _check(ctx, load().aptidx_get_histograms(ctx, roi, path, p, m))
 
 
 def aptidx_get_roi_atoms(ctx, roi: int, xc=None, cap: int = 0):
+    """Debug/parity: the centred FP32 atoms of ROI `roi` as the gather
+    produced them, [n_w, 3] (allocated when xc is None)."""
     n = _i64(0)
     if xc is None:
         rc = load().aptidx_get_roi_atoms(ctx, roi, None, 0, C.byref(n), APTIDX_MEM_HOST)
@@ -326,12 +345,17 @@ def aptidx_get_roi_atoms(ctx, roi: int, xc=None, cap: int = 0):
 
 
 def aptidx_set_reference(ctx, cand: int, node_sig, n_hat: int, img=None):
+    """Reference of candidate `cand`: its normalised signature on the
+    directions (node_sig [nv] float32, the n_hat strongest nodes enter Eq. 3)
+    and optionally its [181, 360] elevation-azimuth image for refinement."""
     p, m, k = _arg(node_sig, np.float32)
     pi, mi, ki = _arg(img, np.float32)
     _check(ctx, load().aptidx_set_reference(ctx, cand, p, n_hat, pi, _one_mem(m, mi)))
 
 
 def aptidx_build_lut(ctx, cand: int, quats):
+    """Look-up table of candidate `cand` for test orientations quats
+    [ng, 4] float64 (w, x, y, z; crystal to lab)."""
     p, m, k = _arg(quats, np.float64)
     ng = (k.numel() if _is_torch(k) else k.size) // 4
     _check(ctx, load().aptidx_build_lut(ctx, cand, p, ng, m))
@@ -349,6 +373,8 @@ def aptidx_get_lut(ctx, cand: int, ng: int = None):
 
 
 def aptidx_match(ctx, cand: int, S, best, score=None):
+    """Eq. 3 for every ROI: best [nroi] int32 = argmin_g Delta(g) (ties:
+    lowest g), score [nroi] float32 = Delta(best); S [nroi, nv] normalised."""
     pS, mS, kS = _arg(S, np.float32)
     pb, mb = _out(best, np.int32)
     ps, ms = _out(score, np.float32)
@@ -366,6 +392,8 @@ def aptidx_match_topk(ctx, cand: int, S, topk: int, best, score=None):
 
 
 def aptidx_refine_loss(ctx, cand: int, S, q0, loss, grad=None, omega=None):
+    """Refinement loss [nroi] and its gradient [nroi, 3] with respect to
+    the axis-angle offset omega [nroi, 3] (None: zero) at q0 [nroi, 4]."""
     pS, mS, kS = _arg(S, np.float32)
     pq, mq, kq = _arg(q0, np.float64)
     pw, mw, kw = _arg(omega, np.float64)
@@ -388,6 +416,7 @@ def aptidx_refine(ctx, cand: int, S, q0, iters: int, q_out, loss=None, best=None
 
 
 def aptidx_path_supported(ctx, path: int) -> bool:
+    """True if `path` runs on the context's device."""
     return bool(load().aptidx_path_supported(ctx, path))
 
 
@@ -400,6 +429,8 @@ def aptidx_get_tuning(ctx, path: int):
 
 
 def aptidx_set_profiling(ctx, enable: bool):
+    """Record per-phase CUDA-event times and kernel counts of the following
+    calls (resets the totals), or stop recording."""
     _check(ctx, load().aptidx_set_profiling(ctx, 1 if enable else 0))
 
 
