@@ -46,6 +46,10 @@
 #ifndef ORC_MUTATION
 #define ORC_MUTATION 0
 #endif
+/* MUT(k, wrong, right): the planted mistake k in a mutant build, the
+ * definition otherwise (a compile-time choice; the default build evaluates
+ * `right` only). */
+#define MUT(k, wrong, right) ((ORC_MUTATION == (k)) ? (wrong) : (right))
 
 /* ------------------------------------------------------------------------ */
 /* Section 2.2 / SI cost O_Proj: atoms of the ROI                            */
@@ -54,7 +58,7 @@
 static int orc_selected(const uint8_t* types, int64_t i, uint32_t type_mask)
 {
     if (!types) return 1;
-    unsigned t = types[i] + (ORC_MUTATION == 19);
+    unsigned t = types[i] + MUT(19, 1u, 0u);
     return t < 32u && ((type_mask >> t) & 1u);
 }
 
@@ -69,7 +73,7 @@ int64_t orc_gather(const float* xyz, int64_t n, const uint8_t* types, uint32_t t
     const double R2 = R * R;
     for (int64_t i = 0; i < n; ++i) {
         if (!orc_selected(types, i, type_mask)) continue;
-        double dx = (double)xyz[3 * i + (ORC_MUTATION == 6 ? 1 : 0)] - c[0];
+        double dx = (double)xyz[3 * i + MUT(6, 1, 0)] - c[0];
         double dy = (double)xyz[3 * i + 1] - c[1];
         double dz = (double)xyz[3 * i + 2] - c[2];
         double xx = dx * dx;
@@ -108,8 +112,8 @@ int orc_bin_eq1(const double* u, const double* x, int m, double R)
 {
     const double dR = R / (double)((1 << (m - 1)) - 1);
     const double s = (u[0] * x[0] + u[1] * x[1]) + u[2] * x[2];
-    const double t = ORC_MUTATION == 4 ? (s + R) * (double)(1 << m) / (2.0 * R)
-                                       : (s + R + dR) * (double)(1 << m) / (dR + 2.0 * R + dR);
+    const double t = MUT(4, (s + R) * (double)(1 << m) / (2.0 * R),
+                            (s + R + dR) * (double)(1 << m) / (dR + 2.0 * R + dR));
     return (int)orc_clamp_bin(floor(t), m);
 }
 
@@ -130,8 +134,7 @@ float orc_project_f32(const float* u, const float* x)
 {
     float p = u[0] * x[0];
     float a = fmaf(u[1], x[1], p);
-    if (ORC_MUTATION == 1) return a;
-    return fmaf(u[2], x[2], a);
+    return MUT(1, a, fmaf(u[2], x[2], a));
 }
 
 int orc_bin_contract(const float* u, const float* x, int m, double R)
@@ -139,7 +142,7 @@ int orc_bin_contract(const float* u, const float* x, int m, double R)
     const float s = orc_project_f32(u, x);
     const float scale = orc_bin_scale(m, R);
     const double prod = (double)s * (double)scale;   /* exact */
-    const double f = (double)((1 << (m - 1)) - (ORC_MUTATION == 2)) + floor(prod);
+    const double f = (double)((1 << (m - 1)) - MUT(2, 1, 0)) + floor(prod);
     return (int)orc_clamp_bin(f, m);
 }
 
@@ -181,7 +184,7 @@ static void orc_twiddles(int m, double* cs, double* sn)
 {
     const int64_t nb = (int64_t)1 << m;
     for (int64_t j = 0; j < nb; ++j) {
-        double th = 2.0 * ORC_PI * (double)j / (double)(nb - (ORC_MUTATION == 21));
+        double th = 2.0 * ORC_PI * (double)j / (double)(nb - MUT(21, 1, 0));
         cs[j] = cos(th);
         sn[j] = sin(th);
     }
@@ -197,7 +200,7 @@ static void orc_band_amplitudes_tw(const int32_t* h, int m, int k_lo, int k_hi,
         double re = 0.0, im = 0.0;
         for (int64_t n = 0; n < nb; ++n) {
             if (!h[n]) continue;
-            int64_t j = ((int64_t)(k + (ORC_MUTATION == 3)) * n) % nb;
+            int64_t j = ((int64_t)(k + MUT(3, 1, 0)) * n) % nb;
             re += (double)h[n] * cs[j];
             im -= (double)h[n] * sn[j];
         }
@@ -239,7 +242,7 @@ void orc_roi_signature(const float* xc, int64_t nw, const float* u, int64_t nv, 
         double best = -1.0;
         int bk = k_lo;
         for (int k = 0; k < nk; ++k)
-            if (ORC_MUTATION == 8 ? amp[k] >= best : amp[k] > best) { best = amp[k]; bk = k_lo + k; }
+            if (MUT(8, amp[k] >= best, amp[k] > best)) { best = amp[k]; bk = k_lo + k; }
         S[v] = nk > 0 ? best : 0.0;
         if (argk) argk[v] = bk;
     }
@@ -276,9 +279,10 @@ void orc_normalise(double* S, int64_t nroi, int64_t nv)
 {
     for (int64_t r = 0; r < nroi; ++r) {
         double mx = 0.0;
-        for (int64_t v = 0; v < nv; ++v)
-            if (ORC_MUTATION == 13) mx += S[r * nv + v];
-            else if (S[r * nv + v] > mx) mx = S[r * nv + v];
+        for (int64_t v = 0; v < nv; ++v) {
+            const double s = S[r * nv + v];
+            mx = MUT(13, mx + s, s > mx ? s : mx);
+        }
         for (int64_t v = 0; v < nv; ++v) S[r * nv + v] = mx > 0.0 ? S[r * nv + v] / mx : 0.0;
     }
 }
@@ -291,13 +295,21 @@ void orc_band_for_spacing(double d_min, double d_max, double R, int m, int32_t* 
 {
     const double dR = R / (double)((1 << (m - 1)) - 1);
     const double W = 2.0 * (R + dR);
-    *k_lo = (int32_t)(ORC_MUTATION == 16 ? floor(W / d_max) : ceil(W / d_max));
-    *k_hi = (int32_t)(ORC_MUTATION == 16 ? ceil(W / d_min) : floor(W / d_min));
+    *k_lo = (int32_t)MUT(16, floor(W / d_max), ceil(W / d_max));
+    *k_hi = (int32_t)MUT(16, ceil(W / d_min), floor(W / d_min));
 }
 
 /* ------------------------------------------------------------------------ */
 /* Rotations (FP64)                                                          */
 /* ------------------------------------------------------------------------ */
+
+static void orc_transpose3(double* M)
+{
+    double t;
+    t = M[1]; M[1] = M[3]; M[3] = t;
+    t = M[2]; M[2] = M[6]; M[6] = t;
+    t = M[5]; M[5] = M[7]; M[7] = t;
+}
 
 /* Rotation matrix of a unit quaternion q = (w, x, y, z); maps crystal to lab.
  * No fused multiply-add, fixed evaluation order. */
@@ -310,12 +322,7 @@ void orc_quat_to_matrix(const double* q, double* M)
     M[0] = 1.0 - 2.0 * (yy + zz); M[1] = 2.0 * (xy - wz);       M[2] = 2.0 * (xz + wy);
     M[3] = 2.0 * (xy + wz);       M[4] = 1.0 - 2.0 * (xx + zz); M[5] = 2.0 * (yz - wx);
     M[6] = 2.0 * (xz - wy);       M[7] = 2.0 * (yz + wx);       M[8] = 1.0 - 2.0 * (xx + yy);
-    if (ORC_MUTATION == 14) {
-        double t;
-        t = M[1]; M[1] = M[3]; M[3] = t;
-        t = M[2]; M[2] = M[6]; M[6] = t;
-        t = M[5]; M[5] = M[7]; M[7] = t;
-    }
+    if (MUT(14, 1, 0)) orc_transpose3(M);
 }
 
 static void orc_quat_mul(const double* a, const double* b, double* o)
@@ -359,7 +366,7 @@ double orc_disorientation_deg(const double* q1, const double* q2)
     double d[4];
     orc_quat_mul(inv, q2, d);
     double best = 0.0;
-    for (int s = 0; s < 24 - (ORC_MUTATION == 12); ++s) {
+    for (int s = 0; s < 24 - MUT(12, 1, 0); ++s) {
         double e[4];
         orc_quat_mul(d, sym[s], e);
         double w = fabs(e[0]) / sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + e[3] * e[3]);
@@ -382,7 +389,7 @@ static int orc_vi_cmp(const void* a, const void* b)
     const orc_vi* y = (const orc_vi*)b;
     if (x->v > y->v) return -1;
     if (x->v < y->v) return 1;
-    return ORC_MUTATION == 10 ? (x->i < y->i) - (x->i > y->i) : (x->i > y->i) - (x->i < y->i);
+    return MUT(10, (x->i < y->i) - (x->i > y->i), (x->i > y->i) - (x->i < y->i));
 }
 
 void orc_top_nodes(const float* sig, int64_t nv, int n_hat, int32_t* out)
@@ -401,7 +408,7 @@ void orc_rotate_node(const double* q, const float* nrm, float* r)
     double M[9];
     orc_quat_to_matrix(q, M);
     for (int i = 0; i < 3; ++i) {
-        const int st = ORC_MUTATION == 20 ? 3 : 1, rs = ORC_MUTATION == 20 ? 1 : 3;
+        const int st = MUT(20, 3, 1), rs = MUT(20, 1, 3);
         double a = M[rs * i + 0 * st] * (double)nrm[0];
         double b = M[rs * i + 1 * st] * (double)nrm[1];
         double c = M[rs * i + 2 * st] * (double)nrm[2];
@@ -414,10 +421,10 @@ void orc_rotate_node(const double* q, const float* nrm, float* r)
 int32_t orc_nearest_node(const float* u, int64_t nv, const float* r)
 {
     int32_t best = 0;
-    float bd = ORC_MUTATION == 11 ? INFINITY : -INFINITY;
+    float bd = MUT(11, INFINITY, -INFINITY);
     for (int64_t p = 0; p < nv; ++p) {
         float d = orc_project_f32(u + 3 * p, r);
-        if (ORC_MUTATION == 11 ? d < bd : d > bd) { bd = d; best = (int32_t)p; }
+        if (MUT(11, d < bd, d > bd)) { bd = d; best = (int32_t)p; }
     }
     return best;
 }
@@ -455,7 +462,7 @@ void orc_match(const float* S_msr, int64_t nroi, int64_t nv, const float* S_ref,
             double acc = 0.0;
             for (int k = 0; k < n_hat; ++k) {
                 double d = (double)s[lut[g * n_hat + k]] - (double)S_ref[top[k]];
-                acc += ORC_MUTATION == 5 ? fabs(d) : d * d;
+                acc += MUT(5, fabs(d), d * d);
             }
             if (scores) scores[r * ng + g] = acc;
             if (acc < bs) { bs = acc; bg = (int32_t)g; }
@@ -501,7 +508,7 @@ int orc_bilinear(const float* img, const double* c, double* val, double* grad, i
     int j0 = (int)floor(fj);
     double ti = fi - (double)i0;
     double tj = fj - (double)j0;
-    if (ORC_MUTATION == 15) tj = 1.0 - tj;
+    tj = MUT(15, 1.0 - tj, tj);
     j0 %= ORC_IMG_NB;
     int j1 = (j0 + 1) % ORC_IMG_NB;
     const double I00 = img[i0 * ORC_IMG_NB + j0], I01 = img[i0 * ORC_IMG_NB + j1];
@@ -550,11 +557,10 @@ void orc_refine_eval(const float* img, const float* S_msr, const float* u, int64
         a[1] = (M[3] * gc[0] + M[4] * gc[1]) + M[5] * gc[2];
         a[2] = (M[6] * gc[0] + M[7] * gc[1]) + M[8] * gc[2];
         double J[3];
-        J[0] = -(a[1] * uz - a[2] * uy);
-        J[1] = -(a[2] * ux - a[0] * uz);
-        J[2] = -(a[0] * uy - a[1] * ux);
-        if (ORC_MUTATION == 9)
-            for (int i = 0; i < 3; ++i) J[i] = -J[i];
+        const double sj = MUT(9, 1.0, -1.0);   /* times -1.0 is an exact negation */
+        J[0] = sj * (a[1] * uz - a[2] * uy);
+        J[1] = sj * (a[2] * ux - a[0] * uz);
+        J[2] = sj * (a[0] * uy - a[1] * ux);
         L += wv * r * r;
         for (int i = 0; i < 3; ++i) {
             g[i] += wv * 2.0 * r * J[i];
@@ -605,7 +611,7 @@ void orc_refine(const float* img, const float* S_msr, const float* u, int64_t nv
         const double lam = 1e-6 * (H[0] + H[4] + H[8]);
         H[0] += lam; H[4] += lam; H[8] += lam;
         double d[3];
-        const double sg = ORC_MUTATION == 18 ? 1.0 : -1.0;
+        const double sg = MUT(18, 1.0, -1.0);
         double nb[3] = {sg * b[0], sg * b[1], sg * b[2]};
         orc_solve3(H, nb, d);
         double e[4], qn[4];
@@ -650,14 +656,14 @@ int orc_openmp_threads(void)
 /* ------------------------------------------------------------------------ */
 void orc_fsp(const float* xc, int64_t nw, int L, double kmax, const int64_t* pts, int64_t npts, double* out)
 {
-    const double dk = 2.0 * kmax / (double)(ORC_MUTATION == 17 ? L : L - 1);
+    const double dk = 2.0 * kmax / (double)MUT(17, L, L - 1);
     for (int64_t p = 0; p < npts; ++p) {
         const int64_t f = pts[p];
         const int iz = (int)(f % L), iy = (int)((f / L) % L), ix = (int)(f / ((int64_t)L * L));
         const double kx = -kmax + ix * dk, ky = -kmax + iy * dk, kz = -kmax + iz * dk;
         double re = 0.0, im = 0.0;
         for (int64_t w = 0; w < nw; ++w) {
-            const double ka = ORC_MUTATION == 7 ? ky : kx, kb = ORC_MUTATION == 7 ? kx : ky;
+            const double ka = MUT(7, ky, kx), kb = MUT(7, kx, ky);
             const double ph = 2.0 * ORC_PI * (ka * (double)xc[3 * w] + kb * (double)xc[3 * w + 1] +
                                                kz * (double)xc[3 * w + 2]);
             re += cos(ph);
