@@ -65,25 +65,31 @@ def parse():
     return ap.parse_args()
 
 
-def tc_traffic_per_launch(n_roi):
-    """DRAM bytes per k_sig_tc launch from the committed ncu summary, scaled
-    to n_roi ROIs; None when the kernel sources changed since the capture."""
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "k_sig_tc_traffic.json")
+
+
+def kernel_sources_sha16(names):
+    """SHA-256 prefix of the named kernel sources (csrc/), concatenated."""
     import hashlib
-    import re
-    try:
-        with open(os.path.join(ROOT, "profiles", "k_sig_tc_bcc1024.md")) as fh:
-            m = re.search(r"traffic_bytes_per_launch_(\d+): ([0-9.e+]+) \(sources ([0-9a-f]+)\)", fh.read())
-    except OSError:
-        return None
-    if not m:
-        return None
     h = hashlib.sha256()
-    for f in ("signature_tc.cu", "common.cuh", "tcgen05.cuh"):
+    for f in names:
         with open(os.path.join(ROOT, "paper_2009_00735_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest()[:16] != m.group(3):
+    return h.hexdigest()[:16]
+
+
+def tc_traffic_per_launch(n_roi):
+    """DRAM bytes per k_sig_tc launch from the committed ncu figure
+    (profiles/k_sig_tc_traffic.json), scaled to n_roi ROIs; None when the
+    kernel sources changed since the capture."""
+    try:
+        with open(TRAFFIC_JSON) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
         return None
-    return float(m.group(2)) * n_roi / int(m.group(1))
+    if kernel_sources_sha16(t["sources"]) != t["sources_sha256_16"]:
+        return None
+    return float(t["dram_bytes_per_launch_captured"]) * n_roi / int(t["captured_rois"])
 
 
 def measured_peaks():
@@ -496,8 +502,8 @@ def run_gb300(args):
     roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / ALU_PEAK_TFLOPS,
             "traffic": tc_traffic_per_launch(nroi) if headline == "tc" else None,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1024-ROI launch scaled by "
-                              "ROIs (profiles/k_sig_tc_bcc1024.md); null once the kernel sources change",
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller launch scaled by "
+                              "ROIs (profiles/k_sig_tc_traffic.json); null once the kernel sources change",
             "kernel": "k_sig_plain" if headline == "plain" else "k_sig_tc",
             "kernel_ms": sig_ms,
             "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (nominal unit counts and max clock)",

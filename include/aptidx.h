@@ -136,6 +136,19 @@ int aptidx_set_binning(aptidx_ctx* ctx, int m, int32_t k_lo, int32_t k_hi, int f
 int aptidx_set_rois(aptidx_ctx* ctx, const double* centres, const double* radii, int64_t nroi,
                     const int32_t* band_lo, const int32_t* band_hi, uint32_t type_mask, int mem);
 
+/* Band of frequency bins holding the plane spacings [d_min, d_max] (nm) for a
+ * ROI of radius R at 2^m bins (Fig. 2 caption: the sampling frequency is
+ * f_s = 2^m / (2 (R + dR)) with dR = R / (2^(m-1) - 1), so frequency bin k
+ * has the period W / k with W = 2 (R + dR); the supplement probes the
+ * amplitude spectrum over the bin interval of a spacing interval):
+ *   k_lo = ceil(W / d_max),  k_hi = floor(W / d_min)   (FP64).
+ * Needs no context.  *k_lo and *k_hi (host) are written whenever the
+ * arguments are valid.  Errors: INVALID_ARG (NULL outputs, 0 < d_min <=
+ * d_max violated or not finite, R outside [1e-6, 1e6], m outside
+ * [APTIDX_MIN_M, APTIDX_MAX_M], or a band that is empty or leaves
+ * [0, 2^(m-1)], which aptidx_set_binning would refuse). */
+int aptidx_band_for_spacing(double d_min, double d_max, double R, int m, int32_t* k_lo, int32_t* k_hi);
+
 /* ---- the hot path -------------------------------------------------------- */
 
 /* Signatures of every ROI: gather and centre the ROI atoms (FP64
@@ -339,14 +352,16 @@ int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, 
  *   xc4     device, 16-byte aligned: centred atom coordinates as rows of four
  *           floats (x, y, z, unused); ROI r owns rows [off[r], off[r+1])
  *   off     device, nroi + 1 int64 row offsets
- *   radii   device, nroi FP64 ROI radii (> 0)
+ *   radii   device, nroi FP64 ROI radii in [1e-6, 1e6] nm
  *   u       device, nv x 3 FP32 unit directions (|u| within 1e-5 of 1)
  *   m, k_lo, k_hi: 2^m bins and the signature band, as in aptidx_set_binning
  *   S       device output, nroi x nv FP32
  *   status  device int or NULL: the kernels OR APTIDX_STATUS_* bits into it
- *           (a ROI above APTIDX_MAX_ATOMS_PER_ROI atoms, whose row of S is
- *           then zero; a direction that is not a unit vector; a bounded wait
- *           that ran out); the caller clears it
+ *           (OVERFLOW: a ROI above APTIDX_MAX_ATOMS_PER_ROI atoms; INVALID: a
+ *           radius outside [1e-6, 1e6] or NaN, or a direction that is not a
+ *           unit vector; TIMEOUT: a bounded wait that ran out).  A ROI flagged
+ *           OVERFLOW or for its radius gets a zero row of S.  The caller
+ *           clears the word.
  *   cuda_stream  the stream to queue on (NULL: the legacy default stream)
  *
  * Work is queued on the stream and the call returns without waiting.  It
@@ -359,8 +374,11 @@ int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, 
  * shares the scratch array, which keeps the last call's contents: calls
  * whose work overlaps on the GPU (other streams, other threads) race, so
  * order them on one stream.  The first call on a device looks up the
- * array's device address (once per device, with that device current); make
- * that first call before any stream capture.
+ * array's device address (once per device, with that device current) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture.  The kept address does not survive cudaDeviceReset: after
+ * a reset of a device, this call must not be used on it again in the same
+ * process.
  * Returns APTIDX_OK, APTIDX_E_INVALID_ARG or APTIDX_E_CUDA. */
 #define APTIDX_NOALLOC_MAX_ROIS 65536
 #define APTIDX_NOALLOC_MAX_DIRS 65536

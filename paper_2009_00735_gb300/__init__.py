@@ -23,7 +23,7 @@ __all__ = [
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
     "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_compute_fsp", "aptidx_refine_loss", "aptidx_refine",
-    "band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
+    "band_for_spacing", "aptidx_band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
     "APTIDX_NORMALISE_MAX", "APTIDX_AUTOTUNE", "APTIDX_GRAPH", "aptidx_get_tuning",
@@ -63,6 +63,7 @@ _i64 = C.c_int64
 _i32 = C.c_int32
 _SIGS = {
     "aptidx_version": (C.c_int, []),
+    "aptidx_band_for_spacing": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, _vp, _vp]),
     "aptidx_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
     "aptidx_destroy": (C.c_int, [_vp]),
     "aptidx_last_error": (C.c_char_p, [_vp]),
@@ -444,24 +445,44 @@ def aptidx_get_profile(ctx):
 
 
 def aptidx_signatures_noalloc(xc4, off, radii, u, m: int, k_lo: int, k_hi: int, S, status=None, stream=None):
-    """The no-allocation call: every array is a CUDA tensor the caller owns
-    (xc4 float32 [N, 4], off int64 [nroi + 1], radii float64 [nroi], u float32
-    [nv, 3], S float32 [nroi, nv], status int32 [1] or None).  Queued on
-    `stream` (default: torch's current stream); returns without waiting."""
+    """The no-allocation call: every array is a contiguous CUDA tensor the
+    caller owns, all on one device -- xc4 float32 [N, 4], off int64
+    [nroi + 1], radii float64 [nroi], u float32 [nv, 3], S float32
+    [nroi, nv], status int32 [>= 1] or None.  Queued on `stream` (default:
+    torch's current stream of S's device); returns without waiting."""
     torch = _torch()
-    for t in (xc4, off, radii, u, S) + ((status,) if status is not None else ()):
+    named = [("xc4", xc4, torch.float32), ("off", off, torch.int64), ("radii", radii, torch.float64),
+             ("u", u, torch.float32), ("S", S, torch.float32)]
+    if status is not None:
+        named.append(("status", status, torch.int32))
+    for name, t, dt in named:
         if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
-            raise ValueError("aptidx_signatures_noalloc takes contiguous CUDA tensors")
-    if stream is None:
-        stream = torch.cuda.current_stream(S.device).cuda_stream
-    elif hasattr(stream, "cuda_stream"):
-        stream = stream.cuda_stream
+            raise ValueError(f"aptidx_signatures_noalloc: {name} must be a contiguous CUDA tensor")
+        if t.dtype != dt:
+            raise TypeError(f"aptidx_signatures_noalloc: {name} must be {dt}, got {t.dtype}")
+        if t.device != S.device:
+            raise ValueError(f"aptidx_signatures_noalloc: {name} is on {t.device}, S on {S.device}")
     nroi = radii.numel()
-    nv = u.numel() // 3
-    rc = load().aptidx_signatures_noalloc(xc4.data_ptr(), off.data_ptr(), radii.data_ptr(), nroi, u.data_ptr(), nv,
-                                          m, k_lo, k_hi, S.data_ptr(),
-                                          status.data_ptr() if status is not None else None,
-                                          _vp(int(stream)) if stream else None)
+    if xc4.dim() != 2 or xc4.shape[1] != 4:
+        raise ValueError("aptidx_signatures_noalloc: xc4 must be [N, 4]")
+    if off.numel() != nroi + 1:
+        raise ValueError("aptidx_signatures_noalloc: off must hold nroi + 1 offsets")
+    if u.dim() != 2 or u.shape[1] != 3:
+        raise ValueError("aptidx_signatures_noalloc: u must be [nv, 3]")
+    nv = u.shape[0]
+    if S.numel() < nroi * nv:
+        raise ValueError("aptidx_signatures_noalloc: S must hold nroi x nv values")
+    if status is not None and status.numel() < 1:
+        raise ValueError("aptidx_signatures_noalloc: status must hold one int32")
+    with torch.cuda.device(S.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(S.device).cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        rc = load().aptidx_signatures_noalloc(xc4.data_ptr(), off.data_ptr(), radii.data_ptr(), nroi, u.data_ptr(),
+                                              nv, m, k_lo, k_hi, S.data_ptr(),
+                                              status.data_ptr() if status is not None else None,
+                                              _vp(int(stream)) if stream else None)
     if rc != APTIDX_OK:
         raise AptidxError(rc, "aptidx_signatures_noalloc: invalid sizes (limits in include/aptidx.h) or CUDA error")
 
@@ -474,18 +495,18 @@ def tc_available(device: int = 0) -> bool:
         ctx.close()
 
 
-# ---------------------------------------------------------------------------
-# conveniences (host-side parameter arithmetic only)
-# ---------------------------------------------------------------------------
+def aptidx_band_for_spacing(d_min: float, d_max: float, R: float, m: int):
+    """Frequency-bin band (k_lo, k_hi) holding plane spacings d_min..d_max
+    (nm) for a ROI of radius R at 2^m bins (computed by the library)."""
+    lo = np.zeros(1, np.int32)
+    hi = np.zeros(1, np.int32)
+    rc = load().aptidx_band_for_spacing(float(d_min), float(d_max), float(R), int(m), lo.ctypes.data, hi.ctypes.data)
+    if rc != APTIDX_OK:
+        raise AptidxError(rc, f"aptidx_band_for_spacing({d_min}, {d_max}, {R}, {m}): invalid arguments or band")
+    return int(lo[0]), int(hi[0])
 
-def band_for_spacing(d_min: float, d_max: float, R: float, m: int):
-    """Frequency-bin band [k_lo, k_hi] holding plane spacings d_min..d_max:
-    bin k has period W / k with W = 2 (R + dR), dR = R / (2^(m-1) - 1)
-    (Fig. 2 caption)."""
-    import math
-    dR = R / ((1 << (m - 1)) - 1)
-    W = 2.0 * (R + dR)
-    return int(math.ceil(W / d_max)), int(math.floor(W / d_min))
+
+band_for_spacing = aptidx_band_for_spacing
 
 
 class Context:

@@ -358,6 +358,21 @@ extern "C" {
 
 int aptidx_version(void) { return 100; }
 
+int aptidx_band_for_spacing(double d_min, double d_max, double R, int m, int32_t* k_lo, int32_t* k_hi) {
+    if (!k_lo || !k_hi) return APTIDX_E_INVALID_ARG;
+    if (!(d_min > 0.0 && d_min <= d_max && isfinite(d_max))) return APTIDX_E_INVALID_ARG;
+    if (!(R >= 1e-6 && R <= 1e6) || m < APTIDX_MIN_M || m > APTIDX_MAX_M) return APTIDX_E_INVALID_ARG;
+    // W = 2^m dR = 2 (R + dR): the histogram span, whose k-th frequency bin has period W / k
+    const double dR = R / (double)((1 << (m - 1)) - 1);
+    const double W = 2.0 * (R + dR);
+    const double lo = ceil(W / d_max), hi = floor(W / d_min);
+    if (!(lo >= -2147483648.0 && hi <= 2147483647.0)) return APTIDX_E_INVALID_ARG;
+    *k_lo = (int32_t)lo;
+    *k_hi = (int32_t)hi;
+    if (*k_lo < 0 || *k_hi < *k_lo || *k_hi > (1 << (m - 1))) return APTIDX_E_INVALID_ARG;
+    return APTIDX_OK;
+}
+
 int aptidx_create(aptidx_ctx** out, int device, void* cuda_stream) {
     if (!out) return APTIDX_E_INVALID_ARG;
     *out = nullptr;

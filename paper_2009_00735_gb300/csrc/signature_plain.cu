@@ -370,7 +370,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[APTIDX_NOALLOC_
 
 // Per-call set-up: counts, scales, bands and identity order per ROI; padded
 // float4 directions; the twiddle table.  Flags ROIs above 65535 atoms
-// (overflow) and directions that are not unit vectors (invalid input).
+// (overflow), radii outside [1e-6, 1e6] nm and directions that are not unit
+// vectors (invalid input); a flagged ROI gets zero atoms, so its row of S is
+// zero.
 __global__ void k_noalloc_setup(unsigned char* scr, const int64_t* __restrict__ off, const double* __restrict__ radii,
                                 int64_t nroi, const float* __restrict__ u, int32_t nv, int32_t nv_pad, int m,
                                 int32_t k_lo, int32_t k_hi, int* status) {
@@ -389,8 +391,13 @@ __global__ void k_noalloc_setup(unsigned char* scr, const int64_t* __restrict__ 
             atomicOr(status, kStatusOverflow);
             n = 0;
         }
+        const double R = radii[r];
+        if (!(R >= 1e-6 && R <= 1e6)) {   // also false for NaN
+            atomicOr(status, kStatusInvalid);
+            n = 0;
+        }
         nw[r] = (int32_t)n;
-        scale[r] = __double2float_rn((double)(half - 1) / radii[r]);
+        scale[r] = n > 0 ? __double2float_rn((double)(half - 1) / R) : 0.f;
         band[2 * r] = k_lo;
         band[2 * r + 1] = k_hi;
         order[r] = (int32_t)r;

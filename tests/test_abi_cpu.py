@@ -58,10 +58,17 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert rc == apt.APTIDX_E_INVALID_ARG and not h.value
 
 
-def test_band_for_spacing_matches_oracle():
+def test_band_for_spacing_matches_oracle(lib):
+    """aptidx_band_for_spacing (host code of the library, no GPU) against the
+    oracle's band arithmetic, and its argument checks."""
     import oracle
     import synth
     for R, m in [(1.0, 8), (2.0, 10), (1.37, 9)]:
         for d in [0.2025, 0.2029, 0.25]:
             lo, hi = synth.band_spacing(d)
-            assert apt.band_for_spacing(lo, hi, R, m) == oracle.band_for_spacing(lo, hi, R, m)
+            assert apt.aptidx_band_for_spacing(lo, hi, R, m) == oracle.band_for_spacing(lo, hi, R, m)
+    assert apt.band_for_spacing is apt.aptidx_band_for_spacing
+    for bad in [(0.0, 0.2, 2.0, 10), (0.3, 0.2, 2.0, 10), (0.2, 0.3, 0.0, 10), (0.2, 0.3, 2.0, 7),
+                (0.2, 0.3, 2.0, 11), (1e-4, 2e-4, 2.0, 8)]:   # the last band exceeds 2^(m-1)
+        with pytest.raises(apt.AptidxError):
+            apt.aptidx_band_for_spacing(*bad)

@@ -50,13 +50,23 @@ def test_clock_sampler_reports_thermal_slowdown(tmp_path, monkeypatch):
     assert c["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
 
 
-def test_committed_traffic_matches_kernel_sources():
-    """profiles/k_sig_tc_bcc1024.md carries the DRAM traffic of the committed
-    tensor-core kernel (its source fingerprint matches), scaled by ROIs."""
+def test_committed_traffic_figure():
+    """profiles/k_sig_tc_traffic.json holds the ncu DRAM traffic of a
+    k_sig_tc launch with the fingerprint of the sources it was taken on;
+    bench.py scales it by ROIs while the fingerprint matches and reports null
+    otherwise."""
+    with open(bench.TRAFFIC_JSON) as fh:
+        t = json.load(fh)
+    assert t["kernel"] == "k_sig_tc" and t["captured_rois"] > 0 and t["dram_bytes_per_launch_captured"] > 0
+    assert len(t["sources_sha256_16"]) == 16
+    assert os.path.exists(os.path.join(ROOT, "profiles", t["summary"]))
     t8 = bench.tc_traffic_per_launch(8192)
     t1 = bench.tc_traffic_per_launch(1024)
-    assert t8 is not None and t8 > 0
-    assert np.isclose(t8, 8 * t1)
+    if bench.kernel_sources_sha16(t["sources"]) == t["sources_sha256_16"]:
+        assert t8 is not None and np.isclose(t8, 8 * t1)
+        assert np.isclose(t1 * t["scaled_rois"] / 1024, t["dram_bytes_per_launch_scaled"], rtol=1e-3)
+    else:
+        assert t8 is None and t1 is None
 
 
 def test_reference_arm_json_line():
