@@ -75,11 +75,12 @@ typedef struct aptidx_ctx aptidx_ctx;
 #define APTIDX_NORMALISE_MAX   1u  /* divide each ROI's signature by its largest value */
 #define APTIDX_AUTOTUNE        2u  /* pick the launch configuration by timing candidates (once per shape) */
 #define APTIDX_GRAPH           4u  /* capture the call's launches in a CUDA graph once, replay afterwards */
+#define APTIDX_DIRECT          8u  /* project every direction, also those whose antipode is in the set */
 
 /* limits */
-#define APTIDX_MAX_ATOMS_PER_ROI 65535   /* u16 histogram counts */
+#define APTIDX_MAX_ATOMS_PER_ROI 16777215   /* selected atoms per ROI (2^24 - 1) */
 #define APTIDX_MIN_M 8
-#define APTIDX_MAX_M 10
+#define APTIDX_MAX_M 12                     /* Section 2.2: m in [8, 12] */
 
 /* ---- context ----------------------------------------------------------- */
 
@@ -116,10 +117,18 @@ int aptidx_load_positions(aptidx_ctx* ctx, const float* xyz, int64_t n, const ui
 
 /* Projection directions (Section 2.2: outer unit normals of the nodes of a
  * geodesic sphere, N_v = 40962 in the paper).  u: nv x 3 FP32 unit vectors
- * (|u| within 1e-5 of 1).  Errors: INVALID_ARG (nv <= 0, non-unit), OOM, CUDA. */
+ * (|u| within 1e-5 of 1).  Directions whose exact negation is also in the set
+ * (every node of a geodesic sphere has its antipode) are paired: the
+ * signature paths project one direction of a pair and give the other the
+ * same value and frequency bin, which is exact (the histogram along -u is the
+ * mirror image of the one along u, with the same amplitude spectrum, unless
+ * an atom's bin product is an exact integer; the kernels detect that case
+ * and then project -u as well).  Errors: INVALID_ARG (nv <= 0, non-unit),
+ * OOM, CUDA. */
 int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem);
 
-/* Histogram resolution 2^m bins (Eq. 1; APTIDX_MIN_M <= m <= APTIDX_MAX_M)
+/* Histogram resolution 2^m bins (Eq. 1; APTIDX_MIN_M <= m <= APTIDX_MAX_M;
+ * above 2^10 bins the kernels build each histogram in chunks of 1024 bins)
  * and the default signature band of frequency bins [k_lo, k_hi]
  * (supplement, Al bicrystal: the largest amplitude over a fixed band of bins),
  * 0 <= k_lo <= k_hi <= 2^(m-1).  flags: reserved, 0. */
@@ -161,7 +170,8 @@ int aptidx_band_for_spacing(double d_min, double d_max, double R, int m, int32_t
  * with the environment variable APTIDX_TUNE_CACHE naming a file, choices
  * persist across processes); APTIDX_GRAPH (the launches of the call are
  * captured in a CUDA graph on first use for these output pointers and sizes
- * and replayed on later calls; input changes discard the graphs).
+ * and replayed on later calls; input changes discard the graphs);
+ * APTIDX_DIRECT (no antipodal pairing: every direction is projected).
  * Outputs (in `mem`; NULL to skip): S nroi x nv FP32; argk nroi x nv u16 (the
  * lowest frequency bin attaining the maximum; not written when normalising
  * is the only change); n_atoms nroi int32 (N_w per ROI).

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -257,8 +258,9 @@ static std::string tune_key(Ctx* c, int path) {
     const int abin = mean > 1.0 ? (int)lround(2.0 * log2(mean)) : 0;
     const int vbin = (int)lround(2.0 * log2((double)std::max(c->nv, 1)));
     const int groups = (c->band_max - c->band_min) / 4 + 1;
-    snprintf(buf, sizeof(buf), "%s/%d|p%d|m%d|g%d|a%d|v%d", prop.name, prop.multiProcessorCount, path, c->m, groups,
-             abin, vbin);
+    const int pairs = c->use_pairs && c->npairs > 0 ? 1 : 0;
+    snprintf(buf, sizeof(buf), "%s/%d|p%d|m%d|g%d|a%d|v%d|s%d", prop.name, prop.multiProcessorCount, path, c->m,
+             groups, abin, vbin, pairs);
     for (char* q = buf; *q; ++q)
         if (*q == ' ') *q = '_';
     return buf;
@@ -416,6 +418,8 @@ int aptidx_destroy(aptidx_ctx* ctx) {
     free_ptr(c->d_types);
     free_ptr(c->d_dirs);
     free_ptr(c->d_dirs_sorted);
+    free_ptr(c->d_slot_dirs);
+    free_ptr(c->d_slot_idx);
     free_ptr(c->d_gn_scratch);
     c->gn_scratch_bytes = 0;
     free_ptr(c->d_match_scratch);
@@ -548,16 +552,73 @@ int aptidx_set_directions(aptidx_ctx* ctx, const float* u, int32_t nv, int mem) 
         memcpy(&w, &bits, sizeof(w));
         ds[k] = make_float4(d4[v].x, d4[v].y, d4[v].z, w);
     }
+    // antipodal pairs: u_p = -u_v component by component (as values: a zero
+    // of either sign matches), each direction in at most one pair; the lower
+    // index is projected and writes its partner
+    std::vector<std::tuple<uint32_t, uint32_t, uint32_t, int32_t>> keys((size_t)nv);
+    auto zbits = [](float f) {
+        const float g = f + 0.0f;   // -0 becomes +0
+        uint32_t b;
+        memcpy(&b, &g, sizeof(b));
+        return b;
+    };
+    for (int32_t v = 0; v < nv; ++v) keys[v] = std::make_tuple(zbits(d4[v].x), zbits(d4[v].y), zbits(d4[v].z), v);
+    std::sort(keys.begin(), keys.end());
+    std::vector<int32_t> partner((size_t)nv, -1);
+    int32_t npairs = 0;
+    for (int32_t v = 0; v < nv; ++v) {
+        if (partner[v] >= 0) continue;
+        const auto want = std::make_tuple(zbits(-d4[v].x), zbits(-d4[v].y), zbits(-d4[v].z), (int32_t)-1);
+        for (auto it = std::upper_bound(keys.begin(), keys.end(), want);
+             it != keys.end() && std::get<0>(*it) == std::get<0>(want) && std::get<1>(*it) == std::get<1>(want) &&
+             std::get<2>(*it) == std::get<2>(want);
+             ++it) {
+            const int32_t q = std::get<3>(*it);
+            if (q != v && partner[q] < 0) {
+                partner[v] = q;
+                partner[q] = v;
+                ++npairs;
+                break;
+            }
+        }
+    }
+    std::vector<float4> sd;
+    std::vector<int2> si;
+    if (npairs > 0) {
+        for (int32_t v = 0; v < nv; ++v) {
+            if (partner[v] >= 0 && partner[v] < v) continue;   // written by its lower-index partner
+            sd.push_back(d4[v]);
+            si.push_back(make_int2(v, partner[v]));
+        }
+        while (sd.size() % kTileDirs) {
+            sd.push_back(make_float4(1.f, 0.f, 0.f, 0.f));
+            si.push_back(make_int2(-1, -1));
+        }
+    }
     free_ptr(c->d_dirs);
     free_ptr(c->d_dirs_sorted);
+    free_ptr(c->d_slot_dirs);
+    free_ptr(c->d_slot_idx);
     clear_graphs(c);
     c->nv = c->nv_pad = 0;
+    c->nslot = c->nslot_pad = c->npairs = 0;
     if ((rc = dev_alloc(c, (void**)&c->d_dirs, (size_t)nv_pad * sizeof(float4)))) return rc;
     if ((rc = dev_alloc(c, (void**)&c->d_dirs_sorted, (size_t)nv * sizeof(float4)))) return rc;
     APTIDX_CUDA(c, cudaMemcpyAsync(c->d_dirs, d4.data(), (size_t)nv_pad * sizeof(float4), cudaMemcpyHostToDevice,
                                    c->stream));
     APTIDX_CUDA(c, cudaMemcpyAsync(c->d_dirs_sorted, ds.data(), (size_t)nv * sizeof(float4), cudaMemcpyHostToDevice,
                                    c->stream));
+    if (npairs > 0) {
+        if ((rc = dev_alloc(c, (void**)&c->d_slot_dirs, sd.size() * sizeof(float4)))) return rc;
+        if ((rc = dev_alloc(c, (void**)&c->d_slot_idx, si.size() * sizeof(int2)))) return rc;
+        APTIDX_CUDA(c, cudaMemcpyAsync(c->d_slot_dirs, sd.data(), sd.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                                       c->stream));
+        APTIDX_CUDA(c, cudaMemcpyAsync(c->d_slot_idx, si.data(), si.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                       c->stream));
+        c->nslot = nv - npairs;
+        c->nslot_pad = (int32_t)sd.size();
+        c->npairs = npairs;
+    }
     APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
     c->nv = nv;
     c->nv_pad = nv_pad;
@@ -696,8 +757,9 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
     if (c->nroi <= 0) return set_error(c, APTIDX_E_STATE, "compute_signatures: set ROIs first");
     if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
         return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
-    if (flags & ~(APTIDX_NORMALISE_MAX | APTIDX_AUTOTUNE | APTIDX_GRAPH))
+    if (flags & ~(APTIDX_NORMALISE_MAX | APTIDX_AUTOTUNE | APTIDX_GRAPH | APTIDX_DIRECT))
         return set_error(c, APTIDX_E_INVALID_ARG, "unknown flags 0x%x", flags);
+    c->use_pairs = !(flags & APTIDX_DIRECT);
     const int64_t nS = c->nroi * (int64_t)c->nv;
     float* dS = S;
     uint16_t* dA = argk;
@@ -718,7 +780,8 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
     if (flags & APTIDX_GRAPH) {
         // capture the sequence once per (arguments, configuration), replay after
         char kb[256];
-        snprintf(kb, sizeof(kb), "%d|%u|%p|%p|%lld|%d|%d|%d|%d", path, flags & APTIDX_NORMALISE_MAX, (void*)dS, (void*)dA,
+        snprintf(kb, sizeof(kb), "%d|%u|%p|%p|%lld|%d|%d|%d|%d", path, flags & (APTIDX_NORMALISE_MAX | APTIDX_DIRECT),
+                 (void*)dS, (void*)dA,
                  (long long)c->nroi, c->nv, c->m, c->tune_tpi[path == APTIDX_PATH_TC_FP16], c->tune_iss);
         auto it = c->graphs.find(kb);
         if (it == c->graphs.end()) {
@@ -754,6 +817,7 @@ int aptidx_compute_signatures(aptidx_ctx* ctx, int path, unsigned flags, float* 
     } else if ((rc = launch_sequence(c, path, flags, dS, dA))) {
         return rc;
     }
+    c->use_pairs = true;
     if (mem == APTIDX_MEM_HOST) {
         if (S) APTIDX_CUDA(c, cudaMemcpyAsync(S, dS, (size_t)nS * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         if (argk)
@@ -846,6 +910,11 @@ int aptidx_get_histograms(aptidx_ctx* ctx, int64_t roi, int path, uint16_t* h, i
     }
     rc = run_gather(c);
     cudaError_t e = cudaSuccess;
+    if (!rc) {
+        // the kernels add the counts of every (atom block, bin chunk) pass
+        e = cudaMemsetAsync(dh, 0, n * sizeof(uint16_t), c->stream);
+        if (e != cudaSuccess) rc = cuda_check(c, e, "zero histograms");
+    }
     if (!rc) {
         if (path == APTIDX_PATH_PLAIN_FP32) {
             e = launch_signatures_plain(c, row, nullptr, dh, roi, 0);
@@ -1154,6 +1223,7 @@ int aptidx_compute_signatures_multi(aptidx_ctx* ctx, int path, unsigned flags, i
     if (path != APTIDX_PATH_PLAIN_FP32 && path != APTIDX_PATH_TC_FP16)
         return set_error(c, APTIDX_E_INVALID_ARG, "unknown path %d", path);
     if (flags & ~APTIDX_NORMALISE_MAX) return set_error(c, APTIDX_E_INVALID_ARG, "unknown flags 0x%x", flags);
+    c->use_pairs = true;
     if (n_sig < 1 || n_sig > 64 || !type_mask || !k_lo || !k_hi || !S)
         return set_error(c, APTIDX_E_INVALID_ARG, "compute_signatures_multi: need 1 <= n_sig <= 64, masks, bands, S");
     const int half = 1 << (c->m - 1);

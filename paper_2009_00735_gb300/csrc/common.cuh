@@ -132,6 +132,11 @@ __device__ __forceinline__ uint64_t f2_fma_rd(uint64_t a, uint64_t b, uint64_t c
     asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ uint64_t f2_fma_ru(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rp.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 __device__ __forceinline__ uint64_t f2_dup(float v) {
     return ((uint64_t)__float_as_uint(v) << 32) | (uint64_t)__float_as_uint(v);
 }
@@ -220,6 +225,113 @@ __device__ __forceinline__ void hist_tile_pairs(uint32_t* H, const float4* A, in
         const float4 d0s = d0, d1s = d1;
         hist_add_atom<false>(hbase, A[cn - 1], d0s, d1s, scale, magic, 0);
     }
+}
+
+// -----------------------------------------------------------------------------
+// Histogram pass of the general tensor-core path: bin chunks, and the count of
+// atoms whose bin product is not an integer.
+//
+// Bin chunks (m > 10): the 2^m bins are split into chunks of 1024 bins (128 KB
+// of histogram words); the pass for chunk bc adds only atoms whose bin lies in
+// [1024 bc, 1024 bc + 1024), at row b - 1024 bc.  The bin fma's bit pattern is
+// 0x4B000000 + b, so the chunk of b is bits 10.. of the pattern.
+//
+// Antipodal directions: along -u the projection is exactly -s (round to
+// nearest is symmetric), so the bin of -u is 2^m - 1 - b(u) whenever the exact
+// product x = s * scale is not an integer, and 2^m - b(u) when it is.  With the
+// product rounded down (t_rd) and up (t_ru) onto the integer grid of
+// [2^23, 2^24), t_ru - t_rd is 1 for a non-integer x and 0 for an integer x; a
+// lane sums it over its atoms (kCount), so the histogram of -u is the mirror
+// image of the histogram of u exactly when that sum equals the lane's atom
+// count.
+// -----------------------------------------------------------------------------
+template <bool kCount, bool kChunked>
+__device__ __forceinline__ void hist_add_pair2(uint32_t hb, ulonglong2 xy, uint64_t zz, const PairDirs& q,
+                                               uint32_t bc, uint32_t cmask, uint32_t& c0, uint32_t& c1) {
+    const uint64_t s0 = f2_fma(zz, q.z0, f2_fma(xy.y, q.y0, f2_mul(xy.x, q.x0)));
+    const uint64_t s1 = f2_fma(zz, q.z1, f2_fma(xy.y, q.y1, f2_mul(xy.x, q.x1)));
+    const uint64_t t0 = f2_fma_rd(s0, q.sc, q.mg);
+    const uint64_t t1 = f2_fma_rd(s1, q.sc, q.mg);
+    if (kCount) {
+        const uint64_t u0 = f2_fma_ru(s0, q.sc, q.mg);
+        const uint64_t u1 = f2_fma_ru(s1, q.sc, q.mg);
+        c0 += ((uint32_t)u0 - (uint32_t)t0) + ((uint32_t)(u0 >> 32) - (uint32_t)(t0 >> 32));
+        c1 += ((uint32_t)u1 - (uint32_t)t1) + ((uint32_t)(u1 >> 32) - (uint32_t)(t1 >> 32));
+    }
+    // (t - 0x4B000000 - 1024 bc) * 128 + H + 4 lane, in wrapping 32-bit arithmetic
+    const uint32_t wa0 = (uint32_t)t0 * 128u + hb, wb0 = (uint32_t)(t0 >> 32) * 128u + hb;
+    const uint32_t wa1 = (uint32_t)t1 * 128u + hb, wb1 = (uint32_t)(t1 >> 32) * 128u + hb;
+    if (kChunked) {
+        if ((((uint32_t)t0 >> 10) & cmask) == bc) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wa0), "r"(1u) : "memory");
+        if ((((uint32_t)(t0 >> 32) >> 10) & cmask) == bc)
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wb0), "r"(1u) : "memory");
+        if ((((uint32_t)t1 >> 10) & cmask) == bc)
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wa1), "r"(0x10000u) : "memory");
+        if ((((uint32_t)(t1 >> 32) >> 10) & cmask) == bc)
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wb1), "r"(0x10000u) : "memory");
+    } else {
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wa0), "r"(1u) : "memory");
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wb0), "r"(1u) : "memory");
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wa1), "r"(0x10000u) : "memory");
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(wb1), "r"(0x10000u) : "memory");
+    }
+}
+
+template <bool kCount, bool kChunked>
+__device__ __forceinline__ void hist_add_one2(uint32_t hb, float4 a, float4 d0, float4 d1, float scale, float magic,
+                                              uint32_t bc, uint32_t cmask, uint32_t& c0, uint32_t& c1) {
+    const float s0 = project_f32(d0.x, d0.y, d0.z, a);
+    const float s1 = project_f32(d1.x, d1.y, d1.z, a);
+    const uint32_t t0 = __float_as_uint(__fmaf_rd(s0, scale, magic));
+    const uint32_t t1 = __float_as_uint(__fmaf_rd(s1, scale, magic));
+    if (kCount) {
+        c0 += __float_as_uint(__fmaf_ru(s0, scale, magic)) - t0;
+        c1 += __float_as_uint(__fmaf_ru(s1, scale, magic)) - t1;
+    }
+    if (!kChunked || ((t0 >> 10) & cmask) == bc)
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(t0 * 128u + hb), "r"(1u) : "memory");
+    if (!kChunked || ((t1 >> 10) & cmask) == bc)
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(t1 * 128u + hb), "r"(0x10000u) : "memory");
+}
+
+// Histograms of one 64-direction tile over `cn` atoms staged by pair_atoms, for
+// bin chunk bc (kChunked) or all bins; warp w takes pairs w, w + W, ...
+// Returns the number of atoms this warp handled; c0, c1 accumulate the lane's
+// non-integer counts of its two directions (kCount).
+template <int W, bool kCount, bool kChunked>
+__device__ __forceinline__ int hist_tile_pairs2(uint32_t* H, const float4* A, int cn, int warp, int lane, float4 d0,
+                                                float4 d1, float scale, float magic, uint32_t bc, uint32_t cmask,
+                                                uint32_t& c0, uint32_t& c1) {
+    const uint32_t hb = smem_u32(H) + 4u * (uint32_t)lane - 0x80000000u - (bc << 17);
+    const PairDirs q = pair_dirs(d0, d1, scale, magic);
+    const int np = cn >> 1;
+    int j = warp;
+    auto ld_xy = [&](int i) { return *reinterpret_cast<const ulonglong2*>(A + 2 * i); };
+    auto ld_z = [&](int i) { return *reinterpret_cast<const uint64_t*>(A + 2 * i + 1); };
+    if (j + W < np) {
+        ulonglong2 xa = ld_xy(j), xb = ld_xy(j + W);
+        uint64_t za = ld_z(j), zb = ld_z(j + W);
+        for (; j + 3 * W < np; j += 2 * W) {
+            const ulonglong2 nxa = ld_xy(j + 2 * W), nxb = ld_xy(j + 3 * W);
+            const uint64_t nza = ld_z(j + 2 * W), nzb = ld_z(j + 3 * W);
+            hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1);
+            hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1);
+            xa = nxa;
+            xb = nxb;
+            za = nza;
+            zb = nzb;
+        }
+        hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1);
+        hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1);
+        j += 2 * W;
+    }
+    for (; j < np; j += W) hist_add_pair2<kCount, kChunked>(hb, ld_xy(j), ld_z(j), q, bc, cmask, c0, c1);
+    int handled = warp < np ? 2 * ((np - warp + W - 1) / W) : 0;
+    if ((cn & 1) && warp == np % W) {
+        hist_add_one2<kCount, kChunked>(hb, A[cn - 1], d0, d1, scale, magic, bc, cmask, c0, c1);
+        handled += 1;
+    }
+    return handled;
 }
 
 // Debug export of a tile's histograms: h_out[v * 2^m + b] for v < nv.

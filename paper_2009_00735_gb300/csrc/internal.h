@@ -74,6 +74,13 @@ struct Ctx {
     // refinement walks this order so that neighbouring lanes sample
     // neighbouring pixels of the reference image
     float4* d_dirs_sorted = nullptr;
+    // antipodal pairs: one slot per pair (the lower index projected, its
+    // partner written from it) and per unpaired direction, padded to whole
+    // tiles; slot = (output direction, partner or -1).  Null without pairs.
+    float4* d_slot_dirs = nullptr;
+    int2* d_slot_idx = nullptr;
+    int32_t nslot = 0, nslot_pad = 0, npairs = 0;
+    bool use_pairs = true;           // cleared by APTIDX_DIRECT for one call
     float* d_gn_scratch = nullptr;   // one signature row per refinement CTA, in the order above
     size_t gn_scratch_bytes = 0;
     BandSet multi;                       // bands of the current pass (multi-signature calls)

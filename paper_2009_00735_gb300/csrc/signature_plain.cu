@@ -27,6 +27,41 @@ constexpr int kDirs = kTileDirs;        // 64 directions per tile
 constexpr int kWords = kDirs / 2;       // u32 words per bin
 constexpr int kKpw = 4;                 // frequencies per warp unit
 constexpr int kPartBytes = kWarps * kKpw * kDirs * 8;
+constexpr int kChunkBins = 1024;        // bins per histogram chunk (128 KB of words)
+constexpr int kBlockAtoms = 65535;      // atoms per block: every 16-bit count of a block is exact
+
+// Histograms of one tile for bin chunk bc over `cn` staged atoms (the
+// multi-pass path: 2^m > 1024 bins, or a ROI above kBlockAtoms atoms): the bin
+// is masked to m bits and only bins of [1024 bc, 1024 bc + 1024) are added,
+// at row b - 1024 bc.
+template <int W>
+__device__ __forceinline__ void hist_tile_chunk(uint32_t* H, const float4* A, int cn, int warp, int lane, float4 d0,
+                                                float4 d1, float scale, float magic, uint32_t nbm1, uint32_t bc) {
+    const uint32_t hb = smem_u32(H) + 4u * (uint32_t)lane;
+    for (int j = warp; j < cn; j += W) {
+        const float4 a = A[j];
+        const uint32_t b0 = __float_as_uint(__fmaf_rd(project_f32(d0.x, d0.y, d0.z, a), scale, magic)) & nbm1;
+        const uint32_t b1 = __float_as_uint(__fmaf_rd(project_f32(d1.x, d1.y, d1.z, a), scale, magic)) & nbm1;
+        if ((b0 >> 10) == bc)
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + ((b0 & 1023u) << 7)), "r"(1u) : "memory");
+        if ((b1 >> 10) == bc)
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hb + ((b1 & 1023u) << 7)), "r"(0x10000u) : "memory");
+    }
+}
+
+// Debug export of one pass: adds the counts of rows [0, nbc) to
+// h_out[v * 2^m + bc * nbc + row] (the caller zeroes h_out).
+__device__ __forceinline__ void hist_export_add_p(const uint32_t* H, int nbc, int NB, int bc, int tile, int nv,
+                                                  uint16_t* h_out, int tid, int nthreads) {
+    for (int i = tid; i < nbc * 32; i += nthreads) {
+        const int b = i >> 5, l = i & 31;
+        const uint32_t w = H[i];
+        const int64_t v0 = (int64_t)tile * 64 + 2 * l;
+        const int64_t col = (int64_t)bc * nbc + b;
+        if (v0 < nv) h_out[v0 * NB + col] = (uint16_t)(h_out[v0 * NB + col] + (w & 0xFFFFu));
+        if (v0 + 1 < nv) h_out[(v0 + 1) * NB + col] = (uint16_t)(h_out[(v0 + 1) * NB + col] + (w >> 16));
+    }
+}
 
 struct SigParams {
     const float4* atoms;
@@ -63,9 +98,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int NB = 1 << p.m;
     const int nbm1 = NB - 1;
+    const int NBc = NB < kChunkBins ? NB : kChunkBins;   // histogram rows held at once
+    const int nchunk = NB / NBc;
     uint32_t* H = reinterpret_cast<uint32_t*>(smem);
-    float2* TW = reinterpret_cast<float2*>(smem + (size_t)NB * kWords * 4);
-    float4* A = reinterpret_cast<float4*>(smem + (size_t)NB * kWords * 4 + (size_t)NB * 8);
+    float2* TW = reinterpret_cast<float2*>(smem + (size_t)NBc * kWords * 4);
+    float4* A = reinterpret_cast<float4*>(smem + (size_t)NBc * kWords * 4 + (size_t)NB * 8);
     float2* PART = reinterpret_cast<float2*>(A + p.atom_cap);
     uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(PART) + kPartBytes);
     int* flag = reinterpret_cast<int*>(bar + 1);
@@ -106,6 +143,115 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
         const bool one_chunk = nw <= p.atom_cap;
         if (one_chunk && !stage_atoms(A, p.atoms + abase, nw, bar, phase, p.status, flag)) return;
 
+        if (nchunk > 1 || nw > kBlockAtoms) {
+            // ---- multi-pass path: the histogram of a tile in passes over atom
+            // blocks of at most kBlockAtoms and bin chunks of 1024; each warp
+            // unit (4 frequencies x a span of the chunk's bins) accumulates its
+            // partial DFT in registers across the passes.  Bands of more than
+            // kWarps groups of frequencies run in rounds of kWarps groups.
+            const int K = khi - klo + 1;
+            const int G = (K + kKpw - 1) / kKpw;
+            const int nblk = (nw + kBlockAtoms - 1) / kBlockAtoms;
+            const int64_t out_base = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv;
+            for (int tile = t0; tile < t1; ++tile) {
+                const float4 d0 = p.dirs[(int64_t)tile * kDirs + 2 * lane];
+                const float4 d1 = p.dirs[(int64_t)tile * kDirs + 2 * lane + 1];
+                float best[kNB];
+                int bk[kNB];
+                if (tid < kDirs) band_init_t<kNB>(p.bands, klo, best, bk);
+                for (int g_lo = 0; g_lo < G; g_lo += kWarps) {
+                    const int Gr = min(kWarps, G - g_lo);
+                    int nsplit = 1;
+                    while (Gr * nsplit * 2 <= kWarps && nsplit * 2 <= NBc / 32) nsplit *= 2;
+                    const int span = NBc / nsplit;
+                    const bool unit = warp < Gr * nsplit;
+                    const int g = g_lo + warp / nsplit, sp = warp % nsplit;
+                    const int k0 = klo + g * kKpw;
+                    float re[kKpw][2], im[kKpw][2];
+#pragma unroll
+                    for (int q = 0; q < kKpw; ++q) re[q][0] = re[q][1] = im[q][0] = im[q][1] = 0.f;
+                    for (int blk = 0; blk < max(nblk, 1); ++blk) {
+                        const int b0 = blk * kBlockAtoms, bn = max(0, min(kBlockAtoms, nw - b0));
+                        for (int bc = 0; bc < nchunk; ++bc) {
+                            uint4* H4 = reinterpret_cast<uint4*>(H);
+                            for (int i = tid; i < NBc * kWords / 4; i += kThreads) H4[i] = make_uint4(0, 0, 0, 0);
+                            __syncthreads();
+                            for (int c0 = 0; c0 < bn; c0 += p.atom_cap) {
+                                const int cn = min(p.atom_cap, bn - c0);
+                                if (!one_chunk) {
+                                    if (!stage_atoms(A, p.atoms + abase + b0 + c0, cn, bar, phase, p.status, flag))
+                                        return;
+                                }
+                                hist_tile_chunk<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic, (uint32_t)nbm1,
+                                                        (uint32_t)bc);
+                                if (!one_chunk) __syncthreads();
+                            }
+                            __syncthreads();
+                            if (p.hist_out && g_lo == 0) {
+                                hist_export_add_p(H, NBc, NB, bc, tile, p.nv, p.hist_out, tid, kThreads);
+                                __syncthreads();
+                            }
+                            if (unit) {
+                                const int n0 = bc * NBc + sp * span;
+                                unsigned idx[kKpw];
+#pragma unroll
+                                for (int q = 0; q < kKpw; ++q)
+                                    idx[q] = (unsigned)(((int64_t)(k0 + q) * n0) & (int64_t)nbm1);
+                                for (int n = 0; n < span; ++n) {
+                                    const uint32_t w = H[(sp * span + n) * kWords + lane];
+                                    const float f0 = u23_to_float(w & 0xFFFFu), f1 = u23_to_float(w >> 16);
+#pragma unroll
+                                    for (int q = 0; q < kKpw; ++q) {
+                                        const float2 t = TW[idx[q]];
+                                        re[q][0] = fmaf(f0, t.x, re[q][0]);
+                                        im[q][0] = fmaf(f0, t.y, im[q][0]);
+                                        re[q][1] = fmaf(f1, t.x, re[q][1]);
+                                        im[q][1] = fmaf(f1, t.y, im[q][1]);
+                                        idx[q] = (idx[q] + (unsigned)(k0 + q)) & (unsigned)nbm1;
+                                    }
+                                }
+                            }
+                            __syncthreads();   // H is read before the next pass zeroes it
+                        }
+                    }
+                    if (unit) {
+#pragma unroll
+                        for (int q = 0; q < kKpw; ++q) {
+                            PART[((size_t)warp * kKpw + q) * kDirs + 2 * lane] = make_float2(re[q][0], im[q][0]);
+                            PART[((size_t)warp * kKpw + q) * kDirs + 2 * lane + 1] = make_float2(re[q][1], im[q][1]);
+                        }
+                    }
+                    __syncthreads();
+                    if (tid < kDirs) {
+                        for (int kk = g_lo * kKpw; kk < min(K, (g_lo + Gr) * kKpw); ++kk) {
+                            const int gg = kk / kKpw - g_lo, q = kk % kKpw;
+                            float sr = 0.f, si = 0.f;
+                            for (int s2 = 0; s2 < nsplit; ++s2) {
+                                const float2 t = PART[((size_t)(gg * nsplit + s2) * kKpw + q) * kDirs + tid];
+                                sr += t.x;
+                                si += t.y;
+                            }
+                            band_update_t<kNB>(p.bands, klo, khi, klo + kk, sqrtf(sr * sr + si * si), best, bk);
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (tid < kDirs) {
+                    const int64_t v = (int64_t)tile * kDirs + tid;
+                    if (v < p.nv) {
+#pragma unroll
+                        for (int b = 0; b < kNB; ++b) {
+                            if (b < band_count_t<kNB>(p.bands)) {
+                                p.S[band_off_t<kNB>(p.bands, b) + out_base + v] = best[b];
+                                if (p.argk) p.argk[band_off_t<kNB>(p.bands, b) + out_base + v] = (uint16_t)bk[b];
+                            }
+                        }
+                    }
+                }
+            }
+            continue;
+        }
+
         for (int tile = t0; tile < t1; ++tile) {
             uint4* H4 = reinterpret_cast<uint4*>(H);
             for (int i = tid; i < NB * kWords / 4; i += kThreads) H4[i] = make_uint4(0, 0, 0, 0);
@@ -120,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_plain(SigParams p) {
             }
             __syncthreads();
 
-            if (p.hist_out) hist_export(H, NB, tile, p.nv, p.hist_out, tid, kThreads);
+            if (p.hist_out) hist_export_add_p(H, NB, NB, 0, tile, p.nv, p.hist_out, tid, kThreads);
 
             // ---- band spectrum (FP32) and band maximum ----
             const int K = khi - klo + 1;
@@ -285,7 +431,8 @@ cudaError_t launch_normalise(Ctx* c, float* S, int64_t rows) {
 
 size_t plain_smem_bytes(int m, int atom_cap) {
     const size_t NB = (size_t)1 << m;
-    return NB * kWords * 4 + NB * 8 + (size_t)atom_cap * 16 + kPartBytes + 64;
+    const size_t NBc = NB < (size_t)kChunkBins ? NB : (size_t)kChunkBins;
+    return NBc * kWords * 4 + NB * 8 + (size_t)atom_cap * 16 + kPartBytes + 64;
 }
 
 cudaError_t launch_signatures_plain(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out, int64_t hist_roi,
@@ -356,8 +503,8 @@ constexpr int64_t kNaMaxRoi = APTIDX_NOALLOC_MAX_ROIS;
 constexpr int64_t kNaMaxDirs = APTIDX_NOALLOC_MAX_DIRS;
 // byte offsets inside the scratch array
 constexpr size_t kNaDirs = 0;                                        // float4 [kNaMaxDirs]
-constexpr size_t kNaTw = kNaDirs + 16 * (size_t)kNaMaxDirs;          // float2 [1024]
-constexpr size_t kNaScale = kNaTw + 8 * 1024;                        // float  [kNaMaxRoi]
+constexpr size_t kNaTw = kNaDirs + 16 * (size_t)kNaMaxDirs;          // float2 [2^APTIDX_MAX_M]
+constexpr size_t kNaScale = kNaTw + 8 * ((size_t)1 << APTIDX_MAX_M);  // float  [kNaMaxRoi]
 constexpr size_t kNaBand = kNaScale + 4 * (size_t)kNaMaxRoi;         // int32  [2 kNaMaxRoi]
 constexpr size_t kNaNw = kNaBand + 8 * (size_t)kNaMaxRoi;            // int32  [kNaMaxRoi]
 constexpr size_t kNaOrder = kNaNw + 4 * (size_t)kNaMaxRoi;           // int32  [kNaMaxRoi]

@@ -1,32 +1,43 @@
 // signature_tc.cu -- steps (a2)-(a5) with the band spectrum on the tcgen05
-// tensor cores: X = H x T, H the [64 directions x 2^m bins] histogram tile and
-// T the [2^m bins x band columns] DFT matrix (cos and sin of 2 pi k n / 2^m),
+// tensor cores: X = H x T, H the [64 directions x bins] histogram tile and T
+// the [bins x band columns] DFT matrix (cos and sin of 2 pi k n / 2^m),
 // accumulated in FP32 in tensor memory (Section 2.2: the Fourier amplitude
 // spectrum of every SDM; the paper notes that the SDMs of a ROI share one
 // bin count, which permits batching their transforms).
 //
-// The contraction runs as M = 128 rows: rows 0-63 are the 64 directions over
-// bins [0, 2^m / 2), rows 64-127 the same directions over [2^m / 2, 2^m).
+// The histogram of a tile is built in chunks of at most 1024 bins (2^m <= 1024:
+// one chunk; m = 11, 12: two or four) and over blocks of at most 2048 atoms,
+// so that every count of a block is exact in fp16; every (block, chunk) pass is
+// contracted into the same tensor-memory accumulators.  The contraction of a
+// pass runs as M = 128 rows: rows 0-63 are the 64 directions over the chunk's
+// first half of bins, rows 64-127 the same directions over its second half.
 // Both halves use the twiddles of the first half, since
-// w^(k (n + 2^m / 2)) = (-1)^k w^(k n) for w = exp(-2 pi i / 2^m); the
-// epilogue forms X(k) = D_lo(k) + (-1)^k D_hi(k).  Half the K steps of an
-// M = 64 contraction, so half the MMA instructions.
+// w^(k (n + h)) = w^(k h) w^(k n) for w = exp(-2 pi i / 2^m) and the half
+// offset h = 2^(m-1) (one chunk: w^(k h) = (-1)^k) or h = 512 (chunks of 1024);
+// the epilogue forms X(k) = D_lo(k) + w^(k h) D_hi(k).
 //
-// Per 64-direction tile of a ROI:
+// Antipodal pairs: when the direction set holds u and -u, only u is projected;
+// -u gets the same signature value and frequency bin (its histogram is the
+// mirror image of u's, whose spectrum has the same amplitudes), provided no
+// atom's bin product along u is an exact integer, which the histogram pass
+// counts exactly (common.cuh).  A tile with such an atom runs a second pass
+// over the negated directions and writes their signatures from their own
+// histograms.
+//
+// Per 64-direction tile of a ROI and (block, chunk) pass:
 //   1. histograms by shared-memory atomics (bank-private columns, as in the
 //      FP32 path); counts c <= 2048, so the u16 bit pattern of c is the fp16
 //      value c * 2^-24 exactly (fp16 is linear through its subnormal range up
 //      to 0x0800) and the histogram is the A operand as it stands;
 //   2. an in-place permutation of 16-byte chunks gives the MN-major 128-byte
 //      swizzled layout (chunk c of bin row k moves to c ^ (k & 7));
-//   3. up to four issuer threads issue the 2^m / 32 tcgen05.mma (M = 128,
-//      K = 16, N = 16 per group of 4 frequencies: 8 hi columns, then 8 lo
-//      columns, where T = T_hi + T_lo with both parts fp16) into FP32
+//   3. up to four issuer threads issue the bins / 32 tcgen05.mma of the chunk
+//      (M = 128, K = 16, N = 16 per group of 4 frequencies: 8 hi columns, then
+//      8 lo columns, where T = T_hi + T_lo with both parts fp16) into FP32
 //      accumulators in TMEM;
-//   4. four warps read the accumulators (tcgen05.ld), add hi and lo parts and
-//      the two bin halves, scale by 2^24 and keep the band maximum of |X(k)|.
-// ROIs with more than 2048 atoms (where a bin could exceed fp16's exact
-// range) run on the FP32 kernel in the same call.
+//   4. after the last pass, four warps read the accumulators (tcgen05.ld), add
+//      hi and lo parts and the two bin halves, scale by 2^24 and keep the band
+//      maximum of |X(k)|.
 #include <cuda_fp16.h>
 
 #include "tcgen05.cuh"
@@ -42,14 +53,15 @@ constexpr int kRows = 2 * kDirs;     // MMA M: (direction, bin half)
 constexpr int kBtBytes = 32 * 1024;  // shared-memory budget of the B operand
 constexpr int kExBytes = kDirs * 8 * 4;   // epilogue exchange: one group's (re, im) x 4 per direction
 constexpr int kIssuers = 4;          // at most this many warps issue MMAs, one TMEM partial accumulator each
+constexpr int kChunkBins = 1024;     // bins per histogram chunk (128 KB of words)
 
 struct TcParams {
     const float4* atoms;
     const int64_t* off;
     const int32_t* nw;
     const int32_t* order;
-    const int32_t* n_big;
-    const float4* dirs;
+    const float4* dirs;     // direction slots, padded to whole tiles with (1, 0, 0)
+    const int2* slot_idx;   // per slot: (output direction, antipodal partner or -1); NULL: slot = direction
     int32_t nv;
     int32_t tiles_per_roi;
     int32_t tiles_per_item;
@@ -59,7 +71,7 @@ struct TcParams {
     const int32_t* band;
     int m;
     int32_t kbase;          // frequency of column group 0
-    const uint8_t* twb;     // global B: [hi|lo][group][k-block] x 1 KB
+    const uint8_t* twb;     // global B: [chunk][hi|lo][group][k-block] x 1 KB
     int32_t ng_total;
     int32_t gb;             // groups per shared-memory batch
     uint32_t tmem_cols;
@@ -69,13 +81,31 @@ struct TcParams {
     int64_t single_roi;
     int32_t* counter;
     int* status;
-    int atom_cap;
+    int atom_cap;           // atoms per block (<= 2048)
     int n_iss;              // MMA issuer warps (1 .. kIssuers)
     BandSet bands;
 };
 
 // instruction descriptor: A MN-major (the histogram), B K-major, M = 128
 __device__ __forceinline__ uint32_t idesc_f16(int n) { return idesc_f16_mk(kRows, n, true); }
+
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+
+// Debug export of one (block, chunk) pass: adds the counts of rows
+// [0, nbc) to h_out[v * 2^m + bc * nbc + row] (the caller zeroes h_out).
+__device__ __forceinline__ void hist_export_add(const uint32_t* H, int nbc, int NB, int bc, int tile, int nv,
+                                                uint16_t* h_out, int tid, int nthreads) {
+    for (int i = tid; i < nbc * 32; i += nthreads) {
+        const int b = i >> 5, l = i & 31;
+        const uint32_t w = H[i];
+        const int64_t v0 = (int64_t)tile * 64 + 2 * l;
+        const int64_t col = (int64_t)bc * nbc + b;
+        if (v0 < nv) h_out[v0 * NB + col] = (uint16_t)(h_out[v0 * NB + col] + (w & 0xFFFFu));
+        if (v0 + 1 < nv) h_out[(v0 + 1) * NB + col] = (uint16_t)(h_out[(v0 + 1) * NB + col] + (w >> 16));
+    }
+}
 
 // ---- the kernel ----------------------------------------------------------------
 
@@ -88,13 +118,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     // shared array keeps the pointers in the shared address space
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int NB = 1 << p.m;
-    const int KB = NB / 128;   // 1 KB K-blocks of the B operand (K = 2^m / 2 rows)
+    const int NBc = NB < kChunkBins ? NB : kChunkBins;   // bins per chunk
+    const int nchunk = NB / NBc;
+    const uint32_t cmask = (uint32_t)(nchunk - 1);
+    const int KB = NBc / 128;   // 1 KB K-blocks of the B operand per chunk (K = NBc / 2 rows)
     uint32_t* H = reinterpret_cast<uint32_t*>(smem);
-    unsigned char* BT = smem + (size_t)NB * 128;
+    unsigned char* BT = smem + (size_t)NBc * 128;
     float* EX = reinterpret_cast<float*>(BT + kBtBytes);   // [kDirs][8]
     float4* A = reinterpret_cast<float4*>(BT + kBtBytes + kExBytes);
     float4* DB = A + p.atom_cap;   // [2][kDirs]: this tile's directions and the next tile's
-    float* EX2 = reinterpret_cast<float*>(DB + 2 * kDirs);   // [128 TMEM lanes][8]: partials 2, 3
+    int2* DI = reinterpret_cast<int2*>(DB + 2 * kDirs);   // [2][kDirs]: (output, partner) of those slots
+    float* EX2 = reinterpret_cast<float*>(DI + 2 * kDirs);   // [128 TMEM lanes][8]: partials 2, 3
     // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per issuer
     uint64_t* bars = reinterpret_cast<uint64_t*>(EX2 + 128 * 8);
     int* flag = reinterpret_cast<int*>(bars + 2 + kIssuers);
@@ -107,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         for (int i = 0; i < 2 + kIssuers; ++i) mbar_init(&bars[i], 1);
         fence_barrier_init();
     }
-    for (int i = tid; i < NB * 8; i += kThreads) reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < NBc * 8; i += kThreads) reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_s)),
                      "r"(p.tmem_cols)
@@ -122,16 +156,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     const uint32_t bt_addr = smem_u32(BT);
 
     uint32_t ph_atoms = 0, ph_b = 0, ph_mma = 0;   // ph_mma: this warp's issuer barrier
-    int cur_g0 = -1, cur_nb = -1;
+    int cur_g0 = -1, cur_nb = -1, cur_bc = -1;     // B operand held in shared memory
     const float magic = bin_magic(p.m);
-
-    int64_t rank_lo = 0, n_items;
-    if (p.single_roi >= 0) {
-        n_items = p.items_per_roi;
-    } else {
-        rank_lo = *p.n_big;
-        n_items = (p.nroi - rank_lo) * p.items_per_roi;
-    }
+    const bool sym = p.slot_idx != nullptr;
+    const int64_t n_items = (p.single_roi >= 0 ? 1 : p.nroi) * (int64_t)p.items_per_roi;
     bool failed = false;
 
     for (;;) {
@@ -140,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         const int64_t item = *item_s;
         __syncthreads();
         if (item >= n_items) break;
-        const int64_t roi = p.single_roi >= 0 ? p.single_roi : (int64_t)p.order[rank_lo + item / p.items_per_roi];
+        const int64_t roi = p.single_roi >= 0 ? p.single_roi : (int64_t)p.order[item / p.items_per_roi];
         const int grp = (int)(item % p.items_per_roi);
         const int nw = p.nw[roi];
         const int64_t abase = p.off[roi];
@@ -151,8 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         const int nbatch = (ng + p.gb - 1) / p.gb;
         const int t0 = grp * p.tiles_per_item;
         const int t1 = min(t0 + p.tiles_per_item, p.tiles_per_roi);
-        const bool one_chunk = nw <= p.atom_cap;
-        if (one_chunk) {
+        const int nblk = max(1, (nw + p.atom_cap - 1) / p.atom_cap);   // atom blocks
+        if (nblk == 1) {
             if (!stage_atoms(A, p.atoms + abase, nw, &bars[0], ph_atoms, p.status, flag)) {
                 failed = true;
                 break;
@@ -161,261 +189,347 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         }
         // the first tile's directions (later tiles' arrive while the tile
         // before them runs)
-        if (tid < kDirs) cp_async16(DB + (t0 & 1) * kDirs + tid, p.dirs + (int64_t)t0 * kDirs + tid);
+        if (tid < kDirs) {
+            cp_async16(DB + (t0 & 1) * kDirs + tid, p.dirs + (int64_t)t0 * kDirs + tid);
+            if (sym) cp_async8(DI + (t0 & 1) * kDirs + tid, p.slot_idx + (int64_t)t0 * kDirs + tid);
+        }
         cp_async_wait_all();
         __syncthreads();
 
         for (int tile = t0; tile < t1 && !failed; ++tile) {
-            // ---- 1. histograms (H is zero here) ----
-            const float4 d0 = DB[(tile & 1) * kDirs + 2 * lane];
-            const float4 d1 = DB[(tile & 1) * kDirs + 2 * lane + 1];
-            if (tile + 1 < t1 && tid < kDirs)
-                cp_async16(DB + ((tile + 1) & 1) * kDirs + tid, p.dirs + (int64_t)(tile + 1) * kDirs + tid);
-            for (int c0 = 0; c0 < nw; c0 += p.atom_cap) {
-                const int cn = min(p.atom_cap, nw - c0);
-                if (!one_chunk) {
-                    if (!stage_atoms(A, p.atoms + abase + c0, cn, &bars[0], ph_atoms, p.status, flag)) {
-                        failed = true;
-                        break;
+            const int cur = tile & 1;
+            float4 d0 = DB[cur * kDirs + 2 * lane];
+            float4 d1 = DB[cur * kDirs + 2 * lane + 1];
+            const int pt0 = sym ? DI[cur * kDirs + 2 * lane].y : -1;
+            const int pt1 = sym ? DI[cur * kDirs + 2 * lane + 1].y : -1;
+            if (tile + 1 < t1 && tid < kDirs) {
+                cp_async16(DB + (cur ^ 1) * kDirs + tid, p.dirs + (int64_t)(tile + 1) * kDirs + tid);
+                if (sym) cp_async8(DI + (cur ^ 1) * kDirs + tid, p.slot_idx + (int64_t)(tile + 1) * kDirs + tid);
+            }
+            int tile_bad = 0;
+            for (int pass = 0; pass < 2 && !failed; ++pass) {
+                if (pass == 1) {
+                    if (!tile_bad) break;
+                    // the partners -u of this tile's directions, from their own histograms
+                    d0 = make_float4(-d0.x, -d0.y, -d0.z, d0.w);
+                    d1 = make_float4(-d1.x, -d1.y, -d1.z, d1.w);
+                }
+                const bool count = sym && pass == 0;
+                uint32_t c0 = 0, c1 = 0;
+                int handled = 0;
+                const int n_sub = nblk * nchunk;
+                for (int sub = 0; sub < n_sub && !failed; ++sub) {
+                    const int blk = sub / nchunk, bc = sub % nchunk;
+                    const int cn = min(p.atom_cap, nw - blk * p.atom_cap);
+                    const bool last = sub == n_sub - 1;
+                    if (nblk > 1 && bc == 0) {
+                        if (!stage_atoms(A, p.atoms + abase + (int64_t)blk * p.atom_cap, cn, &bars[0], ph_atoms,
+                                         p.status, flag)) {
+                            failed = true;
+                            break;
+                        }
+                        pair_atoms(A, cn, tid, kThreads);
+                        __syncthreads();
                     }
-                    pair_atoms(A, cn, tid, kThreads);
+                    // ---- 1. histograms (H is zero here) ----
+                    if (nchunk == 1) {
+                        if (count)
+                            handled += hist_tile_pairs2<kWarps, true, false>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                             0u, 0u, c0, c1);
+                        else
+                            hist_tile_pairs2<kWarps, false, false>(H, A, cn, warp, lane, d0, d1, scale, magic, 0u, 0u,
+                                                                   c0, c1);
+                    } else {
+                        if (count && bc == 0)
+                            handled += hist_tile_pairs2<kWarps, true, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                            (uint32_t)bc, cmask, c0, c1);
+                        else
+                            hist_tile_pairs2<kWarps, false, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                  (uint32_t)bc, cmask, c0, c1);
+                    }
                     __syncthreads();
-                }
-                hist_tile_pairs<kWarps>(H, A, cn, warp, lane, d0, d1, scale, magic);
-                if (!one_chunk) __syncthreads();
-            }
-            if (failed) break;
-            __syncthreads();
-            if (p.hist_out) {
-                hist_export(H, NB, tile, p.nv, p.hist_out, tid, kThreads);
-                __syncthreads();   // every row is read before the permutation moves it
-            }
+                    if (p.hist_out) {
+                        hist_export_add(H, NBc, NB, bc, tile, p.nv, p.hist_out, tid, kThreads);
+                        __syncthreads();   // every row is read before the permutation moves it
+                    }
 
-            // ---- 2. swizzle: every warp brings bin rows into the MN-major
-            // 128-byte swizzled layout in place (a warp holds four rows, 512
-            // contiguous bytes, one 16-byte chunk per lane, and writes chunk c
-            // of row k to chunk c ^ (k & 7); rows with k & 7 == 0 stay).  The
-            // pass runs at the shared-memory bandwidth; interleaving it with
-            // the MMAs below slows both, so the two run one after the other.
-            // ---- 3. contraction: lane 0 of warps 0 .. n_iss-1 issues every
-            // n_iss-th K step into its own partial accumulator (a single
-            // tcgen05.mma costs the issuing warp ~75 cycles whatever its N;
-            // several issuers overlap that cost).
-            const int n_iss = nbatch == 1 ? p.n_iss : 1;
-            const uint32_t sbo_b = (uint32_t)KB * 1024u;
-            const uint32_t cols_b = (uint32_t)(16 * p.gb);   // TMEM columns per accumulator
-            const bool issuer = lane == 0 && warp < n_iss;
-            int ok = 1;
-            if (tid == 0) {
-                // B operand of batch 0 (kept across tiles while the ROI band allows)
-                const int nb0 = min(p.gb, fg1 + 1 - fg0);
-                if (fg0 != cur_g0 || nb0 != cur_nb) {
-                    const uint32_t part = (uint32_t)nb0 * KB * 1024u;
-                    mbar_arrive_expect_tx(&bars[1], 2 * part);
-                    bulk_g2s(BT, p.twb + (size_t)fg0 * KB * 1024, part, &bars[1]);
-                    bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + fg0) * KB * 1024, part, &bars[1]);
-                    ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
-                    if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
-                    ph_b ^= 1u;
-                    cur_g0 = ok ? fg0 : -1;
-                    cur_nb = nb0;
-                }
-                *flag = ok;
-            }
-            // two groups of four rows per pass, 64 rows apart (same k & 7;
-            // NB is a multiple of 128), both loaded before either is stored
-            for (int r0 = warp * 4; r0 < NB; r0 += kWarps * 8) {
-                const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
-                uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
-                uint4* row2 = row + kWarps * 4 * 8;   // row k + 64
-                uint4 x, x2;
-                if (sw) {
-                    x = row[c];
-                    x2 = row2[c];
-                }
-                __syncwarp();
-                if (sw) {
-                    row[c ^ sw] = x;
-                    row2[c ^ sw] = x2;
-                }
-            }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            ok = *flag;
-            if (issuer && ok) {
-                tc_fence_after();
-                const int nb0 = min(p.gb, fg1 + 1 - fg0);
-                const uint32_t idesc = idesc_f16(16 * nb0);
-                const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
-                // A: rows 64-127 (second bin half) one swizzle atom along M
-                // away, NB / 2 bin rows of 128 bytes
-                const uint64_t a0 = sdesc_sw128(h_addr, (uint32_t)NB * 64u, 1024u);
-                const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
-                // descriptors advance by constant steps: A by 2 KB per K step,
-                // B by 32 bytes inside a 128-byte row and 1 KB per 64-bin
-                // block (the address field counts 16-byte units)
-                for (int kk = warp; kk < NB / 32; kk += n_iss) {
-                    const uint64_t ad = a0 + (uint64_t)(kk * 128);
-                    const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
-                    mma_f16(dcol, ad, bd, idesc, kk >= n_iss ? 1u : 0u);
-                }
-                if (tid == 0 && nbatch > 1) {
-                    // wide band: further batches, each reloading the B buffer
-                    for (int b = 1; b < nbatch && ok; ++b) {
-                        mma_commit(&bars[2]);
-                        ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
-                        ph_mma ^= 1u;
-                        if (!ok) break;
-                        const int g0 = fg0 + b * p.gb;
-                        const int nb = min(p.gb, fg1 + 1 - g0);
-                        const uint32_t part = (uint32_t)nb * KB * 1024u;
-                        mbar_arrive_expect_tx(&bars[1], 2 * part);
-                        bulk_g2s(BT, p.twb + (size_t)g0 * KB * 1024, part, &bars[1]);
-                        bulk_g2s(BT + part, p.twb + ((size_t)p.ng_total + g0) * KB * 1024, part, &bars[1]);
-                        ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
-                        if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
-                        ph_b ^= 1u;
-                        cur_g0 = ok ? g0 : -1;
-                        cur_nb = nb;
-                        if (!ok) break;
+                    // ---- 2. swizzle: every warp brings bin rows into the MN-major
+                    // 128-byte swizzled layout in place (a warp holds four rows, 512
+                    // contiguous bytes, one 16-byte chunk per lane, and writes chunk c
+                    // of row k to chunk c ^ (k & 7); rows with k & 7 == 0 stay).  The
+                    // pass runs at the shared-memory bandwidth; interleaving it with
+                    // the MMAs below slows both, so the two run one after the other.
+                    // ---- 3. contraction: lane 0 of warps 0 .. n_iss-1 issues every
+                    // n_iss-th K step into its own partial accumulator (a single
+                    // tcgen05.mma costs the issuing warp ~75 cycles whatever its N;
+                    // several issuers overlap that cost); every pass after the first
+                    // accumulates onto the result so far.
+                    const int n_iss = nbatch == 1 ? p.n_iss : 1;
+                    const uint32_t sbo_b = (uint32_t)KB * 1024u;
+                    const uint32_t cols_b = (uint32_t)(16 * p.gb);   // TMEM columns per accumulator
+                    const bool issuer = lane == 0 && warp < n_iss;
+                    const uint32_t acc0 = sub > 0 ? 1u : 0u;
+                    int ok = 1;
+                    if (tid == 0) {
+                        // B operand of batch 0 for this chunk (kept across tiles while
+                        // the ROI band and the chunk allow)
+                        const int nb0 = min(p.gb, fg1 + 1 - fg0);
+                        if (fg0 != cur_g0 || nb0 != cur_nb || bc != cur_bc) {
+                            const uint32_t part = (uint32_t)nb0 * KB * 1024u;
+                            mbar_arrive_expect_tx(&bars[1], 2 * part);
+                            bulk_g2s(BT, p.twb + ((size_t)(2 * bc) * p.ng_total + fg0) * KB * 1024, part, &bars[1]);
+                            bulk_g2s(BT + part, p.twb + ((size_t)(2 * bc + 1) * p.ng_total + fg0) * KB * 1024, part,
+                                     &bars[1]);
+                            ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                            if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                            ph_b ^= 1u;
+                            cur_g0 = ok ? fg0 : -1;
+                            cur_nb = nb0;
+                            cur_bc = bc;
+                        }
+                        *flag = ok;
+                    }
+                    // two groups of four rows per pass, 64 rows apart (same k & 7;
+                    // the chunk's rows are a multiple of 128)
+                    for (int r0 = warp * 4; r0 < NBc; r0 += kWarps * 8) {
+                        const int k = r0 + (lane >> 3), c = lane & 7, sw = k & 7;
+                        uint4* row = reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(H) + (size_t)k * 128);
+                        uint4* row2 = row + kWarps * 4 * 8;   // row k + 64
+                        uint4 x, x2;
+                        if (sw) {
+                            x = row[c];
+                            x2 = row2[c];
+                        }
+                        __syncwarp();
+                        if (sw) {
+                            row[c ^ sw] = x;
+                            row2[c ^ sw] = x2;
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    __syncthreads();
+                    ok = *flag;
+                    if (issuer && ok) {
                         tc_fence_after();
-                        const uint32_t idb = idesc_f16(16 * nb);
-                        const uint32_t dcb = tmem + (uint32_t)b * cols_b;
-                        for (int kk = 0; kk < NB / 32; ++kk) {
+                        const int nb0 = min(p.gb, fg1 + 1 - fg0);
+                        const uint32_t idesc = idesc_f16(16 * nb0);
+                        const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
+                        // A: rows 64-127 (second bin half) one swizzle atom along M
+                        // away, NBc / 2 bin rows of 128 bytes
+                        const uint64_t a0 = sdesc_sw128(h_addr, (uint32_t)NBc * 64u, 1024u);
+                        const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
+                        // descriptors advance by constant steps: A by 2 KB per K step,
+                        // B by 32 bytes inside a 128-byte row and 1 KB per 64-bin
+                        // block (the address field counts 16-byte units)
+                        for (int kk = warp; kk < NBc / 32; kk += n_iss) {
                             const uint64_t ad = a0 + (uint64_t)(kk * 128);
                             const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
-                            mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : 0u);
+                            mma_f16(dcol, ad, bd, idesc, (kk >= n_iss) ? 1u : acc0);
+                        }
+                        if (tid == 0 && nbatch > 1) {
+                            // wide band: further batches, each reloading the B buffer
+                            for (int b = 1; b < nbatch && ok; ++b) {
+                                mma_commit(&bars[2]);
+                                ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
+                                ph_mma ^= 1u;
+                                if (!ok) break;
+                                const int g0 = fg0 + b * p.gb;
+                                const int nb = min(p.gb, fg1 + 1 - g0);
+                                const uint32_t part = (uint32_t)nb * KB * 1024u;
+                                mbar_arrive_expect_tx(&bars[1], 2 * part);
+                                bulk_g2s(BT, p.twb + ((size_t)(2 * bc) * p.ng_total + g0) * KB * 1024, part, &bars[1]);
+                                bulk_g2s(BT + part, p.twb + ((size_t)(2 * bc + 1) * p.ng_total + g0) * KB * 1024, part,
+                                         &bars[1]);
+                                ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                                if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                                ph_b ^= 1u;
+                                cur_g0 = ok ? g0 : -1;
+                                cur_nb = nb;
+                                cur_bc = bc;
+                                if (!ok) break;
+                                tc_fence_after();
+                                const uint32_t idb = idesc_f16(16 * nb);
+                                const uint32_t dcb = tmem + (uint32_t)b * cols_b;
+                                for (int kk = 0; kk < NBc / 32; ++kk) {
+                                    const uint64_t ad = a0 + (uint64_t)(kk * 128);
+                                    const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
+                                    mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : acc0);
+                                }
+                            }
                         }
                     }
+                    if (issuer) {
+                        int mine = ok;
+                        if (mine) {
+                            mma_commit(&bars[2 + warp]);
+                            mine = mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status) ? 1 : 0;
+                            if (!mine) mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status, 1u << 20);
+                            ph_mma ^= 1u;
+                        }
+                        iss_ok[warp] = mine;
+                    }
+                    // the non-integer counts are complete once the last pass's
+                    // histogram is in: a partner whose count falls short of the
+                    // atoms this warp handled needs its own histogram
+                    const int bad = count && last && ((pt0 >= 0 && c0 != (uint32_t)handled) ||
+                                                      (pt1 >= 0 && c1 != (uint32_t)handled));
+                    const int any_bad = __syncthreads_or(bad);
+                    if (last) tile_bad = any_bad;
+                    {
+                        int all = 1;
+                        for (int i = 0; i < n_iss; ++i) all &= iss_ok[i];
+                        if (!all) {
+                            failed = true;
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    if (!last) {
+                        // H is read by the MMAs above; zero it for the next pass
+                        for (int i = tid; i < NBc * 8; i += kThreads)
+                            reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+                        __syncthreads();
+                    }
                 }
-            }
-            if (issuer) {
-                int mine = ok;
-                if (mine) {
-                    mma_commit(&bars[2 + warp]);
-                    mine = mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status) ? 1 : 0;
-                    if (!mine) mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status, 1u << 20);
-                    ph_mma ^= 1u;
-                }
-                iss_ok[warp] = mine;
-            }
-            __syncthreads();
-            {
-                int all = 1;
-                for (int i = 0; i < n_iss; ++i) all &= iss_ok[i];
-                if (!all) {
-                    failed = true;
-                    break;
-                }
-            }
-            tc_fence_after();
+                if (failed) break;
 
-            // ---- 4. epilogue: |X(k)| and the band maximum (warps 0-3, one per
-            // TMEM lane quadrant); the other warps zero H for the next tile.
-            // With four partial accumulators and one frequency group, warps
-            // 4-7 sum partials 2 and 3 of the same quadrants meanwhile, so
-            // that each warp waits on two tensor-memory round trips, not four ----
-            const bool split = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
-            const int zw0 = split ? 8 : 4;   // first zeroing warp
-            if (warp >= zw0) {
-                for (int i = tid - zw0 * 32; i < NB * 8; i += kThreads - zw0 * 32)
-                    reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
-            } else if (warp >= 4) {
-                const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
-                const uint32_t cols_b = (uint32_t)(16 * p.gb);
-                float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int i = kIssuers / 2; i < kIssuers; ++i) {
-                    const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
-                    float hi[8], lo[8];
-                    tmem_ld8(dcol, hi);
-                    tmem_ld8(dcol + 8u, lo);
-                    tmem_wait_ld();
+                // ---- 4. epilogue: |X(k)| and the band maximum (warps 0-3, one per
+                // TMEM lane quadrant); the other warps zero H for the next tile.
+                // With four partial accumulators and one frequency group, warps
+                // 4-7 sum partials 2 and 3 of the same quadrants meanwhile, so
+                // that each warp waits on two tensor-memory round trips, not four ----
+                const bool split = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
+                const int zw0 = split ? 8 : 4;   // first zeroing warp
+                if (warp >= zw0) {
+                    for (int i = tid - zw0 * 32; i < NBc * 8; i += kThreads - zw0 * 32)
+                        reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
+                } else if (warp >= 4) {
+                    const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
+                    const uint32_t cols_b = (uint32_t)(16 * p.gb);
+                    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int i = kIssuers / 2; i < kIssuers; ++i) {
+                        const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
+                        float hi[8], lo[8];
+                        tmem_ld8(dcol, hi);
+                        tmem_ld8(dcol + 8u, lo);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            re[q] += hi[2 * q] + lo[2 * q];
+                            im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                        }
+                    }
+                    float* e2 = EX2 + (size_t)(tid - 128) * 8;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        re[q] += hi[2 * q] + lo[2 * q];
-                        im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                        e2[2 * q] = re[q];
+                        e2[2 * q + 1] = im[q];
                     }
-                }
-                float* e2 = EX2 + (size_t)(tid - 128) * 8;
+                    asm volatile("bar.sync 2, 256;" ::: "memory");
+                } else {
+                    // warps 0, 1 hold rows 0-63 (the first half of the chunk's
+                    // bins), warps 2, 3 rows 64-127; per frequency group the
+                    // second-half warps hand their sums over through shared memory
+                    float best[kNB];
+                    int bk[kNB];
+                    band_init_t<kNB>(p.bands, klo, best, bk);
+                    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+                    const int n_iss = nbatch == 1 ? p.n_iss : 1;
+                    const uint32_t cols_b = (uint32_t)(16 * p.gb);
+                    const int dir = (warp & 1) * 32 + lane;
+                    for (int b = 0; b < nbatch; ++b) {
+                        const int g0 = fg0 + b * p.gb;
+                        const int nb = min(p.gb, fg1 + 1 - g0);
+                        for (int j = 0; j < nb; ++j) {
+                            float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+                            for (int i = 0; i < (split ? kIssuers / 2 : n_iss); ++i) {
+                                const uint32_t dcol = lane_base + (uint32_t)(b + i) * cols_b;
+                                float hi[8], lo[8];
+                                tmem_ld8(dcol + (uint32_t)(8 * j), hi);
+                                tmem_ld8(dcol + (uint32_t)(8 * nb + 8 * j), lo);
+                                tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    e2[2 * q] = re[q];
-                    e2[2 * q + 1] = im[q];
-                }
-                asm volatile("bar.sync 2, 256;" ::: "memory");
-            } else {
-                // warps 0, 1 hold rows 0-63 (bins of the first half), warps
-                // 2, 3 rows 64-127; per frequency group the second-half warps
-                // hand their sums over through shared memory
-                float best[kNB];
-                int bk[kNB];
-                band_init_t<kNB>(p.bands, klo, best, bk);
-                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-                const int n_iss = nbatch == 1 ? p.n_iss : 1;
-                const uint32_t cols_b = (uint32_t)(16 * p.gb);
-                const int dir = (warp & 1) * 32 + lane;
-                for (int b = 0; b < nbatch; ++b) {
-                    const int g0 = fg0 + b * p.gb;
-                    const int nb = min(p.gb, fg1 + 1 - g0);
-                    for (int j = 0; j < nb; ++j) {
-                        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-                        for (int i = 0; i < (split ? kIssuers / 2 : n_iss); ++i) {
-                            const uint32_t dcol = lane_base + (uint32_t)(b + i) * cols_b;
-                            float hi[8], lo[8];
-                            tmem_ld8(dcol + (uint32_t)(8 * j), hi);
-                            tmem_ld8(dcol + (uint32_t)(8 * nb + 8 * j), lo);
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                re[q] += hi[2 * q] + lo[2 * q];
-                                im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                                for (int q = 0; q < 4; ++q) {
+                                    re[q] += hi[2 * q] + lo[2 * q];
+                                    im[q] += hi[2 * q + 1] + lo[2 * q + 1];
+                                }
                             }
-                        }
-                        if (split) {   // partials 2, 3 from warp + 4 (one group: j = 0)
-                            asm volatile("bar.sync 2, 256;" ::: "memory");
-                            const float* e2 = EX2 + (size_t)tid * 8;
+                            if (split) {   // partials 2, 3 from warp + 4 (one group: j = 0)
+                                asm volatile("bar.sync 2, 256;" ::: "memory");
+                                const float* e2 = EX2 + (size_t)tid * 8;
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                re[q] += e2[2 * q];
-                                im[q] += e2[2 * q + 1];
+                                for (int q = 0; q < 4; ++q) {
+                                    re[q] += e2[2 * q];
+                                    im[q] += e2[2 * q + 1];
+                                }
                             }
-                        }
-                        if (warp >= 2) {
+                            if (warp >= 2) {
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                EX[dir * 8 + 2 * q] = re[q];
-                                EX[dir * 8 + 2 * q + 1] = im[q];
+                                for (int q = 0; q < 4; ++q) {
+                                    EX[dir * 8 + 2 * q] = re[q];
+                                    EX[dir * 8 + 2 * q + 1] = im[q];
+                                }
                             }
-                        }
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
-                        if (warp < 2) {
+                            asm volatile("bar.sync 1, 128;" ::: "memory");
+                            if (warp < 2) {
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const int f = p.kbase + 4 * (g0 + j) + q;
-                                const float sg = (f & 1) ? -1.f : 1.f;
-                                const float xr = re[q] + sg * EX[dir * 8 + 2 * q];
-                                const float xi = im[q] + sg * EX[dir * 8 + 2 * q + 1];
-                                band_update_t<kNB>(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f, best,
-                                                   bk);
+                                for (int q = 0; q < 4; ++q) {
+                                    const int f = p.kbase + 4 * (g0 + j) + q;
+                                    // re = sum h cos, im = sum h sin over a half;
+                                    // X = D_lo + w^(f h) D_hi with D = re - i im
+                                    const float hr = EX[dir * 8 + 2 * q], hs = EX[dir * 8 + 2 * q + 1];
+                                    float xr, xi;
+                                    if (nchunk == 1) {
+                                        const float sg = (f & 1) ? -1.f : 1.f;
+                                        xr = re[q] + sg * hr;
+                                        xi = im[q] + sg * hs;
+                                    } else {
+                                        float fs, fc;   // w^(f h) = fc - i fs, h = 512
+                                        sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
+                                        xr = re[q] + fc * hr - fs * hs;
+                                        xi = im[q] + fs * hr + fc * hs;
+                                    }
+                                    band_update_t<kNB>(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f,
+                                                       best, bk);
+                                }
                             }
+                            asm volatile("bar.sync 1, 128;" ::: "memory");
                         }
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
                     }
-                }
-                if (warp < 2) {
-                    const int64_t v = (int64_t)tile * kDirs + dir;
-                    if (v < p.nv) {
-                        const int64_t o = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv + v;
+                    if (warp < 2) {
+                        // pass 0 writes the slot's direction (and its partner when
+                        // the tile's mirror images are exact); pass 1 the partners
+                        const int slot = tile * kDirs + dir;
+                        int v0, v1;
+                        if (sym) {
+                            const int2 si = DI[cur * kDirs + dir];
+                            v0 = pass == 0 ? si.x : si.y;
+                            v1 = (pass == 0 && !tile_bad) ? si.y : -1;
+                        } else {
+                            v0 = slot < p.nv ? slot : -1;
+                            v1 = -1;
+                        }
+                        const int64_t rb = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv;
 #pragma unroll
                         for (int b = 0; b < kNB; ++b) {
                             if (b < band_count_t<kNB>(p.bands)) {
-                                p.S[band_off_t<kNB>(p.bands, b) + o] = best[b];
-                                if (p.argk) p.argk[band_off_t<kNB>(p.bands, b) + o] = (uint16_t)bk[b];
+                                const int64_t ob = band_off_t<kNB>(p.bands, b) + rb;
+                                if (v0 >= 0) {
+                                    p.S[ob + v0] = best[b];
+                                    if (p.argk) p.argk[ob + v0] = (uint16_t)bk[b];
+                                }
+                                if (v1 >= 0) {
+                                    p.S[ob + v1] = best[b];
+                                    if (p.argk) p.argk[ob + v1] = (uint16_t)bk[b];
+                                }
                             }
                         }
                     }
                 }
+                tc_fence_before();
+                __syncthreads();   // H is zero and the accumulators are read before the next pass
+                tc_fence_after();
             }
             cp_async_wait_all();   // the next tile's directions have landed
             tc_fence_before();
@@ -434,29 +548,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
 
 // ---- the global B operand: DFT matrix columns, fp16 hi + lo, K-major SW128 ----
 
-// K runs over the first half of the bins, n in [0, 2^m / 2).
+// Chunk bc covers bins [bc nbc, bc nbc + nbc) with nbc = min(2^m, 1024); its K
+// rows are the first half of those bins, n = bc nbc + kr, kr < nbc / 2.
+// Layout [chunk][hi|lo][group][64-row K block] x 1 KB.
 __global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng) {
     const int NB = 1 << m;
-    const int NK = NB / 2;
+    const int NBc = NB < kChunkBins ? NB : kChunkBins;
+    const int nchunk = NB / NBc;
+    const int NK = NBc / 2;
     const int KB = NK / 64;
-    const int64_t total = (int64_t)2 * ng * NK * 8;   // [hi|lo] x groups x K rows x 8 columns
+    const int64_t total = (int64_t)nchunk * 2 * ng * NK * 8;   // chunks x [hi|lo] x groups x K rows x 8 columns
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i & 7);
         const int64_t t = i >> 3;
         const int k = (int)(t % NK);
         const int64_t t2 = t / NK;
         const int g = (int)(t2 % ng);
-        const int part = (int)(t2 / ng);   // 0 hi, 1 lo
+        const int64_t t3 = t2 / ng;
+        const int part = (int)(t3 % 2);   // 0 hi, 1 lo
+        const int bc = (int)(t3 / 2);
         const int f = kbase + 4 * g + (r >> 1);
-        const int jn = (int)(((int64_t)f * k) % NB);
+        const int64_t n = (int64_t)bc * NBc + k;
+        const int jn = (int)(((int64_t)f * n) % NB);
         double sn, cs;
         sincospi(2.0 * (double)jn / (double)NB, &sn, &cs);
         const double v = (r & 1) ? sn : cs;
         const __half hi = __double2half(v);
         const __half lo = __double2half(v - (double)__half2float(hi));
         const int kb = k >> 6, kin = k & 63;
-        const size_t off = ((size_t)(part * ng + g) * KB + kb) * 1024 + (size_t)r * 128 + (size_t)(((kin >> 3) ^ r) << 4) +
-                           (size_t)(kin & 7) * 2;
+        const size_t off = ((size_t)((2 * bc + part) * ng + g) * KB + kb) * 1024 + (size_t)r * 128 +
+                           (size_t)(((kin >> 3) ^ r) << 4) + (size_t)(kin & 7) * 2;
         *reinterpret_cast<__half*>(twb + off) = part ? lo : hi;
     }
 }
@@ -471,15 +592,18 @@ bool tc_supported(Ctx* c) {
 }
 
 static size_t tc_smem_bytes(int m, int atom_cap) {
-    return 1024 + ((size_t)1 << m) * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 128 * 8 * 4 +
-           256;
+    const size_t nbc = std::min<size_t>((size_t)1 << m, kChunkBins);
+    return 1024 + nbc * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 2 * kDirs * 8 +
+           128 * 8 * 4 + 256;
 }
 
 // Build the B operand for the current ROI bands and pick the TMEM size.
 int prepare_tc(Ctx* c) {
     if (!tc_supported(c)) return set_error(c, APTIDX_E_INVALID_ARG, "tensor-core path needs an sm_103 device");
     const int NB = 1 << c->m;
-    const int KB = NB / 128;   // 1 KB blocks of 64 K rows, K = NB / 2
+    const int NBc = std::min(NB, kChunkBins);
+    const int nchunk = NB / NBc;
+    const int KB = NBc / 128;   // 1 KB blocks of 64 K rows per chunk, K = NBc / 2
     const int kbase = c->band_min;
     const int ng = (c->band_max - kbase) / 4 + 1;
     const int gb = kBtBytes / (2 * KB * 1024);
@@ -501,11 +625,11 @@ int prepare_tc(Ctx* c) {
         dev_free(c->d_twb);
         c->d_twb = nullptr;
         c->twb_key[0] = c->twb_key[1] = c->twb_key[2] = -1;
-        const size_t bytes = (size_t)2 * ng * KB * 1024;
+        const size_t bytes = (size_t)nchunk * 2 * ng * KB * 1024;
         int rc = dev_alloc(c, &c->d_twb, bytes);
         if (rc) return rc;
-        k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)ng * NB * 8 + 255) / 256, 4096), 256, 0, c->stream>>>(
-            (uint8_t*)c->d_twb, c->m, kbase, ng);
+        k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)nchunk * ng * NBc * 8 + 255) / 256, 4096), 256, 0,
+                      c->stream>>>((uint8_t*)c->d_twb, c->m, kbase, ng);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(c, e, "twiddle operand");
         c->launches += 1;
@@ -521,10 +645,6 @@ int prepare_tc(Ctx* c) {
 
 cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* hist_out, int64_t hist_roi) {
     cudaError_t e;
-    // ROIs above 2048 atoms: FP32 kernel (no-op when there are none)
-    if (!hist_out) {
-        if ((e = launch_signatures_plain(c, S, argk, nullptr, -1, kRanksBig)) != cudaSuccess) return e;
-    }
     static int max_optin = -1;
     if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     const size_t base = tc_smem_bytes(c->m, 0);
@@ -536,15 +656,17 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     auto kern = multi ? k_sig_tc<APTIDX_MAX_BANDS> : k_sig_tc<1>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
+    // antipodal pairs (one projection per pair) unless switched off or exporting
+    const bool pairs = !hist_out && c->use_pairs && c->d_slot_idx;
     TcParams p;
     p.atoms = c->d_atoms;
     p.off = c->d_off;
     p.nw = c->d_nw;
     p.order = c->d_order;
-    p.n_big = c->d_counter + 1;
-    p.dirs = c->d_dirs;
+    p.dirs = pairs ? c->d_slot_dirs : c->d_dirs;
+    p.slot_idx = pairs ? c->d_slot_idx : nullptr;
     p.nv = c->nv;
-    p.tiles_per_roi = c->nv_pad / kDirs;
+    p.tiles_per_roi = (pairs ? c->nslot_pad : c->nv_pad) / kDirs;
     p.tiles_per_item = std::min(std::max(c->tune_tpi[1], 1), p.tiles_per_roi);
     p.items_per_roi = (p.tiles_per_roi + p.tiles_per_item - 1) / p.tiles_per_item;
     p.nroi = c->rank_limit > 0 ? std::min<int64_t>(c->nroi, c->rank_limit) : c->nroi;
@@ -573,7 +695,7 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, items);
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, kThreads, smem, c->stream>>>(p);
-    c->launches += hist_out ? 0 : 1;   // the FP32 launch above is counted by the caller's phase count
+    c->launches += hist_out ? 0 : 1;
     return cudaGetLastError();
 }
 

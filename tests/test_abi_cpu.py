@@ -63,12 +63,12 @@ def test_band_for_spacing_matches_oracle(lib):
     oracle's band arithmetic, and its argument checks."""
     import oracle
     import synth
-    for R, m in [(1.0, 8), (2.0, 10), (1.37, 9)]:
+    for R, m in [(1.0, 8), (2.0, 10), (1.37, 9), (2.5, 11), (3.1, 12)]:
         for d in [0.2025, 0.2029, 0.25]:
             lo, hi = synth.band_spacing(d)
             assert apt.aptidx_band_for_spacing(lo, hi, R, m) == oracle.band_for_spacing(lo, hi, R, m)
     assert apt.band_for_spacing is apt.aptidx_band_for_spacing
     for bad in [(0.0, 0.2, 2.0, 10), (0.3, 0.2, 2.0, 10), (0.2, 0.3, 0.0, 10), (0.2, 0.3, 2.0, 7),
-                (0.2, 0.3, 2.0, 11), (1e-4, 2e-4, 2.0, 8)]:   # the last band exceeds 2^(m-1)
+                (0.2, 0.3, 2.0, 13), (1e-4, 2e-4, 2.0, 8)]:   # the last band exceeds 2^(m-1)
         with pytest.raises(apt.AptidxError):
             apt.aptidx_band_for_spacing(*bad)

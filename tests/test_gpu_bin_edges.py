@@ -16,7 +16,7 @@ from test_oracle_pins import bin_edge_positions
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("m, R", [(8, 1.0), (10, 2.0), (10, 2.37)])
+@pytest.mark.parametrize("m, R", [(8, 1.0), (10, 2.0), (10, 2.37), (11, 2.0), (12, 3.1)])
 @pytest.mark.parametrize("path", [apt.APTIDX_PATH_PLAIN_FP32, apt.APTIDX_PATH_TC_FP16])
 def test_histograms_bit_exact_at_bin_edges(torch_cuda, m, R, path):
     torch = torch_cuda

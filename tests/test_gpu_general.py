@@ -1,0 +1,159 @@
+"""GPU parity of the general signature paths against the FP64 oracle:
+
+  - 2^11 and 2^12 bins (Section 2.2 gives m in [8, 12]): the kernels build
+    each histogram in chunks of 1024 bins; histograms bit-exact on both paths,
+    signatures within 1e-3 (FP32) and 5e-3 (tensor cores);
+  - ROIs of 2049, about 1e4 and about 7e4 atoms: the tensor-core kernel
+    contracts blocks of at most 2048 atoms (every count exact in fp16), the
+    FP32 kernel accumulates its spectrum over blocks of at most 65535 atoms;
+    atom counts and histograms bit-exact, signatures within tolerance;
+  - antipodal pairs: with the direction set closed under negation the
+    tensor-core path projects one direction of a pair; its results equal those
+    of projecting every direction (APTIDX_DIRECT) within FP32 rounding, the
+    pair members carry the same value, and a ROI with atoms whose bin product
+    is an exact integer (where the mirror image of the histogram is not the
+    histogram of -u) still matches the oracle direction by direction.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2009_00735_gb300 as apt
+
+from test_gpu_plain import TOL_PLAIN, gpu_signatures, make_ctx, roi_error, torch_cuda  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+TOL_TC = 5e-3
+PLAIN, TC = apt.APTIDX_PATH_PLAIN_FP32, apt.APTIDX_PATH_TC_FP16
+PATHS = [(PLAIN, TOL_PLAIN), (TC, TOL_TC)]
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.tiny_fcc()
+
+
+@pytest.mark.parametrize("m", [11, 12])
+@pytest.mark.parametrize("path,tol", PATHS)
+def test_many_bins(torch_cuda, tiny, m, path, tol):
+    dirs = np.ascontiguousarray(tiny.dirs[:1500])
+    ctx, band, mm, d = make_ctx(torch_cuda, tiny, dirs=dirs, m=m)
+    assert mm == m
+    nroi, nv = tiny.centres.shape[0], d.shape[0]
+    for roi in (0, 9):
+        h = np.empty((nv, 1 << m), np.uint16)
+        apt.aptidx_get_histograms(ctx.handle, roi, path, h)
+        _, xc = oracle.gather(tiny.xyz, tiny.centres[roi], tiny.radii[roi])
+        assert np.array_equal(h.astype(np.int64), oracle.histograms(xc, d, m, tiny.radii[roi]).astype(np.int64))
+    S, A, N = gpu_signatures(torch_cuda, ctx, nroi, nv, path=path)
+    So, Ao, No = oracle.signatures(tiny.xyz, tiny.centres, tiny.radii, band[0], band[1], d, m)
+    assert np.array_equal(N, No)
+    assert roi_error(S, So).max() <= tol
+    assert (A == Ao).mean() > 0.99
+    # a wide band: several frequency-group batches (tensor cores) or rounds (FP32)
+    apt.aptidx_set_binning(ctx.handle, m, 5, 100)
+    apt.aptidx_set_rois(ctx.handle, tiny.centres[:4], tiny.radii[:4])
+    S, _, _ = gpu_signatures(torch_cuda, ctx, 4, nv, path=path)
+    So, _, _ = oracle.signatures(tiny.xyz, tiny.centres[:4], tiny.radii[:4], 5, 100, d, m)
+    assert roi_error(S, So).max() <= tol
+    ctx.close()
+
+
+def big_rois():
+    """A noisy f.c.c. block and three ROIs whose radii fall between the
+    distances of consecutive atoms, so that they hold exactly 2049, 10000 and
+    70000 atoms."""
+    rng = np.random.default_rng(21)
+    q = synth.random_quaternions(rng, 1)[0]
+    xyz, t = synth.lattice_box("fcc", 0.404, (-7.4, -7.4, -7.4), (7.4, 7.4, 7.4), rot=synth.quat_to_matrix(q),
+                               origin=np.zeros(3))
+    xyz = (xyz.astype(np.float64) + rng.normal(0.0, 0.03, xyz.shape)).astype(np.float32)
+    centres = np.array([[0.11, -0.07, 0.05], [-0.2, 0.13, 0.31], [0.02, 0.04, -0.06]])
+    radii = []
+    for c, n in zip(centres, (2049, 10000, 70000)):
+        d = np.sort(np.sqrt(((xyz.astype(np.float64) - c) ** 2).sum(axis=1)))
+        radii.append(0.5 * (d[n - 1] + d[n]))
+    return np.ascontiguousarray(xyz), centres, np.array(radii)
+
+
+@pytest.mark.parametrize("path,tol", PATHS)
+def test_large_rois(torch_cuda, path, tol):
+    torch = torch_cuda
+    xyz, centres, radii = big_rois()
+    dirs = np.ascontiguousarray(synth.icosphere(2))    # 162 directions, closed under negation
+    m = 10
+    band = oracle.band_for_spacing(0.9 * 0.202, 1.1 * 0.202, float(radii[0]), m)
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(dirs).cuda())
+    apt.aptidx_set_binning(h, m, band[0], band[1])
+    apt.aptidx_set_rois(h, centres, radii)
+    nv = dirs.shape[0]
+    S, A, N = gpu_signatures(torch, ctx, 3, nv, path=path)
+    assert list(N) == [2049, 10000, 70000]
+    So, Ao, No = oracle.signatures(xyz, centres, radii, band[0], band[1], dirs, m)
+    assert np.array_equal(N, No)
+    assert roi_error(S, So).max() <= tol
+    for roi in range(3):
+        hg = np.empty((nv, 1 << m), np.uint16)
+        apt.aptidx_get_histograms(h, roi, path, hg)
+        _, xc = oracle.gather(xyz, centres[roi], radii[roi])
+        ho = oracle.histograms(xc, dirs, m, radii[roi])
+        assert ho.max() < 65536
+        assert np.array_equal(hg.astype(np.int64), ho.astype(np.int64))
+    ctx.close()
+
+
+def test_antipodal_pairs_match_direct(torch_cuda, tiny):
+    ctx, band, m, d = make_ctx(torch_cuda, tiny)
+    nroi, nv = tiny.centres.shape[0], d.shape[0]
+    S, A, N = gpu_signatures(torch_cuda, ctx, nroi, nv, path=TC)
+    Sd, Ad, _ = gpu_signatures(torch_cuda, ctx, nroi, nv, path=TC, flags=apt.APTIDX_DIRECT)
+    assert roi_error(S, Sd).max() <= 1e-5
+    assert (A == Ad).mean() > 0.999
+    So, _, _ = oracle.signatures(tiny.xyz, tiny.centres, tiny.radii, band[0], band[1], d, m)
+    assert roi_error(S, So).max() <= TOL_TC and roi_error(Sd, So).max() <= TOL_TC
+    # every node of the icosphere has its exact antipode; for noisy atoms no
+    # bin product is an integer, so the pair carries one value
+    key = {tuple((d[i] + np.float32(0)).tolist()): i for i in range(nv)}
+    j = np.array([key[tuple((-d[i] + np.float32(0)).tolist())] for i in range(nv)])
+    assert np.array_equal(S, S[:, j]) and np.array_equal(A, A[:, j])
+    ctx.close()
+
+
+def test_antipodal_pairs_with_integer_products(torch_cuda):
+    """Atoms on the plane x = 0 through the ROI centre project to exactly 0
+    along (1, 0, 0), an integer bin product: the histogram along (-1, 0, 0) is
+    then not the mirror image of the one along (1, 0, 0), and the kernel must
+    project (-1, 0, 0) itself.  Checked against the oracle direction by
+    direction, with and without pairing."""
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    yz = (rng.random((40, 2)) - 0.5) * 1.2
+    on_plane = np.column_stack([np.zeros(40), yz])
+    off_plane = np.column_stack([np.full(25, 0.3), (rng.random((25, 2)) - 0.5) * 1.2])
+    rest = (rng.random((300, 3)) - 0.5) * 1.6
+    xyz = np.ascontiguousarray(np.concatenate([on_plane, off_plane, rest]).astype(np.float32))
+    u = rng.standard_normal((40, 3))
+    u = u / np.linalg.norm(u, axis=1, keepdims=True)
+    half = np.concatenate([[[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]], u]).astype(np.float32)
+    dirs = np.ascontiguousarray(np.concatenate([half, -half]))
+    m, band = 8, (3, 9)
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(dirs).cuda())
+    apt.aptidx_set_binning(h, m, band[0], band[1])
+    apt.aptidx_set_rois(h, np.zeros((1, 3)), np.array([1.0]))
+    nv = dirs.shape[0]
+    So, Ao, _ = oracle.signatures(xyz, np.zeros((1, 3)), np.array([1.0]), band[0], band[1], dirs, m)
+    # the mirror image would differ along -x: the oracle's -x signature is not the +x one
+    assert So[0, 0] != So[0, 42]
+    for flags in (0, apt.APTIDX_DIRECT):
+        S, A, _ = gpu_signatures(torch, ctx, 1, nv, path=TC, flags=flags)
+        assert roi_error(S, So).max() <= TOL_TC
+        assert np.abs(S[0] - So[0]).max() <= 1e-5 * So[0].max()
+    ctx.close()

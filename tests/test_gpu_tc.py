@@ -111,9 +111,10 @@ def test_tc_edge_cases(tc, tiny, case):
     ctx.close()
 
 
-def test_tc_routes_large_rois_to_fp32(tc):
-    """ROIs above 2048 atoms run on the FP32 kernel within the same call;
-    the others on the tensor cores.  Both match the oracle."""
+def test_tc_large_rois_in_atom_blocks(tc):
+    """ROIs above 2048 atoms run on the tensor cores in blocks of at most 2048
+    atoms (every count of a block exact in fp16), contracted into the same
+    accumulators; ROIs of both kinds in one call match the oracle."""
     xyz, t = synth.perfect_crystal_roi("fcc", 0.404, 2.7)
     rng = np.random.default_rng(2)
     xyz = (xyz.astype(np.float64) + rng.normal(0, 0.02, xyz.shape)).astype(np.float32)

@@ -130,7 +130,7 @@ def bin_edge_positions(m, R, n=40, seed=0):
     return np.array(xs, np.float32)
 
 
-@pytest.mark.parametrize("m, R", [(8, 1.0), (10, 2.0), (10, 2.37)])
+@pytest.mark.parametrize("m, R", [(8, 1.0), (10, 2.0), (10, 2.37), (11, 2.0), (12, 3.1)])
 def test_bin_contract_at_bin_edges(m, R):
     """Atoms on and one ulp around bin edges (projection along a coordinate
     axis, so s is the coordinate itself): the oracle's contract equals the
