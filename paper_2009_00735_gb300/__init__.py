@@ -26,7 +26,7 @@ __all__ = [
     "band_for_spacing", "aptidx_band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
-    "APTIDX_NORMALISE_MAX", "APTIDX_AUTOTUNE", "APTIDX_GRAPH", "aptidx_get_tuning",
+    "APTIDX_NORMALISE_MAX", "APTIDX_AUTOTUNE", "APTIDX_GRAPH", "APTIDX_DIRECT", "aptidx_get_tuning",
 ]
 
 APTIDX_OK = 0
@@ -47,6 +47,7 @@ APTIDX_PATH_TC_FP16 = 1
 APTIDX_NORMALISE_MAX = 1
 APTIDX_AUTOTUNE = 2
 APTIDX_GRAPH = 4
+APTIDX_DIRECT = 8
 
 _ERR_NAMES = {1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "OVERFLOW", 6: "STATE"}
 
@@ -265,7 +266,7 @@ def aptidx_compute_signatures(ctx, path: int, flags: int, S=None, argk=None, n_a
     """Signatures of every ROI on `path` (APTIDX_PATH_PLAIN_FP32 or
     APTIDX_PATH_TC_FP16): S [nroi, nv] float32, argk [nroi, nv] uint16 and
     n_atoms [nroi] int32 (each optional, host or device); flags:
-    APTIDX_NORMALISE_MAX | APTIDX_AUTOTUNE | APTIDX_GRAPH."""
+    APTIDX_NORMALISE_MAX | APTIDX_AUTOTUNE | APTIDX_GRAPH | APTIDX_DIRECT."""
     pS, mS = _out(S, np.float32)
     pA, mA = _out(argk, np.uint16)
     pN, mN = _out(n_atoms, np.int32)

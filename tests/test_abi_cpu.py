@@ -72,3 +72,20 @@ def test_band_for_spacing_matches_oracle(lib):
                 (0.2, 0.3, 2.0, 13), (1e-4, 2e-4, 2.0, 8)]:   # the last band exceeds 2^(m-1)
         with pytest.raises(apt.AptidxError):
             apt.aptidx_band_for_spacing(*bad)
+
+
+def test_binding_constants_match_header():
+    """Every numeric #define of include/aptidx.h that a caller passes or
+    receives (status codes, memory spaces, paths, flags, limits) exists in the
+    binding with the header's value."""
+    src = open(HEADER).read()
+    defs = dict(re.findall(r"^#define\s+(APTIDX_\w+)\s+\(?([0-9]+)u?\)?", src, re.M))
+    assert len(defs) > 20
+    must = [n for n in defs if n.startswith(("APTIDX_E_", "APTIDX_MEM_", "APTIDX_PATH_"))] + [
+        "APTIDX_OK", "APTIDX_NORMALISE_MAX", "APTIDX_AUTOTUNE", "APTIDX_GRAPH", "APTIDX_DIRECT", "APTIDX_MAX_TOPK",
+        "APTIDX_MAX_BANDS"]
+    for n in must:
+        assert hasattr(apt, n), n
+    for n, v in defs.items():
+        if hasattr(apt, n):
+            assert getattr(apt, n) == int(v), n
