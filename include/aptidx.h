@@ -294,6 +294,29 @@ int aptidx_match(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, in
 int aptidx_match_topk(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nroi, int32_t topk, int32_t* best,
                       float* score, int mem);
 
+/* Phase and orientation from several signatures per candidate (Section 2.3,
+ * "Indexing": every ROI's signatures are compared with the rotated references
+ * of every crystal-structure candidate; the supplement's Al-Li-Mg-Ag case
+ * compares three reference patterns, one for pure Al and one for each
+ * sub-lattice of Al3Li, each probed in its own plane-spacing band).
+ * Candidate c owns the signature channels j in [cand_off[c], cand_off[c+1]);
+ * channel j compares the measured signatures S[sig[j]] (S: n_sig x nroi x nv
+ * FP32, normalised, the layout of aptidx_compute_signatures_multi) with the
+ * reference of slot ref[j] (aptidx_set_reference; its look-up table built by
+ * aptidx_build_lut on one orientation set shared by every slot used).
+ *   Delta_c(g) = (1 / n_c) sum_j Delta_ref[j](g),  n_c = cand_off[c+1] - cand_off[c],
+ * with Delta of Eq. 3 accumulated in FP32 (channels in j order).
+ * best[c * nroi + roi] = argmin_g Delta_c(g) (ties: lowest g);
+ * score[c * nroi + roi] = Delta_c(best); phase[roi] = the candidate with the
+ * lowest score (ties: lowest c).  cand_off, ref, sig: host arrays
+ * (1 <= n_cand <= 8, every candidate at least one channel); S, phase, best,
+ * score (each output may be NULL) in `mem`.  Scores of a chunk of ROIs are
+ * staged on the device (at most 1 GiB, library-owned).  Errors: INVALID_ARG,
+ * STATE, OOM, CUDA. */
+int aptidx_match_phase(aptidx_ctx* ctx, int32_t n_cand, const int32_t* cand_off, const int32_t* ref,
+                       const int32_t* sig, int32_t n_sig, const float* S, int64_t nroi, int32_t* phase, int32_t* best,
+                       float* score, int mem);
+
 /* ---- orientation refinement ------------------------------------------------ */
 
 /* Loss and gradient of the misfit between measured signatures and the

@@ -111,6 +111,8 @@ def _declare(L):
     L.orc_lut.argtypes = [_p, _i64, _p, C.c_int, _p, _i64, _p, C.c_int]
     L.orc_match.restype = None
     L.orc_match.argtypes = [_p, _i64, _i64, _p, _p, C.c_int, _p, _i64, _p, _p, _p, C.c_int]
+    L.orc_match_phase.restype = None
+    L.orc_match_phase.argtypes = [_p, _i64, _i64, C.c_int, _p, _p, _p, _p, C.c_int, _p, _i64, _p, _p, _p, C.c_int]
     L.orc_fsp.restype = None
     L.orc_fsp.argtypes = [_p, _i64, C.c_int, _d, _p, _i64, _p]
     L.orc_bilinear.restype = C.c_int
@@ -326,6 +328,33 @@ def match(S_msr, S_ref, top, lut_, return_scores=False, threads=0):
     lib().orc_match(_ptr(S), nroi, nv, _ptr(ref), _ptr(top), top.shape[0], _ptr(L), ng, _ptr(best),
                     _ptr(bs), _ptr(sc), threads)
     return (best, bs, sc) if return_scores else (best, bs)
+
+
+def match_phase(S, off, sig, refs, tops, luts, threads=0):
+    """Phase and orientation from several signatures per candidate (Eq. 3
+    averaged over a candidate's channels, FP64).  S: float32 [n_sig, nroi,
+    nv] measured signatures; candidate c owns channels off[c] .. off[c+1]-1;
+    channel j compares S[sig[j]] with reference refs[j] (float32 [nv]) at its
+    strongest nodes tops[j] (int32 [n_hat], one n_hat for all) through its
+    look-up table luts[j] (int32 [ng, n_hat], one orientation set).
+    Returns (phase int32 [nroi], best int32 [n_cand, nroi], score float64
+    [n_cand, nroi])."""
+    S = _c(S, np.float32)
+    n_sig, nroi, nv = S.shape
+    off = _c(off, np.int32)
+    sig = _c(sig, np.int32)
+    n_cand = off.shape[0] - 1
+    refs = _c(np.stack(refs), np.float32)
+    tops = _c(np.stack(tops), np.int32)
+    luts = _c(np.stack(luts), np.int32)
+    n_hat = tops.shape[1]
+    ng = luts.shape[1]
+    phase = np.empty(nroi, np.int32)
+    best = np.empty((n_cand, nroi), np.int32)
+    score = np.empty((n_cand, nroi), np.float64)
+    lib().orc_match_phase(_ptr(S), nroi, nv, n_cand, _ptr(off), _ptr(sig), _ptr(refs), _ptr(tops), n_hat,
+                          _ptr(luts), ng, _ptr(phase), _ptr(best), _ptr(score), threads)
+    return phase, best, score
 
 
 # ---------------------------------------------------------------- refinement

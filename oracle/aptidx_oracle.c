@@ -472,6 +472,58 @@ void orc_match(const float* S_msr, int64_t nroi, int64_t nv, const float* S_ref,
     }
 }
 
+/* Phase and orientation from several signatures per candidate (Section 2.3
+ * "Indexing": every ROI's signatures are compared with the rotated references
+ * of every crystal-structure candidate; the supplement's Al-Li-Mg-Ag case
+ * compares three reference patterns, one for pure Al and one for each
+ * sub-lattice of Al3Li).  Candidate c owns the signature channels
+ * j in [off[c], off[c+1]); channel j compares the measured signatures
+ * S + sig[j] * nroi * nv (layout [signature][roi][node]) with reference j:
+ * values S_ref + j * nv, strongest nodes top + j * n_hat, look-up table
+ * lut + j * ng * n_hat, all tables on one set of ng test orientations.
+ *   Delta_c(g) = (1 / n_c) sum_j Delta_j(g),  n_c = off[c+1] - off[c],
+ * with Delta_j of Eq. 3 (FP64).  best[c * nroi + r] = argmin_g Delta_c(g)
+ * (ties: lowest g), score[c * nroi + r] = Delta_c(best); phase[r] = the
+ * candidate of the lowest score (ties: lowest c). */
+void orc_match_phase(const float* S, int64_t nroi, int64_t nv, int n_cand, const int32_t* off, const int32_t* sig,
+                     const float* S_ref, const int32_t* top, int n_hat, const int32_t* lut, int64_t ng,
+                     int32_t* phase, int32_t* best, double* score, int threads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : omp_get_max_threads())
+#endif
+    for (int64_t r = 0; r < nroi; ++r) {
+        double bsc = INFINITY;
+        int32_t bc = 0;
+        for (int c = 0; c < n_cand; ++c) {
+            const int nc = off[c + 1] - off[c];
+            double bs = INFINITY;
+            int32_t bg = 0;
+            for (int64_t g = 0; g < ng; ++g) {
+                double tot = 0.0;
+                for (int j = off[c]; j < off[c + 1]; ++j) {
+                    const float* s = S + ((int64_t)sig[MUT(23, off[c], j)] * nroi + r) * nv;
+                    const float* ref = S_ref + (int64_t)j * nv;
+                    const int32_t* tp = top + (int64_t)j * n_hat;
+                    const int32_t* lt = lut + ((int64_t)j * ng + g) * n_hat;
+                    double acc = 0.0;
+                    for (int k = 0; k < n_hat; ++k) {
+                        const double d = (double)s[lt[k]] - (double)ref[tp[k]];
+                        acc += d * d;
+                    }
+                    tot += acc;
+                }
+                const double dc = MUT(22, tot, tot / (double)nc);
+                if (dc < bs) { bs = dc; bg = (int32_t)g; }
+            }
+            best[(int64_t)c * nroi + r] = bg;
+            score[(int64_t)c * nroi + r] = bs;
+            if (bs < bsc) { bsc = bs; bc = c; }
+        }
+        phase[r] = bc;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Orientation refinement (Gauss-Newton on a bilinear elevation-azimuth      */
 /* reference image).  The paper motivates refining the indexing (Section     */

@@ -22,7 +22,7 @@ __all__ = [
     "aptidx_version", "aptidx_create", "aptidx_destroy", "aptidx_last_error", "aptidx_sync",
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
-    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_compute_fsp", "aptidx_refine_loss", "aptidx_refine",
+    "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_match_phase", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_compute_fsp", "aptidx_refine_loss", "aptidx_refine",
     "band_for_spacing", "aptidx_band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
@@ -82,6 +82,7 @@ _SIGS = {
     "aptidx_match": (C.c_int, [_vp, _i32, _vp, _i64, _vp, _vp, C.c_int]),
     "aptidx_match_topk": (C.c_int, [_vp, _i32, _vp, _i64, _i32, _vp, _vp, C.c_int]),
     "aptidx_compute_fsp": (C.c_int, [_vp, C.c_int32, C.c_double, _vp, C.c_int]),
+    "aptidx_match_phase": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp, C.c_int]),
     "aptidx_refine_roi_grid": (C.c_int, [_vp, _vp, _i64, C.c_float, C.c_double, _i32, _vp, _vp, _i64, _vp,
                                          C.c_int]),
     "aptidx_compute_signatures_multi": (C.c_int, [_vp, C.c_int, C.c_uint, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -391,6 +392,29 @@ def aptidx_match_topk(ctx, cand: int, S, topk: int, best, score=None):
     ps, ms = _out(score, np.float32)
     nroi = best.shape[0]
     _check(ctx, load().aptidx_match_topk(ctx, cand, pS, nroi, int(topk), pb, ps, _one_mem(mS, mb, ms)))
+
+
+def aptidx_match_phase(ctx, cand_off, ref, sig, S, phase=None, best=None, score=None):
+    """Phase and orientation from several signatures per candidate: candidate
+    c owns channels cand_off[c] .. cand_off[c+1]-1 (host sequences), channel j
+    compares S[sig[j]] (S [n_sig, nroi, nv] float32, normalised) with the
+    reference of slot ref[j].  Outputs: phase [nroi] int32, best and score
+    [n_cand, nroi] (int32, float32); any may be None."""
+    off = np.ascontiguousarray(np.asarray(cand_off, dtype=np.int32))
+    rf = np.ascontiguousarray(np.asarray(ref, dtype=np.int32))
+    sg = np.ascontiguousarray(np.asarray(sig, dtype=np.int32))
+    if rf.size != sg.size or off.size < 2 or off[-1] != rf.size:
+        raise ValueError("cand_off[-1] must equal the number of channels in ref and sig")
+    pS, mS, kS = _arg(S, np.float32)
+    if len(kS.shape) != 3:
+        raise ValueError("S must be [n_sig, nroi, nv]")
+    n_sig, nroi = int(kS.shape[0]), int(kS.shape[1])
+    pp, mp = _out(phase, np.int32)
+    pb, mb = _out(best, np.int32)
+    ps, ms = _out(score, np.float32)
+    _check(ctx, load().aptidx_match_phase(ctx, off.size - 1, off.ctypes.data_as(_vp), rf.ctypes.data_as(_vp),
+                                          sg.ctypes.data_as(_vp), n_sig, pS, nroi, pp, pb, ps,
+                                          _one_mem(mS, mp, mb, ms)))
 
 
 def aptidx_refine_loss(ctx, cand: int, S, q0, loss, grad=None, omega=None):

@@ -1209,6 +1209,91 @@ int aptidx_match_topk(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nro
     return APTIDX_OK;
 }
 
+int aptidx_match_phase(aptidx_ctx* ctx, int32_t n_cand, const int32_t* cand_off, const int32_t* ref,
+                       const int32_t* sig, int32_t n_sig, const float* S, int64_t nroi, int32_t* phase, int32_t* best,
+                       float* score, int mem) {
+    CTX_OR_FAIL(ctx);
+    int rc;
+    if ((rc = check_mem(c, mem))) return rc;
+    if (n_cand < 1 || n_cand > kMaxCandidates || !cand_off || !ref || !sig || !S || nroi <= 0 || n_sig < 1)
+        return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: need 1 <= n_cand <= %d, offsets, slots, S, nroi > 0",
+                         kMaxCandidates);
+    if (!phase && !best && !score) return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: no output");
+    if (cand_off[0] != 0) return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: cand_off[0] must be 0");
+    for (int32_t k = 0; k < n_cand; ++k)
+        if (cand_off[k + 1] <= cand_off[k] || cand_off[k + 1] > 64)
+            return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: candidate %d needs 1..64 channels", k);
+    const int32_t n_ch = cand_off[n_cand];
+    int64_t ng = -1;
+    for (int32_t j = 0; j < n_ch; ++j) {
+        if ((rc = check_ref(c, ref[j], true, false))) return rc;
+        if (sig[j] < 0 || sig[j] >= n_sig)
+            return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: channel %d reads signature %d of %d", j, sig[j],
+                             n_sig);
+        if (ng >= 0 && c->ref[ref[j]].ng != ng)
+            return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: the look-up tables hold different orientation sets");
+        ng = c->ref[ref[j]].ng;
+    }
+    static int max_optin = -1;
+    if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    for (int32_t j = 0; j < n_ch; ++j)
+        if (((size_t)c->nv + c->ref[ref[j]].n_hat) * sizeof(float) > (size_t)max_optin)
+            return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: %d directions do not fit one shared-memory row",
+                             c->nv);
+    DevTmp tS, tp, tb, ts, tn, tbw, tsw;
+    const float* dS;
+    int32_t *dp, *db, *dn;
+    float* ds;
+    const size_t nout = (size_t)n_cand * nroi;
+    if ((rc = dev_view(c, S, (size_t)n_sig * nroi * c->nv, mem, tS, &dS))) return rc;
+    if ((rc = dev_out(c, phase, (size_t)nroi, mem, tp, &dp))) return rc;
+    if ((rc = dev_out(c, best, nout, mem, tb, &db))) return rc;
+    if ((rc = dev_out(c, score, nout, mem, ts, &ds))) return rc;
+    if (!db && (rc = dev_alloc(c, &tbw.p, nout * sizeof(int32_t)))) return rc;
+    if (!db) db = static_cast<int32_t*>(tbw.p);
+    if (!ds && (rc = dev_alloc(c, &tsw.p, nout * sizeof(float)))) return rc;
+    if (!ds) ds = static_cast<float*>(tsw.p);
+    std::vector<int32_t> nc((size_t)n_cand);
+    for (int32_t k = 0; k < n_cand; ++k) nc[k] = cand_off[k + 1] - cand_off[k];
+    if ((rc = dev_alloc(c, &tn.p, nc.size() * sizeof(int32_t)))) return rc;
+    dn = static_cast<int32_t*>(tn.p);
+    APTIDX_CUDA(c, cudaMemcpyAsync(dn, nc.data(), nc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    // channel sums of a chunk of ROIs (at most 1 GiB), then the argmin per ROI
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nroi, ((int64_t)1 << 30) / (ng * 4)));
+    const size_t need = (size_t)chunk * ng * sizeof(float);
+    if (need > c->match_scratch_bytes) {
+        free_ptr(c->d_match_scratch);
+        c->match_scratch_bytes = 0;
+        if ((rc = dev_alloc(c, (void**)&c->d_match_scratch, need))) return rc;
+        c->match_scratch_bytes = need;
+    }
+    prof_begin(c, APTIDX_PHASE_MATCH);
+    int launches = 0;
+    for (int32_t k = 0; k < n_cand; ++k) {
+        for (int64_t r0 = 0; r0 < nroi; r0 += chunk) {
+            const int64_t n = std::min(chunk, nroi - r0);
+            cudaError_t e = cudaSuccess;
+            for (int32_t j = cand_off[k]; j < cand_off[k + 1] && e == cudaSuccess; ++j) {
+                e = launch_match(c, &c->ref[ref[j]], dS + ((int64_t)sig[j] * nroi + r0) * c->nv, n, nullptr, nullptr,
+                                 c->d_match_scratch, j > cand_off[k]);
+                ++launches;
+            }
+            if (e == cudaSuccess)
+                e = launch_topk(c, c->d_match_scratch, ng, n, 1, db + (int64_t)k * nroi + r0, ds + (int64_t)k * nroi + r0);
+            if (e != cudaSuccess) return cuda_check(c, e, "match_phase");
+            ++launches;
+        }
+    }
+    cudaError_t e = launch_phase(c, ds, dn, n_cand, nroi, dp);
+    if (e != cudaSuccess) return cuda_check(c, e, "match_phase");
+    prof_end(c, APTIDX_PHASE_MATCH, launches + 1);
+    if ((rc = copy_back(c, phase, dp, (size_t)nroi, mem))) return rc;
+    if ((rc = copy_back(c, best, db, nout, mem))) return rc;
+    if ((rc = copy_back(c, score, ds, nout, mem))) return rc;
+    APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));   // the temporaries are freed on return
+    return read_status(c);
+}
+
 // Several signatures per ROI: signatures are grouped by type mask (one gather
 // each) and their bands by up to APTIDX_MAX_BANDS per contraction; the ROI
 // band of a pass spans the union of its bands, the kernels' epilogue takes

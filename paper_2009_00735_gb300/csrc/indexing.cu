@@ -209,12 +209,13 @@ __device__ __forceinline__ void lut_accumulate(const uint4 w, const float* row, 
     }
 }
 
-// With scores_out, Delta(g) of ROI r also goes to scores_out[r * ng + g].
+// With scores_out, Delta(g) of ROI r also goes to scores_out[r * ng + g]
+// (accumulate: added to the value there, for sums over signature channels).
 template <typename IdxT>
 __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, int64_t nroi, int32_t nv,
                                                 const IdxT* __restrict__ lut_t, int64_t ng, int64_t ng_pad,
                                                 const float* __restrict__ top_val, int32_t n_hat, int32_t* best,
-                                                float* score, float* scores_out) {
+                                                float* score, float* scores_out, bool accumulate) {
     constexpr int G = 16 / (int)sizeof(IdxT);
     extern __shared__ float sm[];
     float* row = sm;                     // nv
@@ -253,7 +254,10 @@ __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, 
             if (scores_out) {
 #pragma unroll
                 for (int e = 0; e < G; ++e)
-                    if (g0 + e < ng) scores_out[r * ng + g0 + e] = acc[e];
+                    if (g0 + e < ng) {
+                        float* o = scores_out + r * ng + g0 + e;
+                        *o = accumulate ? *o + acc[e] : acc[e];
+                    }
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -779,7 +783,7 @@ cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_
 
 template <typename IdxT>
 static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
-                                  float* scores_out) {
+                                  float* scores_out, bool accumulate) {
     constexpr int G = 16 / (int)sizeof(IdxT);
     const size_t smem = ((size_t)c->nv + r->n_hat) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_match<IdxT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -793,14 +797,39 @@ static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t 
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, nroi);
     k_match<IdxT><<<(unsigned)grid, threads, smem, c->stream>>>(S, nroi, c->nv, static_cast<const IdxT*>(r->d_lut),
                                                                 r->ng, r->ng_pad, r->d_top_val, r->n_hat, best, score,
-                                                                scores_out);
+                                                                scores_out, accumulate);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
-                         float* scores_out) {
-    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score, scores_out)
-                             : launch_match_t<int32_t>(c, r, S, nroi, best, score, scores_out);
+                         float* scores_out, bool accumulate) {
+    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score, scores_out, accumulate)
+                             : launch_match_t<int32_t>(c, r, S, nroi, best, score, scores_out, accumulate);
+}
+
+// Phase decision: candidate c's summed channel scores divided by its channel
+// count n_c (in place), then phase[r] = the candidate of the lowest score
+// (ties: lowest c).
+__global__ void k_phase(float* score, const int32_t* n_ch, int32_t n_cand, int64_t nroi, int32_t* phase) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nroi; r += (int64_t)gridDim.x * blockDim.x) {
+        float bs = INFINITY;
+        int32_t bc = 0;
+        for (int c = 0; c < n_cand; ++c) {
+            const float v = score[(int64_t)c * nroi + r] / (float)n_ch[c];
+            score[(int64_t)c * nroi + r] = v;
+            if (v < bs) {
+                bs = v;
+                bc = c;
+            }
+        }
+        if (phase) phase[r] = bc;
+    }
+}
+
+cudaError_t launch_phase(Ctx* c, float* score, const int32_t* n_ch, int32_t n_cand, int64_t nroi, int32_t* phase) {
+    const int64_t grid = std::min<int64_t>((nroi + 255) / 256, (int64_t)c->sm_count * 8);
+    k_phase<<<(unsigned)grid, 256, 0, c->stream>>>(score, n_ch, n_cand, nroi, phase);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_topk(Ctx* c, const float* scores, int64_t ng, int64_t nroi, int32_t topk, int32_t* best,

@@ -212,7 +212,8 @@ size_t plain_smem_bytes(int m, int atom_cap);
 cudaError_t launch_top_nodes(Ctx* c, Reference* r);
 cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng);
 cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
-                         float* scores_out = nullptr);
+                         float* scores_out = nullptr, bool accumulate = false);
+cudaError_t launch_phase(Ctx* c, float* score, const int32_t* n_ch, int32_t n_cand, int64_t nroi, int32_t* phase);
 cudaError_t launch_topk(Ctx* c, const float* scores, int64_t ng, int64_t nroi, int32_t topk, int32_t* best,
                         float* score);
 cudaError_t launch_lut_export(Ctx* c, Reference* r, int32_t* out);

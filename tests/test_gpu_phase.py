@@ -1,0 +1,189 @@
+"""Phase identification from several signatures per candidate (Section 2.3,
+"Indexing"; the supplement's Al-Li-Mg-Ag case compares one reference for pure
+Al and one per sub-lattice of Al3Li, each in its own plane-spacing band):
+aptidx_match_phase against the FP64 oracle, and the fraction of ROIs whose
+lowest candidate score picks the true structure on two workloads.
+
+Candidates and their signature channels (type mask, plane family):
+  b.c.c. (a = 0.287 nm): all atoms {110}, all atoms {200};
+  f.c.c. (a = 0.405 nm): all atoms {200}, all atoms {111};
+  L1_2 Al3Sc (a = 0.410 nm): Sc sub-lattice {100}, Sc sub-lattice {110}
+  (the ordered sub-lattice, as the supplement's Li sub-lattice of Al3Li).
+Each band is the family's spacing +/- 10 %; references are the library's
+signatures of perfect crystals at identity orientation, centred on a site.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2009_00735_gb300 as apt
+
+from test_gpu_plain import torch_cuda  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+ALL, SC = 0xFFFFFFFF, 1 << 1
+CHANNELS = {   # name: (lattice, a, type mask, plane spacing)
+    "bcc110": ("bcc", 0.287, ALL, 0.287 / np.sqrt(2)),
+    "bcc200": ("bcc", 0.287, ALL, 0.287 / 2),
+    "fcc200": ("fcc", 0.405, ALL, 0.405 / 2),
+    "fcc111": ("fcc", 0.405, ALL, 0.405 / np.sqrt(3)),
+    "l12sc100": ("l12", 0.410, SC, 0.410),
+    "l12sc110": ("l12", 0.410, SC, 0.410 / np.sqrt(2)),
+}
+CANDIDATES = {"bcc": ["bcc110", "bcc200"], "fcc": ["fcc200", "fcc111"], "l12": ["l12sc100", "l12sc110"]}
+
+
+def band(d, R, m):
+    return oracle.band_for_spacing(*synth.band_spacing(d), R, m)
+
+
+def reference(torch, name, R, dirs, m):
+    kind, a, mask, d = CHANNELS[name]
+    xyz, t = synth.perfect_crystal_roi(kind, a, R + 0.5)
+    b = band(d, R, m)
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda(), torch.from_numpy(t).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(dirs).cuda())
+    apt.aptidx_set_binning(h, m, b[0], b[1])
+    apt.aptidx_set_rois(h, np.zeros((1, 3)), np.array([R]), type_mask=mask)
+    node = torch.empty((1, dirs.shape[0]), dtype=torch.float32, device="cuda")
+    apt.aptidx_compute_signatures(h, apt.APTIDX_PATH_TC_FP16, apt.APTIDX_NORMALISE_MAX, node, None, None)
+    apt.aptidx_sync(h)
+    ctx.close()
+    return node.reshape(-1).contiguous()
+
+
+def identify(torch, w, centres, radii, cands, grid, n_hat=1000):
+    """Phase of every ROI: the candidates' channels as one multi-signature
+    call, one reference slot per channel, one look-up table per slot on the
+    shared orientation set, then aptidx_match_phase."""
+    names = [ch for cs in cands.values() for ch in cs]
+    R = float(radii[0])
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(w.xyz).cuda(), torch.from_numpy(w.types).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(w.dirs).cuda())
+    lo = min(band(CHANNELS[n][3], R, w.m)[0] for n in names)
+    hi = max(band(CHANNELS[n][3], R, w.m)[1] for n in names)
+    apt.aptidx_set_binning(h, w.m, lo, hi)
+    apt.aptidx_set_rois(h, torch.from_numpy(centres).cuda(), torch.from_numpy(radii).cuda())
+    nroi, nv = centres.shape[0], w.dirs.shape[0]
+    S = torch.empty((len(names), nroi, nv), dtype=torch.float32, device="cuda")
+    masks = [CHANNELS[n][2] for n in names]
+    bands = [band(CHANNELS[n][3], R, w.m) for n in names]
+    apt.aptidx_compute_signatures_multi(h, apt.APTIDX_PATH_TC_FP16, apt.APTIDX_NORMALISE_MAX, masks,
+                                        [b[0] for b in bands], [b[1] for b in bands], S)
+    for j, n in enumerate(names):
+        apt.aptidx_set_reference(h, j, reference(torch, n, R, w.dirs, w.m), n_hat)
+        apt.aptidx_build_lut(h, j, torch.from_numpy(grid).cuda())
+    off = np.concatenate([[0], np.cumsum([len(cs) for cs in cands.values()])])
+    phase = torch.empty(nroi, dtype=torch.int32, device="cuda")
+    score = torch.empty((len(cands), nroi), dtype=torch.float32, device="cuda")
+    apt.aptidx_match_phase(h, off, np.arange(len(names)), np.arange(len(names)), S, phase, None, score)
+    apt.aptidx_sync(h)
+    ctx.close()
+    return phase.cpu().numpy(), score.cpu().numpy()
+
+
+def test_match_phase_parity(torch_cuda):
+    """aptidx_match_phase against oracle.match_phase (with the oracle's own
+    look-up tables): scores within FP32 summation error, the chosen g's
+    oracle score equal to the oracle's minimum, the same phase."""
+    torch = torch_cuda
+    u = synth.icosphere(3)
+    fams = [synth.family_100(), synth.family_110()]
+    refs = []
+    for f in fams:
+        r = synth.bump_values(f, 12.0, u)
+        refs.append((r / r.max()).astype(np.float32))
+    n_hat = 60
+    rng = np.random.default_rng(17)
+    Q = synth.so3_grid(8.0)
+    S = []
+    for f in (fams[0], fams[1], fams[0]):
+        rows = []
+        for _ in range(10):
+            G = synth.quat_to_matrix(synth.random_quaternions(rng, 1)[0])
+            s = synth.bump_values(f @ G.T, 12.0, u) + 0.05 * rng.random(u.shape[0])
+            rows.append(s / s.max())
+        S.append(rows)
+    S = np.ascontiguousarray(np.array(S, np.float32))          # [3 signatures, 10 ROIs, nv]
+    # candidate 0: reference 0 on signature 0; candidate 1: references 1, 0 on signatures 1, 2
+    off, ref_of, sig = [0, 1, 3], [0, 1, 0], [0, 1, 2]
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_set_directions(h, torch.from_numpy(u).cuda())
+    for slot, r in enumerate(refs):
+        apt.aptidx_set_reference(h, slot, torch.from_numpy(r).cuda(), n_hat)
+        apt.aptidx_build_lut(h, slot, torch.from_numpy(Q).cuda())
+    phase = np.empty(10, np.int32)
+    best = np.empty((2, 10), np.int32)
+    score = np.empty((2, 10), np.float32)
+    apt.aptidx_match_phase(h, off, ref_of, sig, S, phase, best, score)
+    ctx.close()
+    tops = [oracle.top_nodes(r, n_hat) for r in refs]
+    luts = [oracle.lut(u, t, Q) for t in tops]
+    po, bo, so = oracle.match_phase(S, off, sig, [refs[i] for i in ref_of], [tops[i] for i in ref_of],
+                                    [luts[i] for i in ref_of])
+    assert np.allclose(score, so, rtol=2e-5, atol=2e-5)
+    # every g's Delta_c from the oracle's Eq. 3 per channel; the oracle's
+    # Delta_c at the GPU's choice is the oracle's minimum
+    full = []
+    for c in range(2):
+        chans = [oracle.match(S[sig[j]], refs[ref_of[j]], tops[ref_of[j]], luts[ref_of[j]],
+                              return_scores=True)[2] for j in range(off[c], off[c + 1])]
+        full.append(sum(chans) / len(chans))
+    for c in range(2):
+        at = full[c][np.arange(10), best[c]]
+        assert np.all(np.abs(at - so[c]) <= 2e-5 * so[c] + 2e-5)
+    gap = np.abs(so[0] - so[1]) > 1e-4 * np.maximum(so[0], so[1]) + 1e-4
+    assert gap.sum() >= 8
+    assert np.array_equal(phase[gap], po[gap])
+
+
+def test_phase_bcc_box(torch_cuda):
+    """The b.c.c. single-crystal box (16384 ROIs of R = 2 nm, the refinement
+    workload): at least 90 % of the ROIs pick b.c.c."""
+    torch = torch_cuda
+    w = synth.single_crystal_bcc(grid=(16, 32, 32))
+    assert w.centres.shape[0] == 16384
+    phase, score = identify(torch, w, w.centres, w.radii, CANDIDATES, synth.so3_grid(5.0))
+    frac = {n: float((phase == i).mean()) for i, n in enumerate(CANDIDATES)}
+    print(f"\nb.c.c. box, 16384 ROIs: phase fractions {frac}; median scores {np.median(score, axis=1)}")
+    assert frac["bcc"] >= 0.9
+
+
+def test_phase_polycrystal(torch_cuda):
+    """The reduced polycrystal (f.c.c. Al grains with L1_2 Al3Sc
+    precipitates): ROIs of R = 1.8 nm lying wholly inside a precipitate or
+    wholly in the matrix; at least 90 % of each kind pick their structure
+    (L1_2 and f.c.c.)."""
+    torch = torch_cuda
+    w = synth.polycrystal(box=(24.0, 24.0, 48.0), n_grains=16, n_roi=10, level=5, m=10)
+    R = 1.8
+    rng = np.random.default_rng(7)
+    inside, matrix = [], []
+    for c, r in w.truth["spheres"]:
+        if r >= R + 0.2:
+            for _ in range(6):   # a few centres per precipitate, each ROI wholly inside it
+                off = rng.standard_normal(3)
+                inside.append(c + off / np.linalg.norm(off) * rng.random() * (r - R - 0.1))
+    box = np.array([24.0, 24.0, 48.0])
+    while len(matrix) < 200:
+        c = R + rng.random(3) * (box - 2 * R)
+        if all(np.linalg.norm(c - cp) > rp + R + 0.3 for cp, rp in w.truth["spheres"]):
+            matrix.append(c)
+    centres = np.ascontiguousarray(np.array(inside + matrix))
+    radii = np.full(centres.shape[0], R)
+    truth = np.array([1] * len(inside) + [0] * len(matrix))
+    cands = {"fcc": CANDIDATES["fcc"], "l12": CANDIDATES["l12"]}
+    phase, score = identify(torch, w, centres, radii, cands, synth.so3_grid(5.0))
+    f_prec = float((phase[truth == 1] == 1).mean())
+    f_mat = float((phase[truth == 0] == 0).mean())
+    print(f"\npolycrystal: {len(inside)} ROIs in precipitates pick L1_2 for {f_prec:.3f}, {len(matrix)} ROIs in the "
+          f"matrix pick f.c.c. for {f_mat:.3f}")
+    assert len(inside) >= 20
+    assert f_prec >= 0.9 and f_mat >= 0.9

@@ -223,7 +223,7 @@ def test_invalid_arguments(torch_cuda, tiny):
     with pytest.raises(apt.AptidxError):
         apt.aptidx_set_directions(h, tiny.dirs * 1.01)
     apt.aptidx_set_directions(h, tiny.dirs)
-    for m, lo, hi in [(7, 1, 2), (11, 1, 2), (8, 5, 4), (8, 0, 129)]:
+    for m, lo, hi in [(7, 1, 2), (13, 1, 2), (8, 5, 4), (8, 0, 129)]:
         with pytest.raises(apt.AptidxError) as ei:
             apt.aptidx_set_binning(h, m, lo, hi)
         assert ei.value.code == apt.APTIDX_E_INVALID_ARG
@@ -240,9 +240,10 @@ def test_invalid_arguments(torch_cuda, tiny):
 
 
 def test_roi_atom_limit(torch_cuda):
-    """A ROI above 65535 selected atoms is refused with OVERFLOW."""
+    """A ROI above APTIDX_MAX_ATOMS_PER_ROI (2^24 - 1) selected atoms is
+    refused with OVERFLOW."""
     rng = np.random.default_rng(0)
-    xyz = (rng.random((70000, 3)) * 0.5).astype(np.float32)
+    xyz = (rng.random((1 << 24, 3), dtype=np.float32) * np.float32(0.5))
     ctx = apt.Context(0)
     h = ctx.handle
     apt.aptidx_load_positions(h, xyz)

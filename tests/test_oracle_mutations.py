@@ -34,6 +34,10 @@ MUTANTS = {
     19: ("atom type bits read one position off", "test_gather_type_mask", {}),
     20: ("reference nodes rotated by the transposed matrix", "test_lut_is_nearest_node", {}),
     21: ("DFT twiddle angles over N_b - 1 instead of N_b", "test_spectrum_matches_numpy_rfft", {"m": 8}),
+    22: ("candidate score summed over its channels instead of averaged",
+         "test_match_phase_reduces_to_eq3_and_averages_channels", {}),
+    23: ("every channel of a candidate reads the measured signature of its first channel",
+         "test_match_phase_recovers_planted_candidate", {}),
 }
 
 

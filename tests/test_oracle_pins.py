@@ -476,6 +476,66 @@ def test_match_recovers_planted_orientation():
     assert sc[0, g] == pytest.approx(float(np.sum((msr[0, L[g]].astype(float) - ref[top]) ** 2)), rel=1e-12)
 
 
+def _phase_case():
+    """Three references (bumps around <100>, <110>, <111>) on a level-3
+    icosphere, 40 strongest nodes each, 60 test orientations."""
+    u = synth.icosphere(3)
+    fam = [synth.family_100(), synth.family_110(),
+           np.array([[1, 1, 1], [1, 1, -1], [1, -1, 1], [-1, 1, 1]], float) / np.sqrt(3)]
+    fam[2] = np.concatenate([fam[2], -fam[2]])
+    refs = []
+    for f in fam:
+        r = synth.bump_values(f, 12.0, u)
+        refs.append((r / r.max()).astype(np.float32))
+    n_hat = 40
+    tops = [oracle.top_nodes(r, n_hat) for r in refs]
+    rng = np.random.default_rng(9)
+    Q = np.concatenate([[[1.0, 0, 0, 0]], synth.random_quaternions(rng, 59)])
+    luts = [oracle.lut(u, t, Q) for t in tops]
+    return u, refs, tops, luts, rng
+
+
+def test_match_phase_reduces_to_eq3_and_averages_channels():
+    """A one-channel candidate gives Eq. 3's argmin and minimum; a candidate
+    of two identical channels gives the same score (the channels' mean, not
+    their sum); equal candidates resolve to the lower index."""
+    u, refs, tops, luts, rng = _phase_case()
+    S = rng.random((2, 5, u.shape[0])).astype(np.float32)
+    off = [0, 1, 3, 5]
+    sig = [0, 1, 1, 1, 1]
+    R = [refs[0], refs[1], refs[1], refs[1], refs[1]]
+    T = [tops[0], tops[1], tops[1], tops[1], tops[1]]
+    L = [luts[0], luts[1], luts[1], luts[1], luts[1]]
+    phase, best, score = oracle.match_phase(S, off, sig, R, T, L)
+    b0, s0 = oracle.match(S[0], refs[0], tops[0], luts[0])
+    b1, s1 = oracle.match(S[1], refs[1], tops[1], luts[1])
+    assert np.array_equal(best[0], b0) and np.allclose(score[0], s0, rtol=1e-12)
+    for c in (1, 2):
+        assert np.array_equal(best[c], b1) and np.allclose(score[c], s1, rtol=1e-12)
+    assert np.all(phase != 2)          # candidates 1 and 2 tie: the lower index wins
+    assert np.array_equal(phase, np.where(score[1] < score[0], 1, 0))
+
+
+def test_match_phase_recovers_planted_candidate():
+    """Measured signatures holding candidate 1's references at the look-up
+    nodes of g* in both of its channels: candidate 1 scores Delta(g*) = 0 and
+    is the phase; candidate 0 (one channel, another reference) scores above 0."""
+    u, refs, tops, luts, rng = _phase_case()
+    ng = luts[0].shape[0]
+    gstar = next(g for g in range(5, ng) if len(np.unique(luts[1][g])) == len(tops[1])
+                 and len(np.unique(luts[2][g])) == len(tops[2]))
+    S = np.full((3, 4, u.shape[0]), 0.05, np.float32)
+    for r in range(4):
+        S[1, r, luts[1][gstar]] = refs[1][tops[1]]
+        S[2, r, luts[2][gstar]] = refs[2][tops[2]]
+    off = [0, 1, 3]
+    sig = [0, 1, 2]
+    phase, best, score = oracle.match_phase(S, off, sig, [refs[0], refs[1], refs[2]], [tops[0], tops[1], tops[2]],
+                                            [luts[0], luts[1], luts[2]])
+    assert np.all(best[1] == gstar) and np.all(score[1] == 0.0)
+    assert np.all(score[0] > 0.0) and np.all(phase == 1)
+
+
 def test_match_topk_orders_solutions():
     """Top-k of Eq. 3: the planted orientation first with Delta = 0, then the
     rest ascending by (Delta, g) as a brute-force ranking of the hand-computed
