@@ -51,10 +51,13 @@ def parse():
     ap.add_argument("--path", default="auto", choices=["auto", "tc", "plain"])
     ap.add_argument("--cpu-rois", type=int, default=0, help="oracle sample size (0: sized for ~15 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bcc", choices=["bcc", "polycrystal", "wideband"],
-                    help="bcc: the timed step; polycrystal: signature throughput of both paths on the "
-                         "uneven-ROI polycrystal (1e5 ROIs, per-ROI bands), not a step; wideband: signature "
-                         "throughput of both paths on the b.c.c. box with the band k = 8..128, not a step")
+    ap.add_argument("--workload", default="bcc", choices=["bcc", "polycrystal", "wideband", "large"],
+                    help="bcc: the timed step (the default line also carries the three measurements below); "
+                         "polycrystal: signature throughput of both paths on the uneven-ROI polycrystal "
+                         "(1e5 ROIs, per-ROI bands); wideband: the same on the b.c.c. box with the band "
+                         "k = 8..128; large: the same for ROIs of R = 4 and 8 nm in the b.c.c. box")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the polycrystal, wide-band and large-ROI measurements of the default line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-paper-index", action="store_true",
                     help="skip the paper-scale indexing measurement (618324 orientations, top-1000)")
@@ -481,6 +484,15 @@ def run_gb300(args):
         fsp["l512"] = l512
         apt.aptidx_set_rois(h, torch.from_numpy(w.centres).cuda(), torch.from_numpy(w.radii).cuda())
 
+    # the other workloads, signature calls only (not part of the step): the
+    # uneven-ROI polycrystal, the wide band k = 8..128, ROIs of R = 4 and 8 nm
+    secondary = None
+    if world == 1 and not args.no_secondary:
+        sw, ss = 2, 2
+        secondary = {"large_rois": measure_large_rois(w, sw, ss),
+                     "wideband": measure_wideband(w, sw, ss),
+                     "polycrystal": measure_polycrystal(sw, ss)}
+
     # roofline of the dominant kernel (the signature kernel of the headline path)
     sig_ms = prof["signature"][0] / max(prof["signature"][1], 1)
     K = band[1] - band[0] + 1
@@ -535,6 +547,7 @@ def run_gb300(args):
                          "median_coarse_match_deg": float(np.median(mis_coarse))},
             "paper_scale_indexing": paper_index,
             "fsp": fsp,
+            "secondary": secondary,
             "roofline": roof,
             "clocks": clk,
             "gpu_launches": int(launches),
@@ -547,7 +560,33 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def run_polycrystal(args):
+def time_both_paths(apt, torch, h, stream, S, warmup, steps, extra=None):
+    """Signature calls of both paths (autotuned launch, graph replay), timed
+    with CUDA events on the library's stream; `extra(name, ms)` adds keys."""
+    out = {}
+    flags = apt.APTIDX_AUTOTUNE | apt.APTIDX_GRAPH
+    for name, code in (("plain", apt.APTIDX_PATH_PLAIN_FP32), ("tc", apt.APTIDX_PATH_TC_FP16)):
+        for _ in range(warmup):
+            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
+        apt.aptidx_sync(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        tpi, iss = apt.aptidx_get_tuning(h, code)
+        r = {"ms_per_call": ms, "value": S.shape[0] * S.shape[1] / (ms / 1e3),
+             "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
+        if extra:
+            r.update(extra(name, ms))
+        out[name] = r
+    return out
+
+
+def measure_polycrystal(warmup, steps):
     """Signature throughput of both paths on the Voronoi polycrystal: 60 x 60 x
     120 nm, 200 f.c.c. grains with L1_2 precipitates (1.3e7 atoms), 1e5 ROIs
     with radii uniform in [1.0, 2.5] nm, per-ROI {200} bands, 40962
@@ -555,17 +594,14 @@ def run_polycrystal(args):
     import torch
     import synth
     import paper_2009_00735_gb300 as apt
-    from paper_2009_00735_gb300 import build as B
-    torch.cuda.set_device(0)
-    B.build()
+    t0 = time.perf_counter()
     w = synth.polycrystal()
+    gen_s = time.perf_counter() - t0
     nroi, nv = w.centres.shape[0], w.dirs.shape[0]
-    blo = np.empty(nroi, np.int32)
-    bhi = np.empty(nroi, np.int32)
-    for i, R in enumerate(w.radii):
-        blo[i], bhi[i] = apt.band_for_spacing(*w.d_spacing, float(R), w.m)
+    bands = np.array([apt.band_for_spacing(*w.d_spacing, float(R), w.m) for R in w.radii], np.int32)
+    blo, bhi = np.ascontiguousarray(bands[:, 0]), np.ascontiguousarray(bands[:, 1])
     stream = torch.cuda.current_stream()
-    ctx = apt.Context(0, stream)
+    ctx = apt.Context(torch.cuda.current_device(), stream)
     h = ctx.handle
     apt.aptidx_load_positions(h, torch.from_numpy(w.xyz).cuda(), torch.from_numpy(w.types).cuda())
     apt.aptidx_set_directions(h, torch.from_numpy(w.dirs).cuda())
@@ -577,50 +613,29 @@ def run_polycrystal(args):
     apt.aptidx_compute_signatures(h, apt.APTIDX_PATH_PLAIN_FP32, 0, S, None, N)
     apt.aptidx_sync(h)
     n_atoms = N.cpu().numpy().astype(np.int64)
-    out = {}
-    flags = apt.APTIDX_AUTOTUNE | apt.APTIDX_GRAPH
-    for name, code in (("plain", apt.APTIDX_PATH_PLAIN_FP32), ("tc", apt.APTIDX_PATH_TC_FP16)):
-        for _ in range(args.warmup):
-            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
-        apt.aptidx_sync(h)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        tpi, iss = apt.aptidx_get_tuning(h, code)
-        out[name] = {"ms_per_call": ms, "value": nroi * nv / (ms / 1e3),
-                     "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
-    print(json.dumps({
-        "metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "higher_is_better": True, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": w.name, "n_roi": nroi, "n_dir": nv, "bins": 1 << w.m, "atoms": int(w.xyz.shape[0]),
-                   "atoms_per_roi": {"mean": float(n_atoms.mean()), "min": int(n_atoms.min()),
-                                     "max": int(n_atoms.max()), "above_2048": int((n_atoms > 2048).sum())},
-                   "bands": [int(blo.min()), int(bhi.max())], "pairs": int(n_atoms.sum()) * nv},
-        "paths": out}))
+    paths = time_both_paths(apt, torch, h, stream, S, warmup, steps)
+    ctx.close()
+    del S
+    torch.cuda.empty_cache()
+    return {"workload": w.name, "n_roi": nroi, "n_dir": nv, "bins": 1 << w.m, "atoms": int(w.xyz.shape[0]),
+            "atoms_per_roi": {"mean": float(n_atoms.mean()), "min": int(n_atoms.min()),
+                              "max": int(n_atoms.max()), "above_2048": int((n_atoms > 2048).sum())},
+            "bands": [int(blo.min()), int(bhi.max())], "pairs": int(n_atoms.sum()) * nv,
+            "steps": steps, "warmup": warmup, "generate_s": gen_s, "paths": paths}
 
 
-def run_wideband(args):
+def measure_wideband(w, warmup, steps):
     """Signature throughput of both paths on the b.c.c. box (8192 ROIs,
     40962 directions, 2^10 bins) with the wide band k = 8..128 (121
     frequencies), where the spectrum contraction dominates; autotuned launch
     and graph replay."""
     import torch
-    import synth
     import paper_2009_00735_gb300 as apt
-    from paper_2009_00735_gb300 import build as B
-    torch.cuda.set_device(0)
-    B.build()
-    w = synth.single_crystal_bcc()
     nroi, nv, nb = w.centres.shape[0], w.dirs.shape[0], 1 << w.m
     k_lo, k_hi = 8, 128
     K = k_hi - k_lo + 1
     stream = torch.cuda.current_stream()
-    ctx = apt.Context(0, stream)
+    ctx = apt.Context(torch.cuda.current_device(), stream)
     h = ctx.handle
     apt.aptidx_load_positions(h, torch.from_numpy(w.xyz).cuda())
     apt.aptidx_set_directions(h, torch.from_numpy(w.dirs).cuda())
@@ -628,42 +643,77 @@ def run_wideband(args):
     apt.aptidx_set_rois(h, torch.from_numpy(w.centres).cuda(), torch.from_numpy(w.radii).cuda())
     S = torch.empty((nroi, nv), dtype=torch.float32, device="cuda")
     N = torch.empty(nroi, dtype=torch.int32, device="cuda")
-    apt.aptidx_compute_signatures(h, apt.APTIDX_PATH_TC_FP16, 0, S, None, N)
+    apt.aptidx_compute_signatures(h, apt.APTIDX_PATH_PLAIN_FP32, 0, S, None, N)
     apt.aptidx_sync(h)
     pairs = float(N.cpu().numpy().astype(np.int64).sum()) * nv
     tpeak = measured_peaks().get("bf16_tflops")
-    out = {}
-    flags = apt.APTIDX_AUTOTUNE | apt.APTIDX_GRAPH
-    for name, code in (("plain", apt.APTIDX_PATH_PLAIN_FP32), ("tc", apt.APTIDX_PATH_TC_FP16)):
-        for _ in range(args.warmup):
-            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
-        apt.aptidx_sync(h)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            apt.aptidx_compute_signatures(h, code, flags, S, None, None)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        tpi, iss = apt.aptidx_get_tuning(h, code)
-        r = {"ms_per_call": ms, "value": nroi * nv / (ms / 1e3), "tuning": {"tiles_per_item": tpi, "mma_issuers": iss}}
+
+    def extra(name, ms):
         if name == "plain":
             fl = 8.0 * pairs + 4.0 * nroi * nv * K * nb          # projection + FP32 DFT (2 FMA per dir, k, bin)
-            r["fp32"] = {"achieved": fl / (ms / 1e3) / 1e12, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": fl / (ms / 1e3) / 1e12 / ALU_PEAK_TFLOPS}
-        else:
-            tf = 2.0 * nroi * nv * nb * (2 * K) * 2               # hi + lo operands, executed
-            r["tensor"] = {"achieved": tf / (ms / 1e3) / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+            return {"fp32": {"achieved": fl / (ms / 1e3) / 1e12, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": fl / (ms / 1e3) / 1e12 / ALU_PEAK_TFLOPS}}
+        tf = 2.0 * nroi * nv * nb * (2 * K) * 2                   # hi + lo operands, every direction
+        return {"tensor": {"achieved": tf / (ms / 1e3) / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                            "frac": (tf / (ms / 1e3) / 1e12 / tpeak) if tpeak else None,
-                           "work": f"{tf:.3e} fp16 flop per call (2 x 2^m x 2K x 2, hi + lo), call time incl. gather"}
-        out[name] = r
-    print(json.dumps({
-        "metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "higher_is_better": True, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": w.name + "-band8-128", "n_roi": nroi, "n_dir": nv, "bins": nb, "band": [k_lo, k_hi],
-                   "pairs": pairs},
-        "paths": out}))
+                           "work": f"{tf:.3e} fp16 flop per call (2 x 2^m x 2K x 2, hi + lo, every direction), "
+                                   "call time incl. gather"}}
+
+    paths = time_both_paths(apt, torch, h, stream, S, warmup, steps, extra)
+    ctx.close()
+    del S
+    torch.cuda.empty_cache()
+    return {"workload": w.name + "-band8-128", "n_roi": nroi, "n_dir": nv, "bins": nb, "band": [k_lo, k_hi],
+            "pairs": pairs, "steps": steps, "warmup": warmup, "paths": paths}
+
+
+def measure_large_rois(w, warmup, steps):
+    """Signature throughput of both paths for ROIs of R = 4 nm and R = 8 nm
+    in the b.c.c. box (the paper benchmarks R = 2-8 nm at m = 10): 1024 and
+    128 ROIs on grids inside the box, 40962 directions, 2^10 bins, the
+    {110} band for the ROI radius."""
+    import torch
+    import synth
+    import paper_2009_00735_gb300 as apt
+    nv = w.dirs.shape[0]
+    stream = torch.cuda.current_stream()
+    out = {}
+    for R, grid, pitch in ((4.0, (8, 8, 16), 3.0), (8.0, (4, 4, 8), 6.0)):
+        centres = synth.roi_grid(grid, pitch, np.array([20.0, 20.0, 40.0]))
+        nroi = centres.shape[0]
+        radii = np.full(nroi, R)
+        band = apt.band_for_spacing(*w.d_spacing, R, w.m)
+        ctx = apt.Context(torch.cuda.current_device(), stream)
+        h = ctx.handle
+        apt.aptidx_load_positions(h, torch.from_numpy(w.xyz).cuda())
+        apt.aptidx_set_directions(h, torch.from_numpy(w.dirs).cuda())
+        apt.aptidx_set_binning(h, w.m, band[0], band[1])
+        apt.aptidx_set_rois(h, torch.from_numpy(centres).cuda(), torch.from_numpy(radii).cuda())
+        S = torch.empty((nroi, nv), dtype=torch.float32, device="cuda")
+        N = torch.empty(nroi, dtype=torch.int32, device="cuda")
+        apt.aptidx_compute_signatures(h, apt.APTIDX_PATH_PLAIN_FP32, 0, S, None, N)
+        apt.aptidx_sync(h)
+        n_atoms = N.cpu().numpy().astype(np.int64)
+        pairs = float(n_atoms.sum()) * nv
+        paths = time_both_paths(apt, torch, h, stream, S, warmup, steps,
+                                lambda name, ms: {"pairs_per_s": pairs / (ms / 1e3)})
+        ctx.close()
+        del S
+        out[f"R{R:.0f}nm"] = {"n_roi": nroi, "n_dir": nv, "bins": 1 << w.m, "band": list(band),
+                             "mean_atoms_per_roi": float(n_atoms.mean()), "max_atoms_per_roi": int(n_atoms.max()),
+                             "pairs": pairs, "paths": paths}
+    torch.cuda.empty_cache()
+    return out
+
+
+def print_secondary(args, fn, *a):
+    import torch
+    from paper_2009_00735_gb300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    r = fn(*a)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f16",
+                      "data": "synthetic", **r}))
 
 
 def main():
@@ -671,9 +721,13 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "polycrystal":
-        run_polycrystal(args)
+        print_secondary(args, measure_polycrystal, args.warmup, args.steps)
     elif args.workload == "wideband":
-        run_wideband(args)
+        import synth
+        print_secondary(args, measure_wideband, synth.single_crystal_bcc(), args.warmup, args.steps)
+    elif args.workload == "large":
+        import synth
+        print_secondary(args, measure_large_rois, synth.single_crystal_bcc(), args.warmup, args.steps)
     else:
         run_gb300(args)
 
