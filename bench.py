@@ -103,6 +103,54 @@ def measured_peaks():
         return {}
 
 
+def measure_l2_peak(torch):
+    """Read bandwidth of the L2 cache with torch's own kernels: a 24 MiB
+    float32 tensor (well inside the 129 MB L2) summed 100 times and copied
+    into a second 24 MiB tensor 100 times, after warm-up; the larger of the
+    two byte rates (copy: read + write) in GB/s."""
+    n = 24 * 1024 * 1024 // 4
+    x = torch.rand(n, device="cuda")
+    y = torch.empty_like(x)
+    out = {}
+    for name, fn, bytes_per in (("sum", lambda: x.sum(), 4 * n), ("copy", lambda: y.copy_(x), 8 * n)):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(100):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 100 * bytes_per / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del x, y
+    return {"gbs": max(out.values()), "sum_gbs": out["sum"], "copy_gbs": out["copy"],
+            "how": "torch sum and copy over a 24 MiB float32 tensor, 100 calls each after 10 warm-up, CUDA events"}
+
+
+def gather_rooflines(l2, match_ms, refine_ms, nroi, nv, ng, ng_pad, n_hat, lut_bytes, passes):
+    """Byte rates of the match and refinement kernels against the measured L2
+    peak.  Eq. 3 reads, per ROI, every look-up table entry (n_hat x n_g) from
+    L2 plus the ROI's signature row; a refinement pass reads, per direction,
+    the direction (16 B), the measured value (4 B) and four bilinear image
+    taps (16 B), the taps mostly from L1."""
+    peak = l2["gbs"] if l2 else None
+    mb = float(nroi) * (n_hat * ng_pad * lut_bytes + nv * 4)
+    rb = float(nroi) * nv * passes * (16 + 4 + 16)
+    out = {"l2_peak": l2}
+    for name, b, ms, what in (("k_match", mb, match_ms, f"{n_hat} x {ng_pad} table entries of {lut_bytes} B + "
+                                                          f"{nv} x 4 B signature row per ROI"),
+                              ("k_refine_gn", rb, refine_ms, f"{passes} passes x {nv} directions x 36 B per ROI "
+                                                             "(direction 16 B, value 4 B, four taps 16 B)")):
+        if not ms:
+            continue
+        gbs = b / (ms / 1e3) / 1e9
+        out[name] = {"bound": "l2", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (gbs / peak) if peak else None, "bytes_per_launch": b, "kernel_ms": ms, "bytes": what}
+    return out
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -522,6 +570,8 @@ def run_gb300(args):
             "work": f"{flop:.3e} algorithmic FP32 flop per launch"}
     if tensor:
         roof["tensor"] = tensor
+    gather = gather_rooflines(measure_l2_peak(torch), per_phase.get("match"), per_phase.get("refine"), nroi, nv,
+                              grid.shape[0], (grid.shape[0] + 7) // 8 * 8, n_hat, 2 if nv <= 65536 else 4, iters + 1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -549,6 +599,7 @@ def run_gb300(args):
             "fsp": fsp,
             "secondary": secondary,
             "roofline": roof,
+            "gather_rooflines": gather,
             "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,

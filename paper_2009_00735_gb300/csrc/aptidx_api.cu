@@ -181,22 +181,29 @@ static int build_grid(Ctx* c, double h) {
     int rc;
     if ((rc = dev_alloc(c, (void**)&c->d_cell_start, (n_cells + 1) * sizeof(int64_t)))) return rc;
     if ((rc = dev_alloc(c, (void**)&c->d_cell_pos, c->n_atoms * sizeof(float4)))) return rc;
-    if ((rc = ensure_scan_tmp(c, n_cells))) return rc;
-    int32_t *cell_of = nullptr, *cursor = nullptr, *idx = nullptr;
-    int64_t* counts = nullptr;
+    const size_t nh = cell_sort_hist_elems(c->n_atoms);
+    if ((rc = ensure_scan_tmp(c, std::max<int64_t>(n_cells, (int64_t)nh)))) return rc;
+    int32_t *cell_of = nullptr, *k2 = nullptr, *idx = nullptr, *v2 = nullptr;
+    int64_t *counts = nullptr, *hist = nullptr, *offs = nullptr;
     rc = dev_alloc(c, (void**)&cell_of, c->n_atoms * sizeof(int32_t));
-    if (!rc) rc = dev_alloc(c, (void**)&cursor, n_cells * sizeof(int32_t));
-    if (!rc) rc = dev_alloc(c, (void**)&counts, n_cells * sizeof(int64_t));
+    if (!rc) rc = dev_alloc(c, (void**)&k2, c->n_atoms * sizeof(int32_t));
     if (!rc) rc = dev_alloc(c, (void**)&idx, c->n_atoms * sizeof(int32_t));
+    if (!rc) rc = dev_alloc(c, (void**)&v2, c->n_atoms * sizeof(int32_t));
+    if (!rc) rc = dev_alloc(c, (void**)&counts, n_cells * sizeof(int64_t));
+    if (!rc) rc = dev_alloc(c, (void**)&hist, nh * sizeof(int64_t));
+    if (!rc) rc = dev_alloc(c, (void**)&offs, nh * sizeof(int64_t));
     if (!rc) {
-        cudaError_t e = launch_cell_build(c, cell_of, cursor, counts, idx);
+        cudaError_t e = launch_cell_build(c, cell_of, k2, idx, v2, counts, hist, offs);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = cuda_check(c, e, "cell grid build");
     }
     dev_free(cell_of);
-    dev_free(cursor);
-    dev_free(counts);
+    dev_free(k2);
     dev_free(idx);
+    dev_free(v2);
+    dev_free(counts);
+    dev_free(hist);
+    dev_free(offs);
     if (rc) free_grid(c);
     return rc;
 }

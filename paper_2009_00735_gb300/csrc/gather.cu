@@ -188,27 +188,71 @@ __global__ void k_cell_of(const float* __restrict__ pos, int64_t n, GridDesc g, 
     }
 }
 
-__global__ void k_cell_scatter(const int32_t* __restrict__ cell_of, int64_t n, const int64_t* __restrict__ start,
-                               int32_t* cursor, int32_t* idx) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int c = cell_of[i];
-        int k = atomicAdd(&cursor[c], 1);
-        idx[start[c] + k] = (int32_t)i;
+// Atom indices in cell order, ascending inside every cell: a stable
+// least-significant-digit radix sort of the cell ids (8 bits per pass) with
+// the atom index as value, starting from ascending indices.  A pass splits the
+// keys into tiles of kRsTile; k_rs_count counts each tile's digits,
+// an exclusive scan of the counts (digit-major) gives every (digit, tile) its
+// output offset, and k_rs_scatter writes each tile's keys in order: within a
+// chunk of 256 keys a key's position is its digit's running offset plus the
+// same-digit keys of lower lanes (warp match) and of lower warps.
+constexpr int kRsThreads = 256;
+constexpr int kRsChunks = 16;
+constexpr int kRsTile = kRsThreads * kRsChunks;
+constexpr int kRsWarps = kRsThreads / 32;
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_count(const int32_t* __restrict__ keys, int64_t n, int shift,
+                                                         int64_t ntiles, int64_t* hist) {
+    __shared__ int32_t h[256];
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t t0 = tile * kRsTile;
+        for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
+            const int64_t k = t0 + i;
+            if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255], 1);
+        }
+        __syncthreads();
+        hist[(int64_t)threadIdx.x * ntiles + tile] = h[threadIdx.x];
+        __syncthreads();
     }
 }
 
-// ascending atom index inside every cell (insertion sort; cells are small)
-__global__ void k_cell_sort(const int64_t* __restrict__ start, int64_t n_cells, int32_t* idx) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t a = start[c], b = start[c + 1];
-        for (int64_t i = a + 1; i < b; ++i) {
-            int32_t v = idx[i];
-            int64_t j = i - 1;
-            while (j >= a && idx[j] > v) {
-                idx[j + 1] = idx[j];
-                --j;
+// vin == nullptr: the values are the key positions (atom indices)
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const int32_t* __restrict__ kin,
+                                                           const int32_t* __restrict__ vin, int64_t n, int shift,
+                                                           int64_t ntiles, const int64_t* __restrict__ offs,
+                                                           int32_t* kout, int32_t* vout) {
+    __shared__ unsigned long long base[256];
+    __shared__ int32_t wcnt[kRsWarps][257];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kRsWarps * 257; i += kRsThreads) (&wcnt[0][0])[i] = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        base[tid] = (unsigned long long)offs[(int64_t)tid * ntiles + tile];
+        for (int ch = 0; ch < kRsChunks; ++ch) {
+            const int64_t k = tile * kRsTile + (int64_t)ch * kRsThreads + tid;
+            const bool valid = k < n;
+            const int32_t key = valid ? kin[k] : 0;
+            const int32_t val = valid ? (vin ? vin[k] : (int32_t)k) : 0;
+            const int d = valid ? ((key >> shift) & 255) : 256;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const bool leader = lane == __ffs(peers) - 1;
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            if (leader) wcnt[warp][d] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                long long pos = (long long)base[d] + rank;
+                for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+                kout[pos] = key;
+                vout[pos] = val;
             }
-            idx[j + 1] = v;
+            __syncthreads();
+            if (leader) {
+                if (valid) atomicAdd(&base[d], (unsigned long long)__popc(peers));
+                wcnt[warp][d] = 0;
+            }
+            __syncthreads();
         }
     }
 }
@@ -234,23 +278,39 @@ static GridDesc grid_desc(const Ctx* c) {
 }
 
 // Build the cell grid of the loaded positions for the cell size c->cell_h.
-// Scratch (caller-owned): cell_of [n] int32, cursor [n_cells] int32,
-// counts [n_cells] int64, idx [n] int32.
-cudaError_t launch_cell_build(Ctx* c, int32_t* d_cell_of, int32_t* d_cursor, int64_t* d_counts,
-                              int32_t* d_idx) {
+// Scratch (caller-owned): cell_of, k2, idx, v2 [n] int32, counts [n_cells]
+// int64, hist and offs [256 * ceil(n / kRsTile) + 1] int64.
+size_t cell_sort_hist_elems(int64_t n) { return (size_t)256 * (size_t)((n + kRsTile - 1) / kRsTile) + 1; }
+
+cudaError_t launch_cell_build(Ctx* c, int32_t* d_cell_of, int32_t* d_k2, int32_t* d_idx, int32_t* d_v2,
+                              int64_t* d_counts, int64_t* d_hist, int64_t* d_offs) {
     cudaStream_t s = c->stream;
     GridDesc g = grid_desc(c);
     const int64_t n = c->n_atoms;
     int blocks = (int)tmin<int64_t>((n + 255) / 256, 8192);
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_counts, 0, sizeof(int64_t) * c->n_cells, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * c->n_cells, s)) != cudaSuccess) return e;
     k_cell_of<<<blocks, 256, 0, s>>>(c->d_pos, n, g, d_cell_of, reinterpret_cast<unsigned long long*>(d_counts));
     if ((e = launch_scan_i64(d_counts, c->d_cell_start, c->n_cells, c->d_scan_tmp, s)) != cudaSuccess) return e;
-    k_cell_scatter<<<blocks, 256, 0, s>>>(d_cell_of, n, c->d_cell_start, d_cursor, d_idx);
-    int cblocks = (int)tmin<int64_t>((c->n_cells + 255) / 256, 8192);
-    k_cell_sort<<<cblocks, 256, 0, s>>>(c->d_cell_start, c->n_cells, d_idx);
-    k_cell_fill<<<blocks, 256, 0, s>>>(c->d_pos, c->d_types, d_idx, n, c->d_cell_pos);
+    // radix passes over the bits of the largest cell id
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < c->n_cells) ++bits;
+    const int passes = tmax(1, (bits + 7) / 8);
+    const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+    const unsigned rblocks = (unsigned)tmin<int64_t>(tmax<int64_t>(ntiles, 1), (int64_t)c->sm_count * 8);
+    const int32_t* kin = d_cell_of;
+    const int32_t* vin = nullptr;
+    int32_t* kbuf[2] = {d_k2, d_cell_of};
+    int32_t* vbuf[2] = {d_idx, d_v2};
+    for (int pass = 0; pass < passes && ntiles > 0; ++pass) {
+        k_rs_count<<<rblocks, kRsThreads, 0, s>>>(kin, n, 8 * pass, ntiles, d_hist);
+        if ((e = launch_scan_i64(d_hist, d_offs, 256 * ntiles, c->d_scan_tmp, s)) != cudaSuccess) return e;
+        k_rs_scatter<<<rblocks, kRsThreads, 0, s>>>(kin, vin, n, 8 * pass, ntiles, d_offs, kbuf[pass & 1],
+                                                    vbuf[pass & 1]);
+        kin = kbuf[pass & 1];
+        vin = vbuf[pass & 1];
+    }
+    k_cell_fill<<<blocks, 256, 0, s>>>(c->d_pos, c->d_types, vin, n, c->d_cell_pos);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,7 @@ struct Ctx {
     int tc_gb = 0;                     // frequency groups per B batch
     int tc_ng = 0;                     // groups in the global B operand
     uint32_t tc_tmem_cols = 0;
+    bool tc_wide = false;              // some ROI band spans more groups than one B batch
 
     // ROIs
     int64_t nroi = 0;
@@ -185,8 +186,9 @@ void dev_free(void* p);
 
 // launches (all async on c->stream) -----------------------------------------
 cudaError_t launch_bbox(const float* pos, int64_t n, float* d_minmax, cudaStream_t s);
-cudaError_t launch_cell_build(Ctx* c, int32_t* d_cell_of, int32_t* d_cursor, int64_t* d_counts,
-                              int32_t* d_idx);
+cudaError_t launch_cell_build(Ctx* c, int32_t* d_cell_of, int32_t* d_k2, int32_t* d_idx, int32_t* d_v2,
+                              int64_t* d_counts, int64_t* d_hist, int64_t* d_offs);
+size_t cell_sort_hist_elems(int64_t n);
 cudaError_t launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t s);
 size_t scan_tmp_elems(int64_t n);
 cudaError_t launch_gather_count(Ctx* c);

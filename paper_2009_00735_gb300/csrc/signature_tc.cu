@@ -50,7 +50,8 @@ constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDirs = kTileDirs;     // 64 directions per tile
 constexpr int kRows = 2 * kDirs;     // MMA M: (direction, bin half)
-constexpr int kBtBytes = 32 * 1024;  // shared-memory budget of the B operand
+constexpr int kBtBytes = 32 * 1024;  // shared-memory budget of the B operand (narrow bands)
+constexpr int kWideStage = 32 * 1024;   // wide bands: one of two twiddle stream stages
 constexpr int kExBytes = kDirs * 8 * 4;   // epilogue exchange: one group's (re, im) x 4 per direction
 constexpr int kIssuers = 4;          // at most this many warps issue MMAs, one TMEM partial accumulator each
 constexpr int kChunkBins = 1024;     // bins per histogram chunk (128 KB of words)
@@ -72,6 +73,9 @@ struct TcParams {
     int m;
     int32_t kbase;          // frequency of column group 0
     const uint8_t* twb;     // global B: [chunk][hi|lo][group][k-block] x 1 KB
+    const uint8_t* twk;     // global B, streamed layout: [chunk][k-block][hi|lo][group] x 1 KB (wide bands),
+                            // ng_total + 1 groups per run, the last one zero
+    int32_t bt_bytes;       // shared-memory bytes of the B region (kBtBytes, or 2 kWideStage)
     int32_t ng_total;
     int32_t gb;             // groups per shared-memory batch
     uint32_t tmem_cols;
@@ -124,21 +128,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     const int KB = NBc / 128;   // 1 KB K-blocks of the B operand per chunk (K = NBc / 2 rows)
     uint32_t* H = reinterpret_cast<uint32_t*>(smem);
     unsigned char* BT = smem + (size_t)NBc * 128;
-    float* EX = reinterpret_cast<float*>(BT + kBtBytes);   // [kDirs][8]
-    float4* A = reinterpret_cast<float4*>(BT + kBtBytes + kExBytes);
+    float* EX = reinterpret_cast<float*>(BT + p.bt_bytes);   // [kDirs][8]
+    float4* A = reinterpret_cast<float4*>(BT + p.bt_bytes + kExBytes);
     float4* DB = A + p.atom_cap;   // [2][kDirs]: this tile's directions and the next tile's
     int2* DI = reinterpret_cast<int2*>(DB + 2 * kDirs);   // [2][kDirs]: (output, partner) of those slots
     float* EX2 = reinterpret_cast<float*>(DI + 2 * kDirs);   // [128 TMEM lanes][8]: partials 2, 3
-    // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per issuer
+    // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per
+    // issuer, then the wide-band stream: two stage loads, two stage MMA completions
+    constexpr int kBars = 2 + kIssuers + 4;
     uint64_t* bars = reinterpret_cast<uint64_t*>(EX2 + 128 * 8);
-    int* flag = reinterpret_cast<int*>(bars + 2 + kIssuers);
-    int64_t* item_s = reinterpret_cast<int64_t*>(bars + 3 + kIssuers);
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + 4 + kIssuers);
-    int* iss_ok = reinterpret_cast<int*>(bars + 5 + kIssuers);   // [kIssuers]
+    uint64_t* wbar = bars + 2 + kIssuers;
+    int* flag = reinterpret_cast<int*>(bars + kBars);
+    int64_t* item_s = reinterpret_cast<int64_t*>(bars + kBars + 1);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + kBars + 2);
+    int* iss_ok = reinterpret_cast<int*>(bars + kBars + 3);   // [kIssuers]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
-        for (int i = 0; i < 2 + kIssuers; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
         fence_barrier_init();
     }
     for (int i = tid; i < NBc * 8; i += kThreads) reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
@@ -156,6 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     const uint32_t bt_addr = smem_u32(BT);
 
     uint32_t ph_atoms = 0, ph_b = 0, ph_mma = 0;   // ph_mma: this warp's issuer barrier
+    uint32_t wph = 0u, wdph = 0u;   // wide stream, thread 0: parity bits (bit i: buffer i) of stage loads, stage MMAs
     int cur_g0 = -1, cur_nb = -1, cur_bc = -1;     // B operand held in shared memory
     const float magic = bin_magic(p.m);
     const bool sym = p.slot_idx != nullptr;
@@ -264,28 +272,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // tcgen05.mma costs the issuing warp ~75 cycles whatever its N;
                     // several issuers overlap that cost); every pass after the first
                     // accumulates onto the result so far.
-                    const int n_iss = nbatch == 1 ? p.n_iss : 1;
+                    // Wide bands (more frequency groups than one B batch holds):
+                    // the twiddles of all the ROI's groups stream through two
+                    // 32 KB stages, one per (64-bin K block, hi|lo part), and every
+                    // group accumulates into tensor-memory columns 8 g .. 8 g + 7
+                    // (hi and lo products into the same columns) with one MMA of
+                    // N = 8 x groups per K step; a stage is refilled by the TMA engine
+                    // while the MMAs of the next stage run.
+                    const bool wide = nbatch > 1;
+                    const int n_iss = wide ? 1 : p.n_iss;
                     const uint32_t sbo_b = (uint32_t)KB * 1024u;
-                    const uint32_t cols_b = (uint32_t)(16 * p.gb);   // TMEM columns per accumulator
                     const bool issuer = lane == 0 && warp < n_iss;
                     const uint32_t acc0 = sub > 0 ? 1u : 0u;
+                    // N = 8 x groups must be a multiple of 16 (M = 128): an odd group
+                    // count takes one more group of twiddles (zeros past the last
+                    // group), whose columns are never read
+                    const int ngw = (ng + 1) & ~1;
+                    const uint32_t wbytes = (uint32_t)ngw * 1024u;
+                    auto wide_load = [&](int s) {   // stage s = 2 x K block + part, into buffer s & 1
+                        const int kb = s >> 1, part = s & 1;
+                        mbar_arrive_expect_tx(&wbar[part], wbytes);
+                        bulk_g2s(BT + (size_t)part * kWideStage,
+                                 p.twk + ((((size_t)bc * KB + kb) * 2 + part) * (p.ng_total + 1) + fg0) * 1024, wbytes,
+                                 &wbar[part]);
+                    };
                     int ok = 1;
                     if (tid == 0) {
-                        // B operand of batch 0 for this chunk (kept across tiles while
-                        // the ROI band and the chunk allow)
-                        const int nb0 = min(p.gb, fg1 + 1 - fg0);
-                        if (fg0 != cur_g0 || nb0 != cur_nb || bc != cur_bc) {
-                            const uint32_t part = (uint32_t)nb0 * KB * 1024u;
-                            mbar_arrive_expect_tx(&bars[1], 2 * part);
-                            bulk_g2s(BT, p.twb + ((size_t)(2 * bc) * p.ng_total + fg0) * KB * 1024, part, &bars[1]);
-                            bulk_g2s(BT + part, p.twb + ((size_t)(2 * bc + 1) * p.ng_total + fg0) * KB * 1024, part,
-                                     &bars[1]);
-                            ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
-                            if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
-                            ph_b ^= 1u;
-                            cur_g0 = ok ? fg0 : -1;
-                            cur_nb = nb0;
-                            cur_bc = bc;
+                        if (wide) {
+                            // the first two stages load while the histogram is swizzled
+                            // (the epilogue before wrote the B region through the
+                            // generic proxy)
+                            fence_proxy_async_smem();
+                            wide_load(0);
+                            wide_load(1);
+                            cur_g0 = -1;   // the narrow-band B operand is overwritten
+                        } else {
+                            // B operand of the band for this chunk (kept across tiles while
+                            // the ROI band and the chunk allow)
+                            const int nb0 = fg1 + 1 - fg0;
+                            if (fg0 != cur_g0 || nb0 != cur_nb || bc != cur_bc) {
+                                const uint32_t part = (uint32_t)nb0 * KB * 1024u;
+                                fence_proxy_async_smem();
+                                mbar_arrive_expect_tx(&bars[1], 2 * part);
+                                bulk_g2s(BT, p.twb + ((size_t)(2 * bc) * p.ng_total + fg0) * KB * 1024, part, &bars[1]);
+                                bulk_g2s(BT + part, p.twb + ((size_t)(2 * bc + 1) * p.ng_total + fg0) * KB * 1024, part,
+                                         &bars[1]);
+                                ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
+                                if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
+                                ph_b ^= 1u;
+                                cur_g0 = ok ? fg0 : -1;
+                                cur_nb = nb0;
+                                cur_bc = bc;
+                            }
                         }
                         *flag = ok;
                     }
@@ -310,14 +348,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     tc_fence_before();
                     __syncthreads();
                     ok = *flag;
-                    if (issuer && ok) {
+                    // A: rows 64-127 (second bin half) one swizzle atom along M
+                    // away, NBc / 2 bin rows of 128 bytes
+                    const uint64_t a0 = sdesc_sw128(h_addr, (uint32_t)NBc * 64u, 1024u);
+                    if (issuer && ok && wide) {
                         tc_fence_after();
-                        const int nb0 = min(p.gb, fg1 + 1 - fg0);
+                        const uint32_t idw = idesc_f16(8 * ngw);
+                        const int S = 2 * KB;
+                        for (int s = 0; s < S && ok; ++s) {
+                            const int kb = s >> 1, part = s & 1;
+                            if (!mbar_wait_bounded(&wbar[part], (wph >> part) & 1u, p.status)) {
+                                mbar_wait_bounded(&wbar[part], (wph >> part) & 1u, p.status, 1u << 20);
+                                ok = 0;
+                            }
+                            wph ^= 1u << part;
+                            if (!ok) break;
+                            tc_fence_after();
+                            // B: 8 x ng rows (4 frequencies x cos, sin per group) of
+                            // 64 bins, 1 KB per 8 rows; 32 bytes per K step
+                            const uint64_t b0 = sdesc_sw128(bt_addr + (uint32_t)part * kWideStage, 16u, 1024u);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = a0 + (uint64_t)((kb * 4 + kk) * 128);
+                                const uint64_t bd = b0 + (uint64_t)(kk * 2);
+                                mma_f16(tmem, ad, bd, idw, (s > 0 || kk > 0) ? 1u : acc0);
+                            }
+                            mma_commit(&wbar[2 + part]);
+                            if (s >= 1 && s + 1 < S) {
+                                // the stage before this one has been contracted once its
+                                // commit arrives; its buffer takes stage s + 1
+                                const int pp = (s - 1) & 1;
+                                if (!mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status)) {
+                                    mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status, 1u << 20);
+                                    ok = 0;
+                                }
+                                wdph ^= 1u << pp;
+                                if (ok) wide_load(s + 1);
+                            }
+                        }
+                        // the last two stages' MMAs
+                        for (int s = S - 2; s < S && ok; ++s) {
+                            const int pp = s & 1;
+                            if (!mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status)) {
+                                mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status, 1u << 20);
+                                ok = 0;
+                            }
+                            wdph ^= 1u << pp;
+                        }
+                    } else if (issuer && ok) {
+                        tc_fence_after();
+                        const int nb0 = fg1 + 1 - fg0;
                         const uint32_t idesc = idesc_f16(16 * nb0);
-                        const uint32_t dcol = tmem + (uint32_t)warp * cols_b;
-                        // A: rows 64-127 (second bin half) one swizzle atom along M
-                        // away, NBc / 2 bin rows of 128 bytes
-                        const uint64_t a0 = sdesc_sw128(h_addr, (uint32_t)NBc * 64u, 1024u);
+                        const uint32_t dcol = tmem + (uint32_t)warp * (uint32_t)(16 * p.gb);
                         const uint64_t b0 = sdesc_sw128(bt_addr, 16u, sbo_b);
                         // descriptors advance by constant steps: A by 2 KB per K step,
                         // B by 32 bytes inside a 128-byte row and 1 KB per 64-bin
@@ -327,41 +409,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
                             mma_f16(dcol, ad, bd, idesc, (kk >= n_iss) ? 1u : acc0);
                         }
-                        if (tid == 0 && nbatch > 1) {
-                            // wide band: further batches, each reloading the B buffer
-                            for (int b = 1; b < nbatch && ok; ++b) {
-                                mma_commit(&bars[2]);
-                                ok = mbar_wait_bounded(&bars[2], ph_mma, p.status) ? 1 : 0;
-                                ph_mma ^= 1u;
-                                if (!ok) break;
-                                const int g0 = fg0 + b * p.gb;
-                                const int nb = min(p.gb, fg1 + 1 - g0);
-                                const uint32_t part = (uint32_t)nb * KB * 1024u;
-                                mbar_arrive_expect_tx(&bars[1], 2 * part);
-                                bulk_g2s(BT, p.twb + ((size_t)(2 * bc) * p.ng_total + g0) * KB * 1024, part, &bars[1]);
-                                bulk_g2s(BT + part, p.twb + ((size_t)(2 * bc + 1) * p.ng_total + g0) * KB * 1024, part,
-                                         &bars[1]);
-                                ok = mbar_wait_bounded(&bars[1], ph_b, p.status) ? 1 : 0;
-                                if (!ok) mbar_wait_bounded(&bars[1], ph_b, p.status, 1u << 20);
-                                ph_b ^= 1u;
-                                cur_g0 = ok ? g0 : -1;
-                                cur_nb = nb;
-                                cur_bc = bc;
-                                if (!ok) break;
-                                tc_fence_after();
-                                const uint32_t idb = idesc_f16(16 * nb);
-                                const uint32_t dcb = tmem + (uint32_t)b * cols_b;
-                                for (int kk = 0; kk < NBc / 32; ++kk) {
-                                    const uint64_t ad = a0 + (uint64_t)(kk * 128);
-                                    const uint64_t bd = b0 + (uint64_t)((kk >> 2) * 64 + (kk & 3) * 2);
-                                    mma_f16(dcb, ad, bd, idb, kk > 0 ? 1u : acc0);
-                                }
-                            }
-                        }
                     }
                     if (issuer) {
                         int mine = ok;
-                        if (mine) {
+                        if (mine && !wide) {
                             mma_commit(&bars[2 + warp]);
                             mine = mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status) ? 1 : 0;
                             if (!mine) mbar_wait_bounded(&bars[2 + warp], ph_mma, p.status, 1u << 20);
@@ -435,16 +486,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     int bk[kNB];
                     band_init_t<kNB>(p.bands, klo, best, bk);
                     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-                    const int n_iss = nbatch == 1 ? p.n_iss : 1;
+                    const bool wide = nbatch > 1;
+                    const int n_iss = wide ? 1 : p.n_iss;
                     const uint32_t cols_b = (uint32_t)(16 * p.gb);
                     const int dir = (warp & 1) * 32 + lane;
-                    for (int b = 0; b < nbatch; ++b) {
-                        const int g0 = fg0 + b * p.gb;
-                        const int nb = min(p.gb, fg1 + 1 - g0);
+                    if (wide) {
+                        // wide bands: warps 2, 3 leave the second-half sums of every
+                        // group in the (now idle) B region as [column][direction],
+                        // 32 columns (4 groups) per tensor-memory load; warps 0, 1
+                        // then combine them with their own and keep the band maximum
+                        float* xw = reinterpret_cast<float*>(BT);   // [8 x 32 groups][kDirs]
+                        const int nb32 = (ng + 3) >> 2;
+                        if (warp >= 2) {
+                            for (int b = 0; b < nb32; ++b) {
+                                float v[32];
+                                tmem_ld32(lane_base + (uint32_t)(32 * b), v);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) xw[(32 * b + i) * kDirs + dir] = v[i];
+                            }
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (warp < 2) {
+                            for (int b = 0; b < nb32; ++b) {
+                                float v[32];
+                                tmem_ld32(lane_base + (uint32_t)(32 * b), v);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int i = 0; i < 32; i += 2) {
+                                    const int f = p.kbase + 4 * (fg0 + 4 * b) + (i >> 1);
+                                    if (f > khi) break;
+                                    const float hr = xw[(32 * b + i) * kDirs + dir];
+                                    const float hs = xw[(32 * b + i + 1) * kDirs + dir];
+                                    float xr, xi;
+                                    if (nchunk == 1) {
+                                        const float sg = (f & 1) ? -1.f : 1.f;
+                                        xr = v[i] + sg * hr;
+                                        xi = v[i + 1] + sg * hs;
+                                    } else {
+                                        float fs, fc;   // w^(f h) = fc - i fs, h = 512
+                                        sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
+                                        xr = v[i] + fc * hr - fs * hs;
+                                        xi = v[i + 1] + fs * hr + fc * hs;
+                                    }
+                                    band_update_t<kNB>(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f,
+                                                       best, bk);
+                                }
+                            }
+                        }
+                    } else {
+                        const int g0 = fg0;
+                        const int nb = ng;
                         for (int j = 0; j < nb; ++j) {
                             float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-                            for (int i = 0; i < (split ? kIssuers / 2 : n_iss); ++i) {
-                                const uint32_t dcol = lane_base + (uint32_t)(b + i) * cols_b;
+                            if (wide) {
+                                // hi and lo products share the group's eight columns
+                                float v[8];
+                                tmem_ld8(lane_base + (uint32_t)(8 * j), v);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    re[q] = v[2 * q];
+                                    im[q] = v[2 * q + 1];
+                                }
+                            }
+                            for (int i = 0; i < (wide ? 0 : split ? kIssuers / 2 : n_iss); ++i) {
+                                const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
                                 float hi[8], lo[8];
                                 tmem_ld8(dcol + (uint32_t)(8 * j), hi);
                                 tmem_ld8(dcol + (uint32_t)(8 * nb + 8 * j), lo);
@@ -550,8 +657,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
 
 // Chunk bc covers bins [bc nbc, bc nbc + nbc) with nbc = min(2^m, 1024); its K
 // rows are the first half of those bins, n = bc nbc + kr, kr < nbc / 2.
-// Layout [chunk][hi|lo][group][64-row K block] x 1 KB.
-__global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng) {
+// Layout [chunk][hi|lo][group][64-row K block] x 1 KB (narrow bands: a batch of
+// groups is one contiguous run per part), or with `streamed`
+// [chunk][64-row K block][hi|lo][group] x 1 KB with ng + 1 groups per run, the
+// last left as the caller's zeros (wide bands: one K block of one part over a
+// run of groups is contiguous).
+__global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng, bool streamed) {
     const int NB = 1 << m;
     const int NBc = NB < kChunkBins ? NB : kChunkBins;
     const int nchunk = NB / NBc;
@@ -576,8 +687,9 @@ __global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng) {
         const __half hi = __double2half(v);
         const __half lo = __double2half(v - (double)__half2float(hi));
         const int kb = k >> 6, kin = k & 63;
-        const size_t off = ((size_t)((2 * bc + part) * ng + g) * KB + kb) * 1024 + (size_t)r * 128 +
-                           (size_t)(((kin >> 3) ^ r) << 4) + (size_t)(kin & 7) * 2;
+        const size_t blk = streamed ? ((size_t)(bc * KB + kb) * 2 + part) * (ng + 1) + g
+                                    : (size_t)((2 * bc + part) * ng + g) * KB + kb;
+        const size_t off = blk * 1024 + (size_t)r * 128 + (size_t)(((kin >> 3) ^ r) << 4) + (size_t)(kin & 7) * 2;
         *reinterpret_cast<__half*>(twb + off) = part ? lo : hi;
     }
 }
@@ -591,9 +703,9 @@ bool tc_supported(Ctx* c) {
     return major == 10 && minor == 3;
 }
 
-static size_t tc_smem_bytes(int m, int atom_cap) {
+static size_t tc_smem_bytes(int m, int atom_cap, size_t bt_bytes) {
     const size_t nbc = std::min<size_t>((size_t)1 << m, kChunkBins);
-    return 1024 + nbc * 128 + kBtBytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 2 * kDirs * 8 +
+    return 1024 + nbc * 128 + bt_bytes + kExBytes + (size_t)atom_cap * 16 + 2 * kDirs * 16 + 2 * kDirs * 8 +
            128 * 8 * 4 + 256;
 }
 
@@ -612,27 +724,36 @@ int prepare_tc(Ctx* c) {
         const int g0 = (c->h_band[2 * r] - kbase) >> 2, g1 = (c->h_band[2 * r + 1] - kbase) >> 2;
         ng_roi_max = std::max(ng_roi_max, g1 - g0 + 1);
     }
-    const int nbatch = (ng_roi_max + gb - 1) / gb;
-    // accumulators: kIssuers partials for single-batch bands, one per batch otherwise
-    const uint32_t need = (uint32_t)(std::max(nbatch, kIssuers) * 16 * gb);
+    // accumulators: kIssuers partials of 16 columns per group for bands that fit
+    // one B batch; wider bands stream their twiddles and accumulate 8 columns per
+    // group, all groups in one MMA of N = 8 x groups <= 256
+    const bool wide = ng_roi_max > gb;
+    if (wide && ng_roi_max > 32)
+        return set_error(c, APTIDX_E_INVALID_ARG,
+                         "tensor-core path: a ROI band spans %d frequency groups (4 frequencies each); at most 32",
+                         ng_roi_max);
+    const uint32_t need = (uint32_t)std::max(kIssuers * 16 * gb, wide ? 8 * ((ng_roi_max + 1) & ~1) : 0);
     uint32_t cols = 32;
     while (cols < need) cols <<= 1;
-    if (cols > 512)
-        return set_error(c, APTIDX_E_INVALID_ARG,
-                         "tensor-core path: a ROI band spans %d frequency groups; at most %d fit in tensor memory",
-                         ng_roi_max, 512 / (16 * gb) * gb);
     if (c->twb_key[0] != c->m || c->twb_key[1] != kbase || c->twb_key[2] != ng) {
         dev_free(c->d_twb);
         c->d_twb = nullptr;
         c->twb_key[0] = c->twb_key[1] = c->twb_key[2] = -1;
+        // both layouts of the same twiddles: [narrow | streamed (one zero group more per run)]
         const size_t bytes = (size_t)nchunk * 2 * ng * KB * 1024;
-        int rc = dev_alloc(c, &c->d_twb, bytes);
+        const size_t sbytes = (size_t)nchunk * 2 * (ng + 1) * KB * 1024;
+        int rc = dev_alloc(c, &c->d_twb, bytes + sbytes);
         if (rc) return rc;
-        k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)nchunk * ng * NBc * 8 + 255) / 256, 4096), 256, 0,
-                      c->stream>>>((uint8_t*)c->d_twb, c->m, kbase, ng);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_check(c, e, "twiddle operand");
-        c->launches += 1;
+        cudaError_t e0 = cudaMemsetAsync((uint8_t*)c->d_twb + bytes, 0, sbytes, c->stream);
+        if (e0 != cudaSuccess) return cuda_check(c, e0, "twiddle operand");
+        for (int streamed = 0; streamed < 2; ++streamed) {
+            k_build_twb<<<(unsigned)std::min<int64_t>(((int64_t)nchunk * ng * NBc * 8 + 255) / 256, 4096), 256, 0,
+                          c->stream>>>((uint8_t*)c->d_twb + streamed * bytes, c->m, kbase, ng, streamed != 0);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_check(c, e, "twiddle operand");
+            c->launches += 1;
+        }
+        c->twb_bytes = bytes;
         c->twb_key[0] = c->m;
         c->twb_key[1] = kbase;
         c->twb_key[2] = ng;
@@ -640,6 +761,7 @@ int prepare_tc(Ctx* c) {
     c->tc_gb = gb;
     c->tc_ng = ng;
     c->tc_tmem_cols = cols;
+    c->tc_wide = wide;
     return APTIDX_OK;
 }
 
@@ -647,11 +769,12 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     cudaError_t e;
     static int max_optin = -1;
     if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    const size_t base = tc_smem_bytes(c->m, 0);
+    const size_t bt_bytes = c->tc_wide ? 2 * (size_t)kWideStage : (size_t)kBtBytes;
+    const size_t base = tc_smem_bytes(c->m, 0, bt_bytes);
     int cap = (int)(((size_t)max_optin - base) / 16);
     cap = std::min(cap, kTcMaxAtoms) & ~15;
     if (cap < 256) return cudaErrorInvalidConfiguration;
-    const size_t smem = tc_smem_bytes(c->m, cap);
+    const size_t smem = tc_smem_bytes(c->m, cap, bt_bytes);
     const bool multi = !hist_out && c->multi.n > 0;
     auto kern = multi ? k_sig_tc<APTIDX_MAX_BANDS> : k_sig_tc<1>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -675,6 +798,8 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     p.m = c->m;
     p.kbase = c->band_min;
     p.twb = (const uint8_t*)c->d_twb;
+    p.twk = (const uint8_t*)c->d_twb + c->twb_bytes;
+    p.bt_bytes = (int32_t)bt_bytes;
     p.ng_total = c->tc_ng;
     p.gb = c->tc_gb;
     p.tmem_cols = c->tc_tmem_cols;

@@ -157,3 +157,43 @@ def test_antipodal_pairs_with_integer_products(torch_cuda):
         assert roi_error(S, So).max() <= TOL_TC
         assert np.abs(S[0] - So[0]).max() <= 1e-5 * So[0].max()
     ctx.close()
+
+
+@pytest.mark.parametrize("m,band", [(8, (3, 100)), (9, (4, 60)), (10, (2, 126))])
+def test_wide_band_stream(torch_cuda, tiny, m, band):
+    """Bands wider than one batch of twiddles in shared memory: the tensor-core
+    kernel streams the twiddles of all the band's frequency groups through two
+    stages per 64-bin block and contracts every group in one MMA per K step
+    (25, 15 and 32 groups: odd counts take a zero group of padding)."""
+    dirs = np.ascontiguousarray(tiny.dirs[:1200])
+    ctx, band, mm, d = make_ctx(torch_cuda, tiny, band=band, dirs=dirs, m=m)
+    nroi, nv = tiny.centres.shape[0], d.shape[0]
+    S, A, N = gpu_signatures(torch_cuda, ctx, nroi, nv, path=TC)
+    Sp, Ap, _ = gpu_signatures(torch_cuda, ctx, nroi, nv, path=PLAIN)
+    So, Ao, No = oracle.signatures(tiny.xyz, tiny.centres, tiny.radii, band[0], band[1], d, m)
+    assert np.array_equal(N, No)
+    assert roi_error(S, So).max() <= TOL_TC
+    assert roi_error(Sp, So).max() <= TOL_PLAIN
+    assert np.all((A >= band[0]) & (A <= band[1]))
+    assert (A == Ao).mean() > 0.99
+    ctx.close()
+
+
+def test_wide_band_large_rois(torch_cuda):
+    """The streamed wide-band contraction over several 2048-atom blocks of one
+    ROI (2049, 10000 and 70000 atoms), band k = 8..128."""
+    torch = torch_cuda
+    xyz, centres, radii = big_rois()
+    dirs = np.ascontiguousarray(synth.icosphere(2))
+    m, band = 10, (8, 128)
+    ctx = apt.Context(0)
+    h = ctx.handle
+    apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda())
+    apt.aptidx_set_directions(h, torch.from_numpy(dirs).cuda())
+    apt.aptidx_set_binning(h, m, band[0], band[1])
+    apt.aptidx_set_rois(h, centres, radii)
+    S, A, N = gpu_signatures(torch, ctx, 3, dirs.shape[0], path=TC)
+    So, Ao, No = oracle.signatures(xyz, centres, radii, band[0], band[1], dirs, m)
+    assert np.array_equal(N, No)
+    assert roi_error(S, So).max() <= TOL_TC
+    ctx.close()
