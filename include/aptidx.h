@@ -304,8 +304,13 @@ int aptidx_match_topk(aptidx_ctx* ctx, int32_t cand, const float* S, int64_t nro
  * FP32, normalised, the layout of aptidx_compute_signatures_multi) with the
  * reference of slot ref[j] (aptidx_set_reference; its look-up table built by
  * aptidx_build_lut on one orientation set shared by every slot used).
- *   Delta_c(g) = (1 / n_c) sum_j Delta_ref[j](g),  n_c = cand_off[c+1] - cand_off[c],
- * with Delta of Eq. 3 accumulated in FP32 (channels in j order).
+ *   Delta_c(g) = (1 / n_c) sum_j Delta_ref[j](g) / E_ref[j],  n_c = cand_off[c+1] - cand_off[c],
+ * with Delta of Eq. 3 accumulated in FP32 (channels in j order) and E the
+ * reference's energy, the sum of its n_hat strongest values squared (FP64,
+ * at aptidx_set_reference): Eq. 3 of an empty signature.  The paper leaves
+ * open how image differences compare across candidates; relative to E a
+ * channel scores 0 for a perfect match and 1 for no signal, whatever the
+ * number of its reference's peaks.  A reference with E = 0 is refused.
  * best[c * nroi + roi] = argmin_g Delta_c(g) (ties: lowest g);
  * score[c * nroi + roi] = Delta_c(best); phase[roi] = the candidate with the
  * lowest score (ties: lowest c).  cand_off, ref, sig: host arrays
@@ -371,6 +376,16 @@ int aptidx_set_profiling(aptidx_ctx* ctx, int enable);
  * [APTIDX_N_PHASES] how many times each phase ran, *launches the number of
  * library kernels launched.  Any pointer may be NULL. */
 int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, int64_t* launches);
+
+/* Read bandwidth of this device's L2 cache, the roof of the gather-bound
+ * kernels (Eq. 3's look-up table reads, the refinement's image taps): a
+ * kernel reads a `bytes`-sized device buffer (small enough to stay in L2;
+ * 1 MiB .. 96 MiB, a multiple of 16) `iters` times with 16-byte loads that
+ * bypass L1, after one untimed pass; *gbs = bytes x iters / kernel time (CUDA
+ * events on the context's stream).  Allocates and frees the buffer; a
+ * measurement helper, not a step of the method.  Errors: INVALID_ARG, OOM,
+ * CUDA. */
+int aptidx_probe_l2(aptidx_ctx* ctx, int64_t bytes, int32_t iters, double* gbs);
 
 /* ---- no-allocation variant ------------------------------------------------ */
 

@@ -332,7 +332,8 @@ def match(S_msr, S_ref, top, lut_, return_scores=False, threads=0):
 
 def match_phase(S, off, sig, refs, tops, luts, threads=0):
     """Phase and orientation from several signatures per candidate (Eq. 3
-    averaged over a candidate's channels, FP64).  S: float32 [n_sig, nroi,
+    of each channel relative to its reference's energy E_j = sum of its
+    squared strongest values, averaged over a candidate's channels, FP64).  S: float32 [n_sig, nroi,
     nv] measured signatures; candidate c owns channels off[c] .. off[c+1]-1;
     channel j compares S[sig[j]] with reference refs[j] (float32 [nv]) at its
     strongest nodes tops[j] (int32 [n_hat], one n_hat for all) through its

@@ -481,10 +481,15 @@ void orc_match(const float* S_msr, int64_t nroi, int64_t nv, const float* S_ref,
  * S + sig[j] * nroi * nv (layout [signature][roi][node]) with reference j:
  * values S_ref + j * nv, strongest nodes top + j * n_hat, look-up table
  * lut + j * ng * n_hat, all tables on one set of ng test orientations.
- *   Delta_c(g) = (1 / n_c) sum_j Delta_j(g),  n_c = off[c+1] - off[c],
- * with Delta_j of Eq. 3 (FP64).  best[c * nroi + r] = argmin_g Delta_c(g)
- * (ties: lowest g), score[c * nroi + r] = Delta_c(best); phase[r] = the
- * candidate of the lowest score (ties: lowest c). */
+ *   Delta_c(g) = (1 / n_c) sum_j Delta_j(g) / E_j,  n_c = off[c+1] - off[c],
+ * with Delta_j of Eq. 3 (FP64) and E_j = sum_k S_ref_j(top_j[k])^2, the Eq. 3
+ * difference of an empty signature against reference j.  The paper compares
+ * image differences across candidates without fixing how; relative to E_j a
+ * channel scores 0 for a perfect match and 1 for no signal, whatever the
+ * number and strength of its reference's peaks.  E_j > 0 is assumed.
+ * best[c * nroi + r] = argmin_g Delta_c(g) (ties: lowest g), score[c * nroi
+ * + r] = Delta_c(best); phase[r] = the candidate of the lowest score (ties:
+ * lowest c). */
 void orc_match_phase(const float* S, int64_t nroi, int64_t nv, int n_cand, const int32_t* off, const int32_t* sig,
                      const float* S_ref, const int32_t* top, int n_hat, const int32_t* lut, int64_t ng,
                      int32_t* phase, int32_t* best, double* score, int threads)
@@ -506,12 +511,13 @@ void orc_match_phase(const float* S, int64_t nroi, int64_t nv, int n_cand, const
                     const float* ref = S_ref + (int64_t)j * nv;
                     const int32_t* tp = top + (int64_t)j * n_hat;
                     const int32_t* lt = lut + ((int64_t)j * ng + g) * n_hat;
-                    double acc = 0.0;
+                    double acc = 0.0, e = 0.0;
                     for (int k = 0; k < n_hat; ++k) {
                         const double d = (double)s[lt[k]] - (double)ref[tp[k]];
                         acc += d * d;
+                        e += (double)ref[tp[k]] * (double)ref[tp[k]];
                     }
-                    tot += acc;
+                    tot += MUT(24, acc, acc / e);
                 }
                 const double dc = MUT(22, tot, tot / (double)nc);
                 if (dc < bs) { bs = dc; bg = (int32_t)g; }

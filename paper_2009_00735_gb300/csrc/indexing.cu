@@ -209,13 +209,14 @@ __device__ __forceinline__ void lut_accumulate(const uint4 w, const float* row, 
     }
 }
 
-// With scores_out, Delta(g) of ROI r also goes to scores_out[r * ng + g]
-// (accumulate: added to the value there, for sums over signature channels).
+// With scores_out, weight x Delta(g) of ROI r also goes to scores_out[r * ng
+// + g] (accumulate: added to the value there, for sums over signature
+// channels).
 template <typename IdxT>
 __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, int64_t nroi, int32_t nv,
                                                 const IdxT* __restrict__ lut_t, int64_t ng, int64_t ng_pad,
                                                 const float* __restrict__ top_val, int32_t n_hat, int32_t* best,
-                                                float* score, float* scores_out, bool accumulate) {
+                                                float* score, float* scores_out, bool accumulate, float weight) {
     constexpr int G = 16 / (int)sizeof(IdxT);
     extern __shared__ float sm[];
     float* row = sm;                     // nv
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(1024, 1) k_match(const float* __restrict__ S, 
                 for (int e = 0; e < G; ++e)
                     if (g0 + e < ng) {
                         float* o = scores_out + r * ng + g0 + e;
-                        *o = accumulate ? *o + acc[e] : acc[e];
+                        *o = accumulate ? fmaf(weight, acc[e], *o) : weight * acc[e];
                     }
             }
         }
@@ -783,7 +784,7 @@ cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_
 
 template <typename IdxT>
 static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
-                                  float* scores_out, bool accumulate) {
+                                  float* scores_out, bool accumulate, float weight) {
     constexpr int G = 16 / (int)sizeof(IdxT);
     const size_t smem = ((size_t)c->nv + r->n_hat) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_match<IdxT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -797,14 +798,14 @@ static cudaError_t launch_match_t(Ctx* c, Reference* r, const float* S, int64_t 
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * per_sm, nroi);
     k_match<IdxT><<<(unsigned)grid, threads, smem, c->stream>>>(S, nroi, c->nv, static_cast<const IdxT*>(r->d_lut),
                                                                 r->ng, r->ng_pad, r->d_top_val, r->n_hat, best, score,
-                                                                scores_out, accumulate);
+                                                                scores_out, accumulate, weight);
     return cudaGetLastError();
 }
 
 cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
-                         float* scores_out, bool accumulate) {
-    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score, scores_out, accumulate)
-                             : launch_match_t<int32_t>(c, r, S, nroi, best, score, scores_out, accumulate);
+                         float* scores_out, bool accumulate, float weight) {
+    return r->lut_bytes == 2 ? launch_match_t<uint16_t>(c, r, S, nroi, best, score, scores_out, accumulate, weight)
+                             : launch_match_t<int32_t>(c, r, S, nroi, best, score, scores_out, accumulate, weight);
 }
 
 // Phase decision: candidate c's summed channel scores divided by its channel

@@ -43,6 +43,7 @@ struct Reference {
     int64_t ng = 0;
     int64_t ng_pad = 0;            // row length of the table: ng rounded up to a multiple of 8
     int32_t nv_at_set = 0;
+    double energy = 0.0;           // sum of the squared n_hat strongest values (Eq. 3 of an empty signature)
 };
 
 struct Ctx {
@@ -214,7 +215,7 @@ size_t plain_smem_bytes(int m, int atom_cap);
 cudaError_t launch_top_nodes(Ctx* c, Reference* r);
 cudaError_t launch_build_lut(Ctx* c, Reference* r, const double* d_quats, int64_t ng);
 cudaError_t launch_match(Ctx* c, Reference* r, const float* S, int64_t nroi, int32_t* best, float* score,
-                         float* scores_out = nullptr, bool accumulate = false);
+                         float* scores_out = nullptr, bool accumulate = false, float weight = 1.0f);
 cudaError_t launch_phase(Ctx* c, float* score, const int32_t* n_ch, int32_t n_cand, int64_t nroi, int32_t* phase);
 cudaError_t launch_topk(Ctx* c, const float* scores, int64_t ng, int64_t nroi, int32_t topk, int32_t* best,
                         float* score);

@@ -38,6 +38,8 @@ MUTANTS = {
          "test_match_phase_reduces_to_eq3_and_averages_channels", {}),
     23: ("every channel of a candidate reads the measured signature of its first channel",
          "test_match_phase_recovers_planted_candidate", {}),
+    24: ("channel differences not divided by the reference's energy",
+         "test_match_phase_empty_signature_scores_one", {}),
 }
 
 

@@ -495,10 +495,16 @@ def _phase_case():
     return u, refs, tops, luts, rng
 
 
+def _energy(ref, top):
+    r = np.asarray(ref, np.float64)[top]
+    return float((r * r).sum())
+
+
 def test_match_phase_reduces_to_eq3_and_averages_channels():
-    """A one-channel candidate gives Eq. 3's argmin and minimum; a candidate
-    of two identical channels gives the same score (the channels' mean, not
-    their sum); equal candidates resolve to the lower index."""
+    """A one-channel candidate gives Eq. 3's argmin and its minimum divided by
+    the reference's energy E = sum of its squared strongest values; a
+    candidate of two identical channels gives the same score (the channels'
+    mean, not their sum); equal candidates resolve to the lower index."""
     u, refs, tops, luts, rng = _phase_case()
     S = rng.random((2, 5, u.shape[0])).astype(np.float32)
     off = [0, 1, 3, 5]
@@ -509,11 +515,27 @@ def test_match_phase_reduces_to_eq3_and_averages_channels():
     phase, best, score = oracle.match_phase(S, off, sig, R, T, L)
     b0, s0 = oracle.match(S[0], refs[0], tops[0], luts[0])
     b1, s1 = oracle.match(S[1], refs[1], tops[1], luts[1])
-    assert np.array_equal(best[0], b0) and np.allclose(score[0], s0, rtol=1e-12)
+    e0, e1 = _energy(refs[0], tops[0]), _energy(refs[1], tops[1])
+    assert abs(e0 - e1) > 0.05 * e1    # the references differ in energy: the division shows
+    assert np.array_equal(best[0], b0) and np.allclose(score[0], s0 / e0, rtol=1e-12)
     for c in (1, 2):
-        assert np.array_equal(best[c], b1) and np.allclose(score[c], s1, rtol=1e-12)
+        assert np.array_equal(best[c], b1) and np.allclose(score[c], s1 / e1, rtol=1e-12)
     assert np.all(phase != 2)          # candidates 1 and 2 tie: the lower index wins
     assert np.array_equal(phase, np.where(score[1] < score[0], 1, 0))
+
+
+def test_match_phase_empty_signature_scores_one():
+    """An empty measured signature differs from every rotated reference by
+    exactly the reference's energy (Eq. 3 with S = 0 sums the squared
+    strongest reference values), so every candidate scores 1 at every
+    orientation, whatever its channels: the lowest g and the lowest
+    candidate win the ties."""
+    u, refs, tops, luts, rng = _phase_case()
+    S = np.zeros((3, 2, u.shape[0]), np.float32)
+    phase, best, score = oracle.match_phase(S, [0, 1, 3], [0, 1, 2], [refs[0], refs[1], refs[2]],
+                                            [tops[0], tops[1], tops[2]], [luts[0], luts[1], luts[2]])
+    assert np.allclose(score, 1.0, rtol=1e-12, atol=0)
+    assert np.all(best == 0) and np.all(phase == 0)
 
 
 def test_match_phase_recovers_planted_candidate():
