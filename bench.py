@@ -103,30 +103,12 @@ def measured_peaks():
         return {}
 
 
-def measure_l2_peak(torch):
-    """Read bandwidth of the L2 cache with torch's own kernels: a 24 MiB
-    float32 tensor (well inside the 129 MB L2) summed 100 times and copied
-    into a second 24 MiB tensor 100 times, after warm-up; the larger of the
-    two byte rates (copy: read + write) in GB/s."""
-    n = 24 * 1024 * 1024 // 4
-    x = torch.rand(n, device="cuda")
-    y = torch.empty_like(x)
-    out = {}
-    for name, fn, bytes_per in (("sum", lambda: x.sum(), 4 * n), ("copy", lambda: y.copy_(x), 8 * n)):
-        for _ in range(10):
-            fn()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(100):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        out[name] = 100 * bytes_per / (e0.elapsed_time(e1) / 1e3) / 1e9
-    del x, y
-    return {"gbs": max(out.values()), "sum_gbs": out["sum"], "copy_gbs": out["copy"],
-            "how": "torch sum and copy over a 24 MiB float32 tensor, 100 calls each after 10 warm-up, CUDA events"}
+def measure_l2_peak(apt, h):
+    """Read bandwidth of the L2 cache (aptidx_probe_l2: a 32 MiB buffer read
+    200 times with 16-byte loads that bypass L1, after one untimed pass)."""
+    gbs = apt.aptidx_probe_l2(h, 32 << 20, 200)
+    return {"gbs": gbs, "how": "aptidx_probe_l2: 32 MiB device buffer (L2-resident) read 200 times, 16-byte "
+                               "ld.global.cg loads, CUDA events"}
 
 
 def gather_rooflines(l2, match_ms, refine_ms, nroi, nv, ng, ng_pad, n_hat, lut_bytes, passes):
@@ -570,7 +552,7 @@ def run_gb300(args):
             "work": f"{flop:.3e} algorithmic FP32 flop per launch"}
     if tensor:
         roof["tensor"] = tensor
-    gather = gather_rooflines(measure_l2_peak(torch), per_phase.get("match"), per_phase.get("refine"), nroi, nv,
+    gather = gather_rooflines(measure_l2_peak(apt, h), per_phase.get("match"), per_phase.get("refine"), nroi, nv,
                               grid.shape[0], (grid.shape[0] + 7) // 8 * 8, n_hat, 2 if nv <= 65536 else 4, iters + 1)
 
     cpu = None

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <tuple>
 #include <vector>
 
@@ -856,6 +857,74 @@ int aptidx_get_tuning(aptidx_ctx* ctx, int path, int32_t* tiles_per_item, int32_
     return APTIDX_OK;
 }
 
+namespace aptidx {
+namespace {
+// every thread streams 16-byte words of the buffer (grid-stride, four loads
+// in flight), `iters` passes; the XOR of what it read keeps the loads alive
+__global__ void __launch_bounds__(256) k_l2_read(const uint4* __restrict__ buf, int64_t n16, int iters,
+                                                 uint32_t* sink) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t acc = 0;
+    for (int it = 0; it < iters; ++it) {
+        int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < n16; i += 4 * stride) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v[u].x), "=r"(v[u].y), "=r"(v[u].z), "=r"(v[u].w)
+                             : "l"(buf + i + u * stride));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+        }
+        for (; i < n16; i += stride) {
+            uint4 v;
+            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "l"(buf + i));
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    }
+    if (acc == 0x9E3779B9u) *sink = acc;
+}
+}  // namespace
+}  // namespace aptidx
+
+int aptidx_probe_l2(aptidx_ctx* ctx, int64_t bytes, int32_t iters, double* gbs) {
+    CTX_OR_FAIL(ctx);
+    if (bytes < (1 << 20) || bytes > ((int64_t)96 << 20) || bytes % 16 != 0 || iters < 1 || iters > 100000 || !gbs)
+        return set_error(c, APTIDX_E_INVALID_ARG, "probe_l2: bytes in [1 MiB, 96 MiB], a multiple of 16; iters >= 1");
+    void* buf = nullptr;
+    int rc = dev_alloc(c, &buf, (size_t)bytes + 256);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(buf, 1, (size_t)bytes + 256, c->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const unsigned grid = (unsigned)c->sm_count * 8;
+    const uint4* b16 = static_cast<const uint4*>(buf);
+    uint32_t* sink = reinterpret_cast<uint32_t*>(static_cast<char*>(buf) + bytes);
+    if (e == cudaSuccess) {
+        k_l2_read<<<grid, 256, 0, c->stream>>>(b16, bytes / 16, 1, sink);   // brings the buffer into L2
+        e = cudaEventRecord(e0, c->stream);
+    }
+    if (e == cudaSuccess) {
+        k_l2_read<<<grid, 256, 0, c->stream>>>(b16, bytes / 16, iters, sink);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(buf);
+    if (e != cudaSuccess) return cuda_check(c, e, "probe_l2");
+    c->launches += 2;
+    *gbs = (double)bytes * iters / (ms * 1e-3) / 1e9;
+    return APTIDX_OK;
+}
+
 int aptidx_set_profiling(aptidx_ctx* ctx, int enable) {
     CTX_OR_FAIL(ctx);
     APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1074,6 +1143,15 @@ int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, i
         APTIDX_CUDA(c, cudaMemcpyAsync(r.d_img, hi.data(), ni * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     }
     r.n_hat = n_hat;
+    {
+        // energy of the strongest n_hat values (which nodes tie at the cut does
+        // not change it), FP64
+        std::vector<float> v(hs.data(), hs.data() + c->nv);
+        std::nth_element(v.begin(), v.begin() + (n_hat - 1), v.end(), std::greater<float>());
+        double en = 0.0;
+        for (int32_t k = 0; k < n_hat; ++k) en += (double)v[k] * (double)v[k];
+        r.energy = en;
+    }
     cudaError_t e = launch_top_nodes(c, &r);
     if (e != cudaSuccess) return cuda_check(c, e, "strongest reference nodes");
     c->launches += 1;
@@ -1239,6 +1317,9 @@ int aptidx_match_phase(aptidx_ctx* ctx, int32_t n_cand, const int32_t* cand_off,
                              n_sig);
         if (ng >= 0 && c->ref[ref[j]].ng != ng)
             return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: the look-up tables hold different orientation sets");
+        if (!(c->ref[ref[j]].energy > 0.0))
+            return set_error(c, APTIDX_E_INVALID_ARG, "match_phase: reference %d has no intensity at its strongest nodes",
+                             ref[j]);
         ng = c->ref[ref[j]].ng;
     }
     static int max_optin = -1;
@@ -1282,7 +1363,7 @@ int aptidx_match_phase(aptidx_ctx* ctx, int32_t n_cand, const int32_t* cand_off,
             cudaError_t e = cudaSuccess;
             for (int32_t j = cand_off[k]; j < cand_off[k + 1] && e == cudaSuccess; ++j) {
                 e = launch_match(c, &c->ref[ref[j]], dS + ((int64_t)sig[j] * nroi + r0) * c->nv, n, nullptr, nullptr,
-                                 c->d_match_scratch, j > cand_off[k]);
+                                 c->d_match_scratch, j > cand_off[k], (float)(1.0 / c->ref[ref[j]].energy));
                 ++launches;
             }
             if (e == cudaSuccess)

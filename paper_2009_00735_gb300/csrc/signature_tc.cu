@@ -273,12 +273,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // several issuers overlap that cost); every pass after the first
                     // accumulates onto the result so far.
                     // Wide bands (more frequency groups than one B batch holds):
-                    // the twiddles of all the ROI's groups stream through two
-                    // 32 KB stages, one per (64-bin K block, hi|lo part), and every
-                    // group accumulates into tensor-memory columns 8 g .. 8 g + 7
-                    // (hi and lo products into the same columns) with one MMA of
-                    // N = 8 x groups per K step; a stage is refilled by the TMA engine
-                    // while the MMAs of the next stage run.
+                    // the twiddles of all the ROI's groups stream through two 32 KB
+                    // shared-memory stages, one per (64-bin K block, hi|lo part),
+                    // and every group accumulates into tensor-memory columns 8 g ..
+                    // 8 g + 7 (hi and lo products into the same columns) with one
+                    // MMA of N = 8 x groups per K step.  A tcgen05.mma occupies its
+                    // issuing thread ~200 cycles whatever N, so the MMAs are as wide
+                    // as the stage allows; the TMA engine refills a stage while the
+                    // other stage's MMAs run.
                     const bool wide = nbatch > 1;
                     const int n_iss = wide ? 1 : p.n_iss;
                     const uint32_t sbo_b = (uint32_t)KB * 1024u;
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             wph ^= 1u << part;
                             if (!ok) break;
                             tc_fence_after();
-                            // B: 8 x ng rows (4 frequencies x cos, sin per group) of
+                            // B: 8 x groups rows (4 frequencies x cos, sin per group) of
                             // 64 bins, 1 KB per 8 rows; 32 bytes per K step
                             const uint64_t b0 = sdesc_sw128(bt_addr + (uint32_t)part * kWideStage, 16u, 1024u);
 #pragma unroll
@@ -491,47 +493,70 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     const uint32_t cols_b = (uint32_t)(16 * p.gb);
                     const int dir = (warp & 1) * 32 + lane;
                     if (wide) {
-                        // wide bands: warps 2, 3 leave the second-half sums of every
-                        // group in the (now idle) B region as [column][direction],
-                        // 32 columns (4 groups) per tensor-memory load; warps 0, 1
-                        // then combine them with their own and keep the band maximum
+                        // wide bands: warps 0, 1 (first half of the chunk's bins) finish
+                        // the first half of the 4-group batches, warps 2, 3 (second
+                        // half of the bins) the rest; each first hands the other the
+                        // sums of the batches it does not finish, through the (now
+                        // idle) B region as [column][direction].  The band maximum is
+                        // kept on |X|^2 (sqrt is monotonic: the maximum's root is the
+                        // maximum amplitude); warps 2, 3, holding the higher
+                        // frequencies, pass theirs to warps 0, 1 at the end.
                         float* xw = reinterpret_cast<float*>(BT);   // [8 x 32 groups][kDirs]
                         const int nb32 = (ng + 3) >> 2;
-                        if (warp >= 2) {
-                            for (int b = 0; b < nb32; ++b) {
-                                float v[32];
-                                tmem_ld32(lane_base + (uint32_t)(32 * b), v);
-                                tmem_wait_ld();
+                        const int nhalf = (nb32 + 1) >> 1;
+                        const bool first = warp < 2;
+                        const int m0 = first ? 0 : nhalf, m1 = first ? nhalf : nb32;
+                        const int o0 = first ? nhalf : 0, o1 = first ? nb32 : nhalf;
+                        for (int b = o0; b < o1; ++b) {
+                            float v[32];
+                            tmem_ld32(lane_base + (uint32_t)(32 * b), v);
+                            tmem_wait_ld();
 #pragma unroll
-                                for (int i = 0; i < 32; ++i) xw[(32 * b + i) * kDirs + dir] = v[i];
+                            for (int i = 0; i < 32; ++i) xw[(32 * b + i) * kDirs + dir] = v[i];
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        for (int b = m0; b < m1; ++b) {
+                            float v[32];
+                            tmem_ld32(lane_base + (uint32_t)(32 * b), v);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const int f = p.kbase + 4 * (fg0 + 4 * b) + q;
+                                const float orr = xw[(32 * b + 2 * q) * kDirs + dir];
+                                const float ori = xw[(32 * b + 2 * q + 1) * kDirs + dir];
+                                const float lr = first ? v[2 * q] : orr, li = first ? v[2 * q + 1] : ori;
+                                const float hr = first ? orr : v[2 * q], hs = first ? ori : v[2 * q + 1];
+                                float xr, xi;
+                                if (nchunk == 1) {
+                                    const float sg = (f & 1) ? -1.f : 1.f;
+                                    xr = lr + sg * hr;
+                                    xi = li + sg * hs;
+                                } else {
+                                    float fs, fc;   // w^(f h) = fc - i fs, h = 512
+                                    sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
+                                    xr = lr + fc * hr - fs * hs;
+                                    xi = li + fs * hr + fc * hs;
+                                }
+                                band_update_t<kNB>(p.bands, klo, khi, f, xr * xr + xi * xi, best, bk);
+                            }
+                        }
+                        if (!first) {
+#pragma unroll
+                            for (int b = 0; b < kNB; ++b) {
+                                EX[dir * 8 + 2 * b] = best[b];
+                                EX[dir * 8 + 2 * b + 1] = __int_as_float(bk[b]);
                             }
                         }
                         asm volatile("bar.sync 1, 128;" ::: "memory");
-                        if (warp < 2) {
-                            for (int b = 0; b < nb32; ++b) {
-                                float v[32];
-                                tmem_ld32(lane_base + (uint32_t)(32 * b), v);
-                                tmem_wait_ld();
+                        if (first) {
 #pragma unroll
-                                for (int i = 0; i < 32; i += 2) {
-                                    const int f = p.kbase + 4 * (fg0 + 4 * b) + (i >> 1);
-                                    if (f > khi) break;
-                                    const float hr = xw[(32 * b + i) * kDirs + dir];
-                                    const float hs = xw[(32 * b + i + 1) * kDirs + dir];
-                                    float xr, xi;
-                                    if (nchunk == 1) {
-                                        const float sg = (f & 1) ? -1.f : 1.f;
-                                        xr = v[i] + sg * hr;
-                                        xi = v[i + 1] + sg * hs;
-                                    } else {
-                                        float fs, fc;   // w^(f h) = fc - i fs, h = 512
-                                        sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
-                                        xr = v[i] + fc * hr - fs * hs;
-                                        xi = v[i + 1] + fs * hr + fc * hs;
-                                    }
-                                    band_update_t<kNB>(p.bands, klo, khi, f, sqrtf(xr * xr + xi * xi) * 16777216.0f,
-                                                       best, bk);
+                            for (int b = 0; b < kNB; ++b) {
+                                const float ob = EX[dir * 8 + 2 * b];
+                                if (ob > best[b]) {   // higher frequencies: strictly greater only
+                                    best[b] = ob;
+                                    bk[b] = __float_as_int(EX[dir * 8 + 2 * b + 1]);
                                 }
+                                if (best[b] >= 0.f) best[b] = sqrtf(best[b]) * 16777216.0f;
                             }
                         }
                     } else {

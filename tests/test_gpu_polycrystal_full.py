@@ -54,8 +54,8 @@ def test_full_polycrystal_sampled(torch_cuda):
         for _ in range(2):        # the second call replays the captured graph
             apt.aptidx_compute_signatures(h, path, flags, S, A, N)
         apt.aptidx_sync(h)
-        out[name] = (S[idx_r][:, idx_v].cpu().numpy(), A[idx_r][:, idx_v].cpu().numpy().astype(np.int64),
-                     N.cpu().numpy())
+        out[name] = (S[idx_r][:, idx_v].cpu().numpy(), A.view(torch.int16)[idx_r][:, idx_v].cpu().numpy()
+                     .astype(np.int64) & 0xFFFF, N.cpu().numpy())
     ctx.close()
     del S, A
     torch.cuda.empty_cache()
