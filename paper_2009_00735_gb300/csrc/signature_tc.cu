@@ -447,39 +447,106 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 }
                 if (failed) break;
 
-                // ---- 4. epilogue: |X(k)| and the band maximum (warps 0-3, one per
-                // TMEM lane quadrant); the other warps zero H for the next tile.
-                // With four partial accumulators and one frequency group, warps
-                // 4-7 sum partials 2 and 3 of the same quadrants meanwhile, so
-                // that each warp waits on two tensor-memory round trips, not four ----
-                const bool split = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
-                const int zw0 = split ? 8 : 4;   // first zeroing warp
+                // ---- 4. epilogue: |X(k)| and the band maximum; the warps from zw0 on
+                // zero H for the next tile meanwhile.  With four partial
+                // accumulators and one frequency group (the common case), warps
+                // 0-7 each read two partials of one TMEM lane quadrant and warps
+                // 0, 1 combine the four contributions of their directions after a
+                // single exchange; otherwise warps 0-3 (one per quadrant) read
+                // every partial and exchange per frequency group ----
+                // warps 0, 1: pass 0 writes the slot's direction (and its partner
+                // when the tile's mirror images are exact); pass 1 the partners
+                auto write_out = [&](const float* best, const int* bk, int dir) {
+                    const int slot = tile * kDirs + dir;
+                    int v0, v1;
+                    if (sym) {
+                        const int2 si = DI[cur * kDirs + dir];
+                        v0 = pass == 0 ? si.x : si.y;
+                        v1 = (pass == 0 && !tile_bad) ? si.y : -1;
+                    } else {
+                        v0 = slot < p.nv ? slot : -1;
+                        v1 = -1;
+                    }
+                    const int64_t rb = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv;
+#pragma unroll
+                    for (int b = 0; b < kNB; ++b) {
+                        if (b < band_count_t<kNB>(p.bands)) {
+                            const int64_t ob = band_off_t<kNB>(p.bands, b) + rb;
+                            if (v0 >= 0) {
+                                p.S[ob + v0] = best[b];
+                                if (p.argk) p.argk[ob + v0] = (uint16_t)bk[b];
+                            }
+                            if (v1 >= 0) {
+                                p.S[ob + v1] = best[b];
+                                if (p.argk) p.argk[ob + v1] = (uint16_t)bk[b];
+                            }
+                        }
+                    }
+                };
+                const bool quad = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
+                const int zw0 = quad ? 8 : 4;   // first zeroing warp
                 if (warp >= zw0) {
                     for (int i = tid - zw0 * 32; i < NBc * 8; i += kThreads - zw0 * 32)
                         reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
-                } else if (warp >= 4) {
-                    const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
+                } else if (quad) {
+                    // warp w: partials 2 (w >> 2) and 2 (w >> 2) + 1 (hi and lo
+                    // columns) of lane quadrant w & 3; warps 2-7 leave their sums
+                    // in shared memory (EX: warps 2, 3; EX2: warps 4-7)
                     const uint32_t cols_b = (uint32_t)(16 * p.gb);
-                    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-                    for (int i = kIssuers / 2; i < kIssuers; ++i) {
-                        const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
-                        float hi[8], lo[8];
-                        tmem_ld8(dcol, hi);
-                        tmem_ld8(dcol + 8u, lo);
-                        tmem_wait_ld();
+                    const uint32_t c0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(2 * (warp >> 2)) * cols_b;
+                    float a[8], b[8], c[8], d[8], x[8];
+                    tmem_ld8(c0, a);
+                    tmem_ld8(c0 + 8u, b);
+                    tmem_ld8(c0 + cols_b, c);
+                    tmem_ld8(c0 + cols_b + 8u, d);
+                    tmem_wait_ld();
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            re[q] += hi[2 * q] + lo[2 * q];
-                            im[q] += hi[2 * q + 1] + lo[2 * q + 1];
-                        }
-                    }
-                    float* e2 = EX2 + (size_t)(tid - 128) * 8;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        e2[2 * q] = re[q];
-                        e2[2 * q + 1] = im[q];
+                    for (int i = 0; i < 8; ++i) x[i] = (a[i] + b[i]) + (c[i] + d[i]);
+                    if (warp >= 2) {
+                        float4* xs = reinterpret_cast<float4*>((warp < 4 ? EX + (warp - 2) * 32 * 8 : EX2 + (warp - 4) * 32 * 8) +
+                                                               lane * 8);
+                        xs[0] = make_float4(x[0], x[1], x[2], x[3]);
+                        xs[1] = make_float4(x[4], x[5], x[6], x[7]);
                     }
                     asm volatile("bar.sync 2, 256;" ::: "memory");
+                    if (warp < 2) {
+                        // direction dir: rows dir (first bin half: this warp, partials
+                        // 0-1; warp 4 + warp, partials 2-3) and 64 + dir (second half:
+                        // warp 2 + warp, partials 0-1; warp 6 + warp, partials 2-3)
+                        const int dir = warp * 32 + lane;
+                        const float4* pl = reinterpret_cast<const float4*>(EX2 + (warp * 32 + lane) * 8);
+                        const float4* ph = reinterpret_cast<const float4*>(EX + (warp * 32 + lane) * 8);
+                        const float4* ph2 = reinterpret_cast<const float4*>(EX2 + ((2 + warp) * 32 + lane) * 8);
+                        const float4 l0 = pl[0], l1 = pl[1], h0 = ph[0], h1 = ph[1], g0 = ph2[0], g1 = ph2[1];
+                        const float lo[8] = {x[0] + l0.x, x[1] + l0.y, x[2] + l0.z, x[3] + l0.w,
+                                             x[4] + l1.x, x[5] + l1.y, x[6] + l1.z, x[7] + l1.w};
+                        const float hv[8] = {h0.x + g0.x, h0.y + g0.y, h0.z + g0.z, h0.w + g0.w,
+                                             h1.x + g1.x, h1.y + g1.y, h1.z + g1.z, h1.w + g1.w};
+                        float best[kNB];
+                        int bk[kNB];
+                        band_init_t<kNB>(p.bands, klo, best, bk);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int f = p.kbase + 4 * fg0 + q;
+                            float xr, xi;
+                            if (nchunk == 1) {
+                                const float sg = (f & 1) ? -1.f : 1.f;
+                                xr = lo[2 * q] + sg * hv[2 * q];
+                                xi = lo[2 * q + 1] + sg * hv[2 * q + 1];
+                            } else {
+                                float fs, fc;   // w^(f h) = fc - i fs, h = 512
+                                sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
+                                xr = lo[2 * q] + fc * hv[2 * q] - fs * hv[2 * q + 1];
+                                xi = lo[2 * q + 1] + fs * hv[2 * q] + fc * hv[2 * q + 1];
+                            }
+                            // the band maximum on |X|^2: its root is the maximum amplitude
+                            band_update_t<kNB>(p.bands, klo, khi, f, xr * xr + xi * xi, best, bk);
+                        }
+#pragma unroll
+                        for (int b = 0; b < kNB; ++b)
+                            if (best[b] >= 0.f) best[b] = sqrtf(best[b]) * 16777216.0f;
+                        write_out(best, bk, dir);
+                    }
                 } else {
                     // warps 0, 1 hold rows 0-63 (the first half of the chunk's
                     // bins), warps 2, 3 rows 64-127; per frequency group the
@@ -575,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                                     im[q] = v[2 * q + 1];
                                 }
                             }
-                            for (int i = 0; i < (wide ? 0 : split ? kIssuers / 2 : n_iss); ++i) {
+                            for (int i = 0; i < (wide ? 0 : n_iss); ++i) {
                                 const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
                                 float hi[8], lo[8];
                                 tmem_ld8(dcol + (uint32_t)(8 * j), hi);
@@ -585,15 +652,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                                 for (int q = 0; q < 4; ++q) {
                                     re[q] += hi[2 * q] + lo[2 * q];
                                     im[q] += hi[2 * q + 1] + lo[2 * q + 1];
-                                }
-                            }
-                            if (split) {   // partials 2, 3 from warp + 4 (one group: j = 0)
-                                asm volatile("bar.sync 2, 256;" ::: "memory");
-                                const float* e2 = EX2 + (size_t)tid * 8;
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    re[q] += e2[2 * q];
-                                    im[q] += e2[2 * q + 1];
                                 }
                             }
                             if (warp >= 2) {
@@ -629,35 +687,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             asm volatile("bar.sync 1, 128;" ::: "memory");
                         }
                     }
-                    if (warp < 2) {
-                        // pass 0 writes the slot's direction (and its partner when
-                        // the tile's mirror images are exact); pass 1 the partners
-                        const int slot = tile * kDirs + dir;
-                        int v0, v1;
-                        if (sym) {
-                            const int2 si = DI[cur * kDirs + dir];
-                            v0 = pass == 0 ? si.x : si.y;
-                            v1 = (pass == 0 && !tile_bad) ? si.y : -1;
-                        } else {
-                            v0 = slot < p.nv ? slot : -1;
-                            v1 = -1;
-                        }
-                        const int64_t rb = (p.single_roi >= 0 ? 0 : roi) * (int64_t)p.nv;
-#pragma unroll
-                        for (int b = 0; b < kNB; ++b) {
-                            if (b < band_count_t<kNB>(p.bands)) {
-                                const int64_t ob = band_off_t<kNB>(p.bands, b) + rb;
-                                if (v0 >= 0) {
-                                    p.S[ob + v0] = best[b];
-                                    if (p.argk) p.argk[ob + v0] = (uint16_t)bk[b];
-                                }
-                                if (v1 >= 0) {
-                                    p.S[ob + v1] = best[b];
-                                    if (p.argk) p.argk[ob + v1] = (uint16_t)bk[b];
-                                }
-                            }
-                        }
-                    }
+                    if (warp < 2) write_out(best, bk, dir);
                 }
                 tc_fence_before();
                 __syncthreads();   // H is zero and the accumulators are read before the next pass

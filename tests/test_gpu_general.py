@@ -197,3 +197,16 @@ def test_wide_band_large_rois(torch_cuda):
     assert np.array_equal(N, No)
     assert roi_error(S, So).max() <= TOL_TC
     ctx.close()
+
+
+def test_probe_l2(torch_cuda):
+    """The L2 read-bandwidth probe returns a plausible rate and refuses sizes
+    outside [1 MiB, 96 MiB] or not a multiple of 16."""
+    ctx = apt.Context(0)
+    g = apt.aptidx_probe_l2(ctx.handle, 8 << 20, 20)
+    assert 1e3 < g < 1e5, g
+    for nbytes in (1 << 19, (96 << 20) + 16, (8 << 20) + 8):
+        with pytest.raises(apt.AptidxError) as ei:
+            apt.aptidx_probe_l2(ctx.handle, nbytes, 10)
+        assert ei.value.code == apt.APTIDX_E_INVALID_ARG
+    ctx.close()
