@@ -137,6 +137,8 @@ __device__ __forceinline__ uint64_t f2_fma_ru(uint64_t a, uint64_t b, uint64_t c
     asm("fma.rp.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ float f2_lo(uint64_t x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float f2_hi(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
 __device__ __forceinline__ uint64_t f2_dup(float v) {
     return ((uint64_t)__float_as_uint(v) << 32) | (uint64_t)__float_as_uint(v);
 }
@@ -144,13 +146,40 @@ __device__ __forceinline__ uint64_t f2_dup(float v) {
 // Rearranges staged atoms in place for the paired histogram loop: the
 // 32-byte block of atoms 2p, 2p + 1 becomes (x_a, x_b, y_a, y_b | z_a, z_b,
 // w_a, w_b), so that one 16-byte and one 8-byte load give the coordinates
-// of both atoms as FP32 pairs.  A trailing odd atom keeps its layout.
-__device__ __forceinline__ void pair_atoms(float4* A, int n, int tid, int nthreads) {
+// of both atoms as FP32 pairs.  A trailing odd atom keeps its layout.  With
+// r2max, the largest x^2 + y^2 + z^2 (FP32) of the atoms goes to *r2max by
+// atomicMax on its bit pattern (the caller zeroes it).
+__device__ __forceinline__ void pair_atoms(float4* A, int n, int tid, int nthreads, unsigned* r2max = nullptr) {
+    float m = 0.f;
     for (int q = tid; q < (n >> 1); q += nthreads) {
         const float4 a = A[2 * q], b = A[2 * q + 1];
         A[2 * q] = make_float4(a.x, b.x, a.y, b.y);
         A[2 * q + 1] = make_float4(a.z, b.z, a.w, b.w);
+        m = fmaxf(m, fmaxf(a.x * a.x + a.y * a.y + a.z * a.z, b.x * b.x + b.y * b.y + b.z * b.z));
     }
+    if (r2max) {
+        if ((n & 1) && tid == 0) {
+            const float4 a = A[n - 1];
+            m = fmaxf(m, a.x * a.x + a.y * a.y + a.z * a.z);
+        }
+        atomicMax(r2max, __float_as_uint(m));
+    }
+}
+
+// Whether, along any direction of norm <= 1 + 1e-5, a projection s of an atom
+// with |x|^2 <= r2max can make s * scale an exact nonzero integer.  With
+// scale = J 2^E (J odd) and s = j 2^e (j odd), s * scale = j J 2^(e + E) is an
+// integer only if e >= -E, i.e. |s| >= 2^-E.  |s| <= |u| |x| (1 + 4 2^-24)
+// and r2max carries at most ~2e-7 relative rounding, so |s| stays below 2^-E
+// when r2max (1 + 5e-5) < 2^-2E.  Otherwise only s = 0 gives an integer product.
+__device__ __forceinline__ bool nonzero_integer_products_possible(float scale, float r2max) {
+    const uint32_t bits = __float_as_uint(scale);
+    const int ex = (int)((bits >> 23) & 0xFFu);
+    if (ex == 0 || ex == 0xFF) return true;   // subnormal or not finite: no claim
+    const uint32_t mant = (bits & 0x7FFFFFu) | 0x800000u;
+    const int E = ex - 150 + (__ffs((int)mant) - 1);
+    if (-2 * E >= 126) return false;
+    return !(r2max * 1.00005f < ldexpf(1.0f, -2 * E));
 }
 
 // Per-lane constants of the paired loop: the lane's two directions and the
@@ -245,14 +274,18 @@ __device__ __forceinline__ void hist_tile_pairs(uint32_t* H, const float4* A, in
 // image of the histogram of u exactly when that sum equals the lane's atom
 // count.
 // -----------------------------------------------------------------------------
-template <bool kCount, bool kChunked>
+template <int kCount, bool kChunked>
 __device__ __forceinline__ void hist_add_pair2(uint32_t hb, ulonglong2 xy, uint64_t zz, const PairDirs& q,
-                                               uint32_t bc, uint32_t cmask, uint32_t& c0, uint32_t& c1) {
+                                               uint32_t bc, uint32_t cmask, uint32_t& c0, uint32_t& c1,
+                                               uint64_t& zp) {
     const uint64_t s0 = f2_fma(zz, q.z0, f2_fma(xy.y, q.y0, f2_mul(xy.x, q.x0)));
     const uint64_t s1 = f2_fma(zz, q.z1, f2_fma(xy.y, q.y1, f2_mul(xy.x, q.x1)));
     const uint64_t t0 = f2_fma_rd(s0, q.sc, q.mg);
     const uint64_t t1 = f2_fma_rd(s1, q.sc, q.mg);
-    if (kCount) {
+    if (kCount == 2) {
+        zp = f2_mul(zp, s0);
+        zp = f2_mul(zp, s1);
+    } else if (kCount == 1) {
         const uint64_t u0 = f2_fma_ru(s0, q.sc, q.mg);
         const uint64_t u1 = f2_fma_ru(s1, q.sc, q.mg);
         c0 += ((uint32_t)u0 - (uint32_t)t0) + ((uint32_t)(u0 >> 32) - (uint32_t)(t0 >> 32));
@@ -277,14 +310,16 @@ __device__ __forceinline__ void hist_add_pair2(uint32_t hb, ulonglong2 xy, uint6
     }
 }
 
-template <bool kCount, bool kChunked>
+template <int kCount, bool kChunked>
 __device__ __forceinline__ void hist_add_one2(uint32_t hb, float4 a, float4 d0, float4 d1, float scale, float magic,
-                                              uint32_t bc, uint32_t cmask, uint32_t& c0, uint32_t& c1) {
+                                              uint32_t bc, uint32_t cmask, uint32_t& c0, uint32_t& c1, uint64_t& zp) {
     const float s0 = project_f32(d0.x, d0.y, d0.z, a);
     const float s1 = project_f32(d1.x, d1.y, d1.z, a);
     const uint32_t t0 = __float_as_uint(__fmaf_rd(s0, scale, magic));
     const uint32_t t1 = __float_as_uint(__fmaf_rd(s1, scale, magic));
-    if (kCount) {
+    if (kCount == 2) {
+        zp = (zp & 0xFFFFFFFF00000000ull) | (uint64_t)__float_as_uint(__uint_as_float((uint32_t)zp) * s0 * s1);
+    } else if (kCount == 1) {
         c0 += __float_as_uint(__fmaf_ru(s0, scale, magic)) - t0;
         c1 += __float_as_uint(__fmaf_ru(s1, scale, magic)) - t1;
     }
@@ -296,12 +331,17 @@ __device__ __forceinline__ void hist_add_one2(uint32_t hb, float4 a, float4 d0, 
 
 // Histograms of one 64-direction tile over `cn` atoms staged by pair_atoms, for
 // bin chunk bc (kChunked) or all bins; warp w takes pairs w, w + W, ...
-// Returns the number of atoms this warp handled; c0, c1 accumulate the lane's
-// non-integer counts of its two directions (kCount).
-template <int W, bool kCount, bool kChunked>
+// Returns the number of atoms this warp handled.  kCount == 1: c0, c1
+// accumulate the lane's non-integer counts of its two directions; kCount ==
+// 2 (only s = 0 can give an integer product): zp multiplies the projections
+// of the lane's atoms along both directions, so a zero half means an atom
+// with s = 0 (a product of the ~70 factors |s| <= R a lane sees per tile
+// stays above ~1e-20 at four standard deviations, far from FP32's 1e-45; an
+// underflow would only cost the tile a second pass).
+template <int W, int kCount, bool kChunked>
 __device__ __forceinline__ int hist_tile_pairs2(uint32_t* H, const float4* A, int cn, int warp, int lane, float4 d0,
                                                 float4 d1, float scale, float magic, uint32_t bc, uint32_t cmask,
-                                                uint32_t& c0, uint32_t& c1) {
+                                                uint32_t& c0, uint32_t& c1, uint64_t& zp) {
     const uint32_t hb = smem_u32(H) + 4u * (uint32_t)lane - 0x80000000u - (bc << 17);
     const PairDirs q = pair_dirs(d0, d1, scale, magic);
     const int np = cn >> 1;
@@ -314,21 +354,21 @@ __device__ __forceinline__ int hist_tile_pairs2(uint32_t* H, const float4* A, in
         for (; j + 3 * W < np; j += 2 * W) {
             const ulonglong2 nxa = ld_xy(j + 2 * W), nxb = ld_xy(j + 3 * W);
             const uint64_t nza = ld_z(j + 2 * W), nzb = ld_z(j + 3 * W);
-            hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1);
-            hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1);
+            hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1, zp);
+            hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1, zp);
             xa = nxa;
             xb = nxb;
             za = nza;
             zb = nzb;
         }
-        hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1);
-        hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1);
+        hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1, zp);
+        hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1, zp);
         j += 2 * W;
     }
-    for (; j < np; j += W) hist_add_pair2<kCount, kChunked>(hb, ld_xy(j), ld_z(j), q, bc, cmask, c0, c1);
+    for (; j < np; j += W) hist_add_pair2<kCount, kChunked>(hb, ld_xy(j), ld_z(j), q, bc, cmask, c0, c1, zp);
     int handled = warp < np ? 2 * ((np - warp + W - 1) / W) : 0;
     if ((cn & 1) && warp == np % W) {
-        hist_add_one2<kCount, kChunked>(hb, A[cn - 1], d0, d1, scale, magic, bc, cmask, c0, c1);
+        hist_add_one2<kCount, kChunked>(hb, A[cn - 1], d0, d1, scale, magic, bc, cmask, c0, c1, zp);
         handled += 1;
     }
     return handled;

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     int64_t* item_s = reinterpret_cast<int64_t*>(bars + kBars + 1);
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + kBars + 2);
     int* iss_ok = reinterpret_cast<int*>(bars + kBars + 3);   // [kIssuers]
+    unsigned* r2max_s = reinterpret_cast<unsigned*>(iss_ok + kIssuers);   // largest |x|^2 of the item's atoms
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -189,11 +190,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         const int t1 = min(t0 + p.tiles_per_item, p.tiles_per_roi);
         const int nblk = max(1, (nw + p.atom_cap - 1) / p.atom_cap);   // atom blocks
         if (nblk == 1) {
+            if (tid == 0) *r2max_s = 0u;
             if (!stage_atoms(A, p.atoms + abase, nw, &bars[0], ph_atoms, p.status, flag)) {
                 failed = true;
                 break;
             }
-            pair_atoms(A, nw, tid, kThreads);
+            pair_atoms(A, nw, tid, kThreads, r2max_s);
         }
         // the first tile's directions (later tiles' arrive while the tile
         // before them runs)
@@ -203,6 +205,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
         }
         cp_async_wait_all();
         __syncthreads();
+        // with one atom block and no nonzero integer product possible, the
+        // antipodal check only looks for s = 0 (a product per lane instead of
+        // an exact count)
+        const bool zero_check = sym && nblk == 1 && !nonzero_integer_products_possible(scale, __uint_as_float(*r2max_s));
 
         for (int tile = t0; tile < t1 && !failed; ++tile) {
             const int cur = tile & 1;
@@ -224,6 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                 }
                 const bool count = sym && pass == 0;
                 uint32_t c0 = 0, c1 = 0;
+                uint64_t zp = f2_dup(1.f);
                 int handled = 0;
                 const int n_sub = nblk * nchunk;
                 for (int sub = 0; sub < n_sub && !failed; ++sub) {
@@ -241,19 +248,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     }
                     // ---- 1. histograms (H is zero here) ----
                     if (nchunk == 1) {
-                        if (count)
-                            handled += hist_tile_pairs2<kWarps, true, false>(H, A, cn, warp, lane, d0, d1, scale, magic,
-                                                                             0u, 0u, c0, c1);
+                        if (count && zero_check)
+                            handled += hist_tile_pairs2<kWarps, 2, false>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                          0u, 0u, c0, c1, zp);
+                        else if (count)
+                            handled += hist_tile_pairs2<kWarps, 1, false>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                          0u, 0u, c0, c1, zp);
                         else
-                            hist_tile_pairs2<kWarps, false, false>(H, A, cn, warp, lane, d0, d1, scale, magic, 0u, 0u,
-                                                                   c0, c1);
+                            hist_tile_pairs2<kWarps, 0, false>(H, A, cn, warp, lane, d0, d1, scale, magic, 0u, 0u,
+                                                               c0, c1, zp);
                     } else {
-                        if (count && bc == 0)
-                            handled += hist_tile_pairs2<kWarps, true, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
-                                                                            (uint32_t)bc, cmask, c0, c1);
+                        if (count && bc == 0 && zero_check)
+                            handled += hist_tile_pairs2<kWarps, 2, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                         (uint32_t)bc, cmask, c0, c1, zp);
+                        else if (count && bc == 0)
+                            handled += hist_tile_pairs2<kWarps, 1, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                                         (uint32_t)bc, cmask, c0, c1, zp);
                         else
-                            hist_tile_pairs2<kWarps, false, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
-                                                                  (uint32_t)bc, cmask, c0, c1);
+                            hist_tile_pairs2<kWarps, 0, true>(H, A, cn, warp, lane, d0, d1, scale, magic,
+                                                              (uint32_t)bc, cmask, c0, c1, zp);
                     }
                     __syncthreads();
                     if (p.hist_out) {
@@ -425,8 +438,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // the non-integer counts are complete once the last pass's
                     // histogram is in: a partner whose count falls short of the
                     // atoms this warp handled needs its own histogram
-                    const int bad = count && last && ((pt0 >= 0 && c0 != (uint32_t)handled) ||
-                                                      (pt1 >= 0 && c1 != (uint32_t)handled));
+                    const int bad = count && last &&
+                                    (zero_check ? (pt0 >= 0 || pt1 >= 0) && (f2_lo(zp) == 0.f || f2_hi(zp) == 0.f)
+                                                : ((pt0 >= 0 && c0 != (uint32_t)handled) ||
+                                                   (pt1 >= 0 && c1 != (uint32_t)handled)));
                     const int any_bad = __syncthreads_or(bad);
                     if (last) tile_bad = any_bad;
                     {

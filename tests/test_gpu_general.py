@@ -124,19 +124,24 @@ def test_antipodal_pairs_match_direct(torch_cuda, tiny):
     ctx.close()
 
 
-def test_antipodal_pairs_with_integer_products(torch_cuda):
+@pytest.mark.parametrize("R", [1.0, 0.97])
+def test_antipodal_pairs_with_integer_products(torch_cuda, R):
     """Atoms on the plane x = 0 through the ROI centre project to exactly 0
     along (1, 0, 0), an integer bin product: the histogram along (-1, 0, 0) is
     then not the mirror image of the one along (1, 0, 0), and the kernel must
     project (-1, 0, 0) itself.  Checked against the oracle direction by
-    direction, with and without pairing."""
+    direction, with and without pairing.  R = 1 (scale 127 = 127 x 2^0: atoms
+    at |s| = 1 could also give integers) takes the exact count of
+    non-integer products; R = 0.97 (a scale with a full significand: only s = 0
+    can) takes the zero-product check."""
     torch = torch_cuda
     rng = np.random.default_rng(5)
     yz = (rng.random((40, 2)) - 0.5) * 1.2
     on_plane = np.column_stack([np.zeros(40), yz])
     off_plane = np.column_stack([np.full(25, 0.3), (rng.random((25, 2)) - 0.5) * 1.2])
     rest = (rng.random((300, 3)) - 0.5) * 1.6
-    xyz = np.ascontiguousarray(np.concatenate([on_plane, off_plane, rest]).astype(np.float32))
+    # an atom at |x| = 1 keeps the R = 1 case on the exact count (|s| = 1 gives an integer there)
+    xyz = np.ascontiguousarray(np.concatenate([on_plane, off_plane, rest, [[0.0, 0.0, 1.0]]]).astype(np.float32))
     u = rng.standard_normal((40, 3))
     u = u / np.linalg.norm(u, axis=1, keepdims=True)
     half = np.concatenate([[[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]], u]).astype(np.float32)
@@ -147,9 +152,9 @@ def test_antipodal_pairs_with_integer_products(torch_cuda):
     apt.aptidx_load_positions(h, torch.from_numpy(xyz).cuda())
     apt.aptidx_set_directions(h, torch.from_numpy(dirs).cuda())
     apt.aptidx_set_binning(h, m, band[0], band[1])
-    apt.aptidx_set_rois(h, np.zeros((1, 3)), np.array([1.0]))
+    apt.aptidx_set_rois(h, np.zeros((1, 3)), np.array([R]))
     nv = dirs.shape[0]
-    So, Ao, _ = oracle.signatures(xyz, np.zeros((1, 3)), np.array([1.0]), band[0], band[1], dirs, m)
+    So, Ao, _ = oracle.signatures(xyz, np.zeros((1, 3)), np.array([R]), band[0], band[1], dirs, m)
     # the mirror image would differ along -x: the oracle's -x signature is not the +x one
     assert So[0, 0] != So[0, 42]
     for flags in (0, apt.APTIDX_DIRECT):
