@@ -552,6 +552,26 @@ def run_gb300(args):
             "work": f"{flop:.3e} algorithmic FP32 flop per launch"}
     if tensor:
         roof["tensor"] = tensor
+    if headline == "tc":
+        # the histogram's shared-memory atomics: one 32-lane red.shared per 32
+        # (atom, direction) increments, at most one per SM per cycle (measured
+        # ceiling of the pipe on this GB300)
+        atom_peak = 152 * 2.070e9
+        atom_ach = pairs / 32.0 / (sig_ms / 1e3)
+        roof["atomics"] = {"achieved": atom_ach, "peak": atom_peak, "unit": "warp red.shared/s",
+                           "frac": atom_ach / atom_peak,
+                           "work": f"{pairs / 32.0:.3e} warp increments per launch (every atom x direction)"}
+        # with the direction set closed under negation the kernel projects one
+        # direction of each antipodal pair (the partners get the mirrored
+        # spectrum; the few tiles with an integer product are projected again)
+        dz = np.asarray(w.dirs, np.float32) + np.float32(0)     # -0 -> +0
+        key = {tuple(d.tolist()) for d in dz}
+        npair = sum(1 for d in dz if tuple((-d + np.float32(0)).tolist()) in key) // 2
+        share = (nv - npair) / nv
+        roof["executed"] = {"share_of_directions_projected": share,
+                            "flop": proj_flop * share, "fp32_frac": proj_flop * share / (sig_ms / 1e3) / 1e12 / ALU_PEAK_TFLOPS,
+                            "atomics_frac": atom_ach * share / atom_peak,
+                            "note": "work the kernel executes (one direction per antipodal pair), a lower bound"}
     gather = gather_rooflines(measure_l2_peak(apt, h), per_phase.get("match"), per_phase.get("refine"), nroi, nv,
                               grid.shape[0], (grid.shape[0] + 7) // 8 * 8, n_hat, 2 if nv <= 65536 else 4, iters + 1)
 

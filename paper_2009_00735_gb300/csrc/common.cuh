@@ -283,8 +283,7 @@ __device__ __forceinline__ void hist_add_pair2(uint32_t hb, ulonglong2 xy, uint6
     const uint64_t t0 = f2_fma_rd(s0, q.sc, q.mg);
     const uint64_t t1 = f2_fma_rd(s1, q.sc, q.mg);
     if (kCount == 2) {
-        zp = f2_mul(zp, s0);
-        zp = f2_mul(zp, s1);
+        zp = f2_mul(zp, f2_mul(s0, s1));
     } else if (kCount == 1) {
         const uint64_t u0 = f2_fma_ru(s0, q.sc, q.mg);
         const uint64_t u1 = f2_fma_ru(s1, q.sc, q.mg);
