@@ -51,7 +51,7 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kDirs = kTileDirs;     // 64 directions per tile
 constexpr int kRows = 2 * kDirs;     // MMA M: (direction, bin half)
 constexpr int kBtBytes = 32 * 1024;  // shared-memory budget of the B operand (narrow bands)
-constexpr int kWideStage = 32 * 1024;   // wide bands: one of two twiddle stream stages
+constexpr int kWideStage = 16 * 1024;   // wide bands: one of four twiddle stream stages
 constexpr int kExBytes = kDirs * 8 * 4;   // epilogue exchange: one group's (re, im) x 4 per direction
 constexpr int kIssuers = 4;          // at most this many warps issue MMAs, one TMEM partial accumulator each
 constexpr int kChunkBins = 1024;     // bins per histogram chunk (128 KB of words)
@@ -73,9 +73,10 @@ struct TcParams {
     int m;
     int32_t kbase;          // frequency of column group 0
     const uint8_t* twb;     // global B: [chunk][hi|lo][group][k-block] x 1 KB
-    const uint8_t* twk;     // global B, streamed layout: [chunk][k-block][hi|lo][group] x 1 KB (wide bands),
-                            // ng_total + 1 groups per run, the last one zero
-    int32_t bt_bytes;       // shared-memory bytes of the B region (kBtBytes, or 2 kWideStage)
+    const uint8_t* twk;     // global B, streamed layout: [chunk][32-bin block of the first quarter][hi|lo]
+                            // [group] x 512 B, 64-byte swizzle (wide bands), ng_total + 1 groups per run,
+                            // the last one zero
+    int32_t bt_bytes;       // shared-memory bytes of the B region (kBtBytes, or 4 kWideStage)
     int32_t ng_total;
     int32_t gb;             // groups per shared-memory batch
     uint32_t tmem_cols;
@@ -115,6 +116,22 @@ __device__ __forceinline__ void hist_export_add(const uint32_t* H, int nbc, int 
 
 // kNB: band slots of the epilogue (1: the ROI's own band; APTIDX_MAX_BANDS:
 // the pass's BandSet, aptidx_compute_signatures_multi)
+// v += (-i)^(R0 + q) u for the n complex pairs (re, im) of v and u, where a
+// pair (r, i) stands for r - i i: multiplying by -i maps it to (-i, r), by -1
+// to (-r, -i), by i to (i, -r)
+template <int R0>
+__device__ __forceinline__ void quarter_rot(float* v, const float* u, int n) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        if (q < n) {
+            const int ph = (R0 + q) & 3;   // constant once unrolled
+            const float ur = u[2 * q], ui = u[2 * q + 1];
+            v[2 * q] += ph == 0 ? ur : ph == 1 ? -ui : ph == 2 ? -ur : ui;
+            v[2 * q + 1] += ph == 0 ? ui : ph == 1 ? ur : ph == 2 ? -ui : -ur;
+        }
+    }
+}
+
 template <int kNB>
 __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -134,8 +151,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     int2* DI = reinterpret_cast<int2*>(DB + 2 * kDirs);   // [2][kDirs]: (output, partner) of those slots
     float* EX2 = reinterpret_cast<float*>(DI + 2 * kDirs);   // [128 TMEM lanes][8]: partials 2, 3
     // barriers: [0] atoms, [1] B operand, [2 .. 2 + kIssuers) MMA completion per
-    // issuer, then the wide-band stream: two stage loads, two stage MMA completions
-    constexpr int kBars = 2 + kIssuers + 4;
+    // issuer, then the wide-band stream: four stage loads, four stage MMA completions
+    constexpr int kBars = 2 + kIssuers + 8;
     uint64_t* bars = reinterpret_cast<uint64_t*>(EX2 + 128 * 8);
     uint64_t* wbar = bars + 2 + kIssuers;
     int* flag = reinterpret_cast<int*>(bars + kBars);
@@ -143,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + kBars + 2);
     int* iss_ok = reinterpret_cast<int*>(bars + kBars + 3);   // [kIssuers]
     unsigned* r2max_s = reinterpret_cast<unsigned*>(iss_ok + kIssuers);   // largest |x|^2 of the item's atoms
+    int* prod_ok = reinterpret_cast<int*>(r2max_s + 1);                      // wide-band stream producer
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -164,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     const uint32_t bt_addr = smem_u32(BT);
 
     uint32_t ph_atoms = 0, ph_b = 0, ph_mma = 0;   // ph_mma: this warp's issuer barrier
-    uint32_t wph = 0u, wdph = 0u;   // wide stream, thread 0: parity bits (bit i: buffer i) of stage loads, stage MMAs
+    uint32_t wph = 0u, wdph = 0u;   // wide stream parity bits (bit i: buffer i): stage loads (thread 0), stage MMAs (thread 32)
     int cur_g0 = -1, cur_nb = -1, cur_bc = -1;     // B operand held in shared memory
     const float magic = bin_magic(p.m);
     const bool sym = p.slot_idx != nullptr;
@@ -286,14 +304,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // several issuers overlap that cost); every pass after the first
                     // accumulates onto the result so far.
                     // Wide bands (more frequency groups than one B batch holds):
-                    // the twiddles of all the ROI's groups stream through two 32 KB
-                    // shared-memory stages, one per (64-bin K block, hi|lo part),
-                    // and every group accumulates into tensor-memory columns 8 g ..
-                    // 8 g + 7 (hi and lo products into the same columns) with one
-                    // MMA of N = 8 x groups per K step.  A tcgen05.mma occupies its
-                    // issuing thread ~200 cycles whatever N, so the MMAs are as wide
-                    // as the stage allows; the TMA engine refills a stage while the
-                    // other stage's MMAs run.
+                    // the chunk's bins split into four quarters, and the twiddles of
+                    // the first quarter, all the ROI's groups, stream through four
+                    // 16 KB shared-memory stages, one per (32-bin K block, hi|lo
+                    // part), in the 64-byte-swizzled K-major layout.  Each stage
+                    // feeds two M = 128 MMAs per K step: block 0 (rows 0-63 the first
+                    // quarter's bins, rows 64-127 the third's) into tensor-memory
+                    // columns 8 g .. 8 g + 7 of group g, block 1 (second and fourth
+                    // quarters) into the same columns from bo1 on; hi and lo products
+                    // accumulate into the same columns, one MMA of N = 8 x groups per
+                    // block and K step.  Twiddle row n serves bin n + j NBc / 4 of
+                    // quarter j up to the factor w^(f j NBc / 4) the epilogue applies,
+                    // so a stage's bytes feed twice the tensor work of the bin-half
+                    // split alone.  Thread 0 issues the MMAs as stages land; thread 32
+                    // refills a stage once its MMAs are done, three stages ahead.
                     const bool wide = nbatch > 1;
                     const int n_iss = wide ? 1 : p.n_iss;
                     const uint32_t sbo_b = (uint32_t)KB * 1024u;
@@ -303,13 +327,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // count takes one more group of twiddles (zeros past the last
                     // group), whose columns are never read
                     const int ngw = (ng + 1) & ~1;
-                    const uint32_t wbytes = (uint32_t)ngw * 1024u;
-                    auto wide_load = [&](int s) {   // stage s = 2 x K block + part, into buffer s & 1
-                        const int kb = s >> 1, part = s & 1;
-                        mbar_arrive_expect_tx(&wbar[part], wbytes);
-                        bulk_g2s(BT + (size_t)part * kWideStage,
-                                 p.twk + ((((size_t)bc * KB + kb) * 2 + part) * (p.ng_total + 1) + fg0) * 1024, wbytes,
-                                 &wbar[part]);
+                    const uint32_t bo1 = (uint32_t)((8 * ngw + 31) & ~31);   // block 1's first column
+                    const uint32_t wbytes = (uint32_t)ngw * 512u;
+                    const int KB4 = NBc / 128;      // 32-bin K blocks of the chunk's first quarter
+                    const int S = 2 * KB4;          // stages: (block, part)
+                    auto wide_load = [&](int s) {   // stage s = 2 x block + part, into buffer s & 3
+                        const int kb = s >> 1, part = s & 1, bf = s & 3;
+                        mbar_arrive_expect_tx(&wbar[bf], wbytes);
+                        bulk_g2s(BT + (size_t)bf * kWideStage,
+                                 p.twk + ((((size_t)bc * KB4 + kb) * 2 + part) * (p.ng_total + 1) + fg0) * 512, wbytes,
+                                 &wbar[bf]);
                     };
                     int ok = 1;
                     if (tid == 0) {
@@ -318,9 +345,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             // (the epilogue before wrote the B region through the
                             // generic proxy)
                             fence_proxy_async_smem();
-                            wide_load(0);
-                            wide_load(1);
+                            for (int st = 0; st < 4; ++st) wide_load(st);
                             cur_g0 = -1;   // the narrow-band B operand is overwritten
+                            *prod_ok = 1;
                         } else {
                             // B operand of the band for this chunk (kept across tiles while
                             // the ROI band and the chunk allow)
@@ -367,49 +394,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // away, NBc / 2 bin rows of 128 bytes
                     const uint64_t a0 = sdesc_sw128(h_addr, (uint32_t)NBc * 64u, 1024u);
                     if (issuer && ok && wide) {
+                        // the consumer: MMAs of each stage as it lands
                         tc_fence_after();
                         const uint32_t idw = idesc_f16(8 * ngw);
-                        const int S = 2 * KB;
                         for (int s = 0; s < S && ok; ++s) {
-                            const int kb = s >> 1, part = s & 1;
-                            if (!mbar_wait_bounded(&wbar[part], (wph >> part) & 1u, p.status)) {
-                                mbar_wait_bounded(&wbar[part], (wph >> part) & 1u, p.status, 1u << 20);
+                            const int kb = s >> 1, bf = s & 3;
+                            if (!mbar_wait_bounded(&wbar[bf], (wph >> bf) & 1u, p.status)) {
+                                mbar_wait_bounded(&wbar[bf], (wph >> bf) & 1u, p.status, 1u << 20);
                                 ok = 0;
                             }
-                            wph ^= 1u << part;
+                            wph ^= 1u << bf;
                             if (!ok) break;
                             tc_fence_after();
                             // B: 8 x groups rows (4 frequencies x cos, sin per group) of
-                            // 64 bins, 1 KB per 8 rows; 32 bytes per K step
-                            const uint64_t b0 = sdesc_sw128(bt_addr + (uint32_t)part * kWideStage, 16u, 1024u);
+                            // 32 bins, 512 bytes per 8 rows; 32 bytes per K step.  A:
+                            // block 0 from bin 0, block 1 from bin NBc / 4 (NBc x 32
+                            // bytes on), the other half NBc / 2 bins away in both
+                            const uint64_t b0 = sdesc_sw64(bt_addr + (uint32_t)bf * kWideStage, 16u, 512u);
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = a0 + (uint64_t)((kb * 4 + kk) * 128);
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const uint64_t ad = a0 + (uint64_t)((2 * kb + kk) * 128);
                                 const uint64_t bd = b0 + (uint64_t)(kk * 2);
-                                mma_f16(tmem, ad, bd, idw, (s > 0 || kk > 0) ? 1u : acc0);
+                                const uint32_t acc = (s > 0 || kk > 0) ? 1u : acc0;
+                                mma_f16(tmem, ad, bd, idw, acc);
+                                mma_f16(tmem + bo1, ad + (uint64_t)(NBc * 2), bd, idw, acc);
                             }
-                            mma_commit(&wbar[2 + part]);
-                            if (s >= 1 && s + 1 < S) {
-                                // the stage before this one has been contracted once its
-                                // commit arrives; its buffer takes stage s + 1
-                                const int pp = (s - 1) & 1;
-                                if (!mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status)) {
-                                    mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status, 1u << 20);
-                                    ok = 0;
-                                }
-                                wdph ^= 1u << pp;
-                                if (ok) wide_load(s + 1);
-                            }
+                            mma_commit(&wbar[4 + bf]);
                         }
-                        // the last two stages' MMAs
-                        for (int s = S - 2; s < S && ok; ++s) {
-                            const int pp = s & 1;
-                            if (!mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status)) {
-                                mbar_wait_bounded(&wbar[2 + pp], (wdph >> pp) & 1u, p.status, 1u << 20);
-                                ok = 0;
+                    } else if (wide && tid == 32 && ok) {
+                        // the producer: a stage's buffer takes the stage four later
+                        // once its MMAs are done; then the last four stages' MMAs
+                        int pok = 1;
+                        for (int s = 4; s < S + 4 && pok; ++s) {
+                            const int bf = s & 3;
+                            if (!mbar_wait_bounded(&wbar[4 + bf], (wdph >> bf) & 1u, p.status)) {
+                                mbar_wait_bounded(&wbar[4 + bf], (wdph >> bf) & 1u, p.status, 1u << 20);
+                                pok = 0;
                             }
-                            wdph ^= 1u << pp;
+                            wdph ^= 1u << bf;
+                            if (pok && s < S) wide_load(s);
                         }
+                        *prod_ok = pok;
                     } else if (issuer && ok) {
                         tc_fence_after();
                         const int nb0 = fg1 + 1 - fg0;
@@ -445,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     const int any_bad = __syncthreads_or(bad);
                     if (last) tile_bad = any_bad;
                     {
-                        int all = 1;
+                        int all = wide ? *prod_ok : 1;
                         for (int i = 0; i < n_iss; ++i) all &= iss_ok[i];
                         if (!all) {
                             failed = true;
@@ -499,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     }
                 };
                 const bool quad = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
-                const int zw0 = quad ? 8 : 4;   // first zeroing warp
+                const int zw0 = (quad || nbatch > 1) ? 8 : 4;   // first zeroing warp
                 if (warp >= zw0) {
                     for (int i = tid - zw0 * 32; i < NBc * 8; i += kThreads - zw0 * 32)
                         reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
@@ -562,6 +587,138 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             if (best[b] >= 0.f) best[b] = sqrtf(best[b]) * 16777216.0f;
                         write_out(best, bk, dir);
                     }
+                } else if (nbatch > 1) {
+                    // Wide bands, warps 0-7: the 64 directions form two groups
+                    // (32 p .. 32 p + 31, p = warp & 1); a group's first-half rows are
+                    // lane quadrant p (warps p, p + 4), its second-half rows quadrant
+                    // 2 + p (warps p + 2, p + 6).  The 4-group column batches split
+                    // into four frequency quarters, one per warp of the group
+                    // (quarter 0: warp p, 1: p + 4, 2: p + 2, 3: p + 6).  Each warp
+                    // first hands the warp of quarter qi ^ 2 (the other bin half)
+                    // its own rows of that quarter through the (now idle) B region
+                    // as [column][direction], then forms X = D_lo + w^(f h) D_hi over
+                    // its quarter and keeps the band maximum of |X|^2 (its root is
+                    // the maximum amplitude); quarters 1-3 pass their maxima to
+                    // quarter 0 through EX and EX2, which keeps a higher quarter's
+                    // value only when strictly greater (lowest-k ties).
+                    float best[kNB];
+                    int bk[kNB];
+                    band_init_t<kNB>(p.bands, klo, best, bk);
+                    const int q4 = warp & 3;
+                    const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
+                    const int dir = (warp & 1) * 32 + lane;
+                    const bool first = q4 < 2;                       // first bin half
+                    const int qi = (first ? 0 : 2) + (warp >> 2);    // frequency quarter
+                    float* xw = reinterpret_cast<float*>(BT);        // [8 x 32 groups][kDirs]
+                    const int nb32 = (ng + 3) >> 2;
+                    auto qb = [&](int j) { return (j * nb32 + 3) >> 2; };   // quarter j = batches [qb(j), qb(j + 1))
+                    const uint32_t bo1 = (uint32_t)((8 * ((ng + 1) & ~1) + 31) & ~31);
+                    // columns [c, c + 2 n) of batch b (n frequencies from f0, cos and
+                    // sin) over this lane quadrant's bin half: D = D_a + w^(f NBc / 4)
+                    // D_b from blocks 0 and 1; w^(f N / 4) = (-i)^f for one chunk,
+                    // whose exponent mod 4 follows from kbase mod 4 (a permutation
+                    // with signs, fixed per unrolled frequency)
+                    auto quarter_add = [&](float* v, const float* u, int n, int f0) {
+                        if (nchunk == 1) {
+                            switch (p.kbase & 3) {
+                                case 0: quarter_rot<0>(v, u, n); break;
+                                case 1: quarter_rot<1>(v, u, n); break;
+                                case 2: quarter_rot<2>(v, u, n); break;
+                                default: quarter_rot<3>(v, u, n); break;
+                            }
+                        } else {
+                            for (int q = 0; q < n; ++q) {
+                                float fs, fc;   // w^(f NBc / 4) = fc - i fs
+                                sincospif((float)(f0 + q) * (float)NBc / (float)(2 * NB), &fs, &fc);
+                                const float ur = u[2 * q], ui = u[2 * q + 1];
+                                v[2 * q] += fc * ur - fs * ui;
+                                v[2 * q + 1] += fs * ur + fc * ui;
+                            }
+                        }
+                    };
+                    for (int b = qb(qi ^ 2); b < qb((qi ^ 2) + 1); ++b) {
+                        float v[32], u[32];
+                        const uint32_t col = lane_base + (uint32_t)(32 * b);
+                        tmem_ld16(col, v);
+                        tmem_ld16(col + 16u, v + 16);
+                        tmem_ld16(col + bo1, u);
+                        tmem_ld16(col + bo1 + 16u, u + 16);
+                        tmem_wait_ld();
+                        quarter_add(v, u, 16, p.kbase + 4 * (fg0 + 4 * b));
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) xw[(32 * b + i) * kDirs + dir] = v[i];
+                    }
+                    asm volatile("bar.sync 1, 256;" ::: "memory");
+                    for (int b = qb(qi); b < qb(qi + 1); ++b) {
+                        float v[32];
+                        {
+                            float u[32];
+                            const uint32_t col = lane_base + (uint32_t)(32 * b);
+                            tmem_ld16(col, v);
+                            tmem_ld16(col + 16u, v + 16);
+                            tmem_ld16(col + bo1, u);
+                            tmem_ld16(col + bo1 + 16u, u + 16);
+                            tmem_wait_ld();
+                            quarter_add(v, u, 16, p.kbase + 4 * (fg0 + 4 * b));
+                        }
+                        const int f0 = p.kbase + 4 * (fg0 + 4 * b);
+                        const float* xo = xw + 32 * b * kDirs + dir;
+                        // the second half's factor w^(f h): (-1)^f for one chunk (a
+                        // branch outside the frequency loop, so that the loop carries
+                        // no predicated sincos), else cos and sin of pi f h 2 / 2^m
+                        if (nchunk == 1) {
+                            const float sg0 = (f0 & 1) ? -1.f : 1.f;
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const float orr = xo[(2 * q) * kDirs], ori = xo[(2 * q + 1) * kDirs];
+                                const float lr = first ? v[2 * q] : orr, li = first ? v[2 * q + 1] : ori;
+                                const float hr = first ? orr : v[2 * q], hs = first ? ori : v[2 * q + 1];
+                                const float sg = (q & 1) ? -sg0 : sg0;
+                                const float xr = lr + sg * hr, xi = li + sg * hs;
+                                band_update_t<kNB>(p.bands, klo, khi, f0 + q, xr * xr + xi * xi, best, bk);
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const int f = f0 + q;
+                                const float orr = xo[(2 * q) * kDirs], ori = xo[(2 * q + 1) * kDirs];
+                                const float lr = first ? v[2 * q] : orr, li = first ? v[2 * q + 1] : ori;
+                                const float hr = first ? orr : v[2 * q], hs = first ? ori : v[2 * q + 1];
+                                float fs, fc;   // w^(f h) = fc - i fs, h = 512
+                                sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
+                                const float xr = lr + fc * hr - fs * hs, xi = li + fs * hr + fc * hs;
+                                band_update_t<kNB>(p.bands, klo, khi, f, xr * xr + xi * xi, best, bk);
+                            }
+                        }
+                    }
+                    // maxima of quarters 1-3: slot ((qi - 1) x 64 + dir) x 8 of EX
+                    // (first 512 floats) and EX2
+                    auto mx = [&](int qq, int k) -> float& {
+                        const int f = ((qq - 1) * kDirs + dir) * 8 + k;
+                        return f < kDirs * 8 ? EX[f] : EX2[f - kDirs * 8];
+                    };
+                    if (qi > 0) {
+#pragma unroll
+                        for (int b = 0; b < kNB; ++b) {
+                            mx(qi, 2 * b) = best[b];
+                            mx(qi, 2 * b + 1) = __int_as_float(bk[b]);
+                        }
+                    }
+                    asm volatile("bar.sync 1, 256;" ::: "memory");
+                    if (qi == 0) {
+#pragma unroll
+                        for (int b = 0; b < kNB; ++b) {
+                            for (int qq = 1; qq < 4; ++qq) {
+                                const float ob = mx(qq, 2 * b);
+                                if (ob > best[b]) {
+                                    best[b] = ob;
+                                    bk[b] = __float_as_int(mx(qq, 2 * b + 1));
+                                }
+                            }
+                            if (best[b] >= 0.f) best[b] = sqrtf(best[b]) * 16777216.0f;
+                        }
+                        write_out(best, bk, dir);
+                    }
                 } else {
                     // warps 0, 1 hold rows 0-63 (the first half of the chunk's
                     // bins), warps 2, 3 rows 64-127; per frequency group the
@@ -570,94 +727,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     int bk[kNB];
                     band_init_t<kNB>(p.bands, klo, best, bk);
                     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-                    const bool wide = nbatch > 1;
-                    const int n_iss = wide ? 1 : p.n_iss;
+                    const int n_iss = p.n_iss;
                     const uint32_t cols_b = (uint32_t)(16 * p.gb);
                     const int dir = (warp & 1) * 32 + lane;
-                    if (wide) {
-                        // wide bands: warps 0, 1 (first half of the chunk's bins) finish
-                        // the first half of the 4-group batches, warps 2, 3 (second
-                        // half of the bins) the rest; each first hands the other the
-                        // sums of the batches it does not finish, through the (now
-                        // idle) B region as [column][direction].  The band maximum is
-                        // kept on |X|^2 (sqrt is monotonic: the maximum's root is the
-                        // maximum amplitude); warps 2, 3, holding the higher
-                        // frequencies, pass theirs to warps 0, 1 at the end.
-                        float* xw = reinterpret_cast<float*>(BT);   // [8 x 32 groups][kDirs]
-                        const int nb32 = (ng + 3) >> 2;
-                        const int nhalf = (nb32 + 1) >> 1;
-                        const bool first = warp < 2;
-                        const int m0 = first ? 0 : nhalf, m1 = first ? nhalf : nb32;
-                        const int o0 = first ? nhalf : 0, o1 = first ? nb32 : nhalf;
-                        for (int b = o0; b < o1; ++b) {
-                            float v[32];
-                            tmem_ld32(lane_base + (uint32_t)(32 * b), v);
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) xw[(32 * b + i) * kDirs + dir] = v[i];
-                        }
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
-                        for (int b = m0; b < m1; ++b) {
-                            float v[32];
-                            tmem_ld32(lane_base + (uint32_t)(32 * b), v);
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                const int f = p.kbase + 4 * (fg0 + 4 * b) + q;
-                                const float orr = xw[(32 * b + 2 * q) * kDirs + dir];
-                                const float ori = xw[(32 * b + 2 * q + 1) * kDirs + dir];
-                                const float lr = first ? v[2 * q] : orr, li = first ? v[2 * q + 1] : ori;
-                                const float hr = first ? orr : v[2 * q], hs = first ? ori : v[2 * q + 1];
-                                float xr, xi;
-                                if (nchunk == 1) {
-                                    const float sg = (f & 1) ? -1.f : 1.f;
-                                    xr = lr + sg * hr;
-                                    xi = li + sg * hs;
-                                } else {
-                                    float fs, fc;   // w^(f h) = fc - i fs, h = 512
-                                    sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
-                                    xr = lr + fc * hr - fs * hs;
-                                    xi = li + fs * hr + fc * hs;
-                                }
-                                band_update_t<kNB>(p.bands, klo, khi, f, xr * xr + xi * xi, best, bk);
-                            }
-                        }
-                        if (!first) {
-#pragma unroll
-                            for (int b = 0; b < kNB; ++b) {
-                                EX[dir * 8 + 2 * b] = best[b];
-                                EX[dir * 8 + 2 * b + 1] = __int_as_float(bk[b]);
-                            }
-                        }
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
-                        if (first) {
-#pragma unroll
-                            for (int b = 0; b < kNB; ++b) {
-                                const float ob = EX[dir * 8 + 2 * b];
-                                if (ob > best[b]) {   // higher frequencies: strictly greater only
-                                    best[b] = ob;
-                                    bk[b] = __float_as_int(EX[dir * 8 + 2 * b + 1]);
-                                }
-                                if (best[b] >= 0.f) best[b] = sqrtf(best[b]) * 16777216.0f;
-                            }
-                        }
-                    } else {
+                    {
                         const int g0 = fg0;
                         const int nb = ng;
                         for (int j = 0; j < nb; ++j) {
                             float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-                            if (wide) {
-                                // hi and lo products share the group's eight columns
-                                float v[8];
-                                tmem_ld8(lane_base + (uint32_t)(8 * j), v);
-                                tmem_wait_ld();
-#pragma unroll
-                                for (int q = 0; q < 4; ++q) {
-                                    re[q] = v[2 * q];
-                                    im[q] = v[2 * q + 1];
-                                }
-                            }
-                            for (int i = 0; i < (wide ? 0 : n_iss); ++i) {
+                            for (int i = 0; i < n_iss; ++i) {
                                 const uint32_t dcol = lane_base + (uint32_t)i * cols_b;
                                 float hi[8], lo[8];
                                 tmem_ld8(dcol + (uint32_t)(8 * j), hi);
@@ -727,17 +805,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
 
 // Chunk bc covers bins [bc nbc, bc nbc + nbc) with nbc = min(2^m, 1024); its K
 // rows are the first half of those bins, n = bc nbc + kr, kr < nbc / 2.
-// Layout [chunk][hi|lo][group][64-row K block] x 1 KB (narrow bands: a batch of
-// groups is one contiguous run per part), or with `streamed`
-// [chunk][64-row K block][hi|lo][group] x 1 KB with ng + 1 groups per run, the
-// last left as the caller's zeros (wide bands: one K block of one part over a
-// run of groups is contiguous).
+// Layout [chunk][hi|lo][group][64-row K block] x 1 KB, 128-byte swizzle
+// (narrow bands: a batch of groups is one contiguous run per part), or with
+// `streamed` the first nbc / 4 rows only, [chunk][32-row K block][hi|lo][group]
+// x 512 B, 64-byte swizzle, with ng + 1 groups per run, the last left as the
+// caller's zeros (wide bands: one K block of one part over a run of groups is
+// contiguous).
 __global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng, bool streamed) {
     const int NB = 1 << m;
     const int NBc = NB < kChunkBins ? NB : kChunkBins;
     const int nchunk = NB / NBc;
-    const int NK = NBc / 2;
-    const int KB = NK / 64;
+    const int NK = streamed ? NBc / 4 : NBc / 2;
+    const int KB = NBc / 128;
     const int64_t total = (int64_t)nchunk * 2 * ng * NK * 8;   // chunks x [hi|lo] x groups x K rows x 8 columns
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i & 7);
@@ -756,10 +835,16 @@ __global__ void k_build_twb(uint8_t* twb, int m, int kbase, int ng, bool streame
         const double v = (r & 1) ? sn : cs;
         const __half hi = __double2half(v);
         const __half lo = __double2half(v - (double)__half2float(hi));
-        const int kb = k >> 6, kin = k & 63;
-        const size_t blk = streamed ? ((size_t)(bc * KB + kb) * 2 + part) * (ng + 1) + g
-                                    : (size_t)((2 * bc + part) * ng + g) * KB + kb;
-        const size_t off = blk * 1024 + (size_t)r * 128 + (size_t)(((kin >> 3) ^ r) << 4) + (size_t)(kin & 7) * 2;
+        size_t off;
+        if (streamed) {
+            const int kb = k >> 5, kin = k & 31;
+            const size_t blk = ((size_t)(bc * KB + kb) * 2 + part) * (ng + 1) + g;
+            off = blk * 512 + (size_t)r * 64 + (size_t)(((kin >> 3) ^ ((r >> 1) & 3)) << 4) + (size_t)(kin & 7) * 2;
+        } else {
+            const int kb = k >> 6, kin = k & 63;
+            const size_t blk = (size_t)((2 * bc + part) * ng + g) * KB + kb;
+            off = blk * 1024 + (size_t)r * 128 + (size_t)(((kin >> 3) ^ r) << 4) + (size_t)(kin & 7) * 2;
+        }
         *reinterpret_cast<__half*>(twb + off) = part ? lo : hi;
     }
 }
@@ -796,13 +881,16 @@ int prepare_tc(Ctx* c) {
     }
     // accumulators: kIssuers partials of 16 columns per group for bands that fit
     // one B batch; wider bands stream their twiddles and accumulate 8 columns per
-    // group, all groups in one MMA of N = 8 x groups <= 256
+    // group in each of two blocks (bin quarters 0 and 2, 1 and 3), all groups in
+    // one MMA of N = 8 x groups <= 256 per block
     const bool wide = ng_roi_max > gb;
     if (wide && ng_roi_max > 32)
         return set_error(c, APTIDX_E_INVALID_ARG,
                          "tensor-core path: a ROI band spans %d frequency groups (4 frequencies each); at most 32",
                          ng_roi_max);
-    const uint32_t need = (uint32_t)std::max(kIssuers * 16 * gb, wide ? 8 * ((ng_roi_max + 1) & ~1) : 0);
+    // (wide: two blocks of 8 x groups columns, the second from a multiple of 32)
+    const int wcols = 8 * ((ng_roi_max + 1) & ~1);
+    const uint32_t need = (uint32_t)std::max(kIssuers * 16 * gb, wide ? ((wcols + 31) & ~31) + wcols : 0);
     uint32_t cols = 32;
     while (cols < need) cols <<= 1;
     if (c->twb_key[0] != c->m || c->twb_key[1] != kbase || c->twb_key[2] != ng) {
@@ -811,7 +899,7 @@ int prepare_tc(Ctx* c) {
         c->twb_key[0] = c->twb_key[1] = c->twb_key[2] = -1;
         // both layouts of the same twiddles: [narrow | streamed (one zero group more per run)]
         const size_t bytes = (size_t)nchunk * 2 * ng * KB * 1024;
-        const size_t sbytes = (size_t)nchunk * 2 * (ng + 1) * KB * 1024;
+        const size_t sbytes = (size_t)nchunk * 2 * (ng + 1) * KB * 512;
         int rc = dev_alloc(c, &c->d_twb, bytes + sbytes);
         if (rc) return rc;
         cudaError_t e0 = cudaMemsetAsync((uint8_t*)c->d_twb + bytes, 0, sbytes, c->stream);
@@ -839,7 +927,7 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     cudaError_t e;
     static int max_optin = -1;
     if (max_optin < 0) cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    const size_t bt_bytes = c->tc_wide ? 2 * (size_t)kWideStage : (size_t)kBtBytes;
+    const size_t bt_bytes = c->tc_wide ? 4 * (size_t)kWideStage : (size_t)kBtBytes;
     const size_t base = tc_smem_bytes(c->m, 0, bt_bytes);
     int cap = (int)(((size_t)max_optin - base) / 16);
     cap = std::min(cap, kTcMaxAtoms) & ~15;
