@@ -38,7 +38,9 @@ if ROOT not in sys.path:
 METRIC = "ROI x direction signatures/s, plain FP32 vs batched tensor-core, at stated oracle error"
 UNIT = "signatures/s"
 # FP32 FMA peak from the unit counts and the maximum SM clock: 152 SMs x 128
-# FP32 lanes x 2 flop x 2.07 GHz
+# FP32 lanes x 2 flop x 2.07 GHz.  The packed instructions the histogram
+# kernels use (fma.rn.f32x2) measured the same 125 FMAs per SM-cycle as scalar
+# FMAs: they save issue slots, not FMA-pipe time.
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
@@ -109,6 +111,16 @@ def measure_l2_peak(apt, h):
     gbs = apt.aptidx_probe_l2(h, 32 << 20, 200)
     return {"gbs": gbs, "how": "aptidx_probe_l2: 32 MiB device buffer (L2-resident) read 200 times, 16-byte "
                                "ld.global.cg loads, CUDA events"}
+
+
+def measure_atomic_peak(apt, h):
+    """Throughput of 32-lane shared-memory atomic adds (aptidx_probe_smem_atomics:
+    one 512-thread block per SM, lane-private banks, random rows, 4096 x 16
+    increments per thread), the roof of the histogram of Eq. 1."""
+    incr, per_cycle = apt.aptidx_probe_smem_atomics(h, 512, 4096)
+    return {"warp_reds_per_s": incr / 32.0, "reds_per_sm_cycle": per_cycle,
+            "how": "aptidx_probe_smem_atomics: 512 threads per SM, red.shared.add.u32 into lane-private banks of "
+                   "random 128-byte rows, CUDA events"}
 
 
 def gather_rooflines(l2, match_ms, refine_ms, nroi, nv, ng, ng_pad, n_hat, lut_bytes, passes):
@@ -548,18 +560,19 @@ def run_gb300(args):
                               "ROIs (profiles/k_sig_tc_traffic.json); null once the kernel sources change",
             "kernel": "k_sig_plain" if headline == "plain" else "k_sig_tc",
             "kernel_ms": sig_ms,
-            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (nominal unit counts and max clock)",
+            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock; packed "
+                           "fma.rn.f32x2 runs at the same FMA rate)",
             "work": f"{flop:.3e} algorithmic FP32 flop per launch"}
     if tensor:
         roof["tensor"] = tensor
     if headline == "tc":
         # the histogram's shared-memory atomics: one 32-lane red.shared per 32
-        # (atom, direction) increments, at most one per SM per cycle (measured
-        # ceiling of the pipe on this GB300)
-        atom_peak = 152 * 2.070e9
+        # (atom, direction) increments, against the rate the probe measures
+        ap = measure_atomic_peak(apt, h)
+        atom_peak = ap["warp_reds_per_s"]
         atom_ach = pairs / 32.0 / (sig_ms / 1e3)
         roof["atomics"] = {"achieved": atom_ach, "peak": atom_peak, "unit": "warp red.shared/s",
-                           "frac": atom_ach / atom_peak,
+                           "frac": atom_ach / atom_peak, "peak_source": ap,
                            "work": f"{pairs / 32.0:.3e} warp increments per launch (every atom x direction)"}
         # with the direction set closed under negation the kernel projects one
         # direction of each antipodal pair (the partners get the mirrored

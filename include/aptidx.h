@@ -387,6 +387,20 @@ int aptidx_get_profile(aptidx_ctx* ctx, double* phase_ms, int64_t* phase_calls, 
  * CUDA. */
 int aptidx_probe_l2(aptidx_ctx* ctx, int64_t bytes, int32_t iters, double* gbs);
 
+/* Throughput of shared-memory atomic adds on this device, the roof of the
+ * histogram of Eq. 1 as the signature kernels build it (one 32-bit
+ * red.shared.add per warp lane, each lane in its own bank, rows drawn at
+ * random): one block of `threads` threads (a multiple of 32 in [32, 1024])
+ * per SM, each thread issuing `iters` x 16 increments into a 128 KB shared
+ * array, after one untimed pass.  *incr_per_s = lane increments per second
+ * over the whole device (CUDA events on the context's stream);
+ * *reds_per_sm_cycle (may be NULL) = 32-lane atomic instructions per SM and
+ * SM clock cycle (clock64 inside the blocks).  Each block checks that its
+ * array holds every increment (else APTIDX_E_CUDA).  A measurement helper, not
+ * a step of the method.  Errors: INVALID_ARG, OOM, CUDA. */
+int aptidx_probe_smem_atomics(aptidx_ctx* ctx, int32_t threads, int32_t iters, double* incr_per_s,
+                              double* reds_per_sm_cycle);
+
 /* ---- no-allocation variant ------------------------------------------------ */
 
 /* The paper has no counterpart of this call; it serves callers that cannot

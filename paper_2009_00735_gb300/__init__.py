@@ -23,7 +23,7 @@ __all__ = [
     "aptidx_load_positions", "aptidx_set_directions", "aptidx_set_binning", "aptidx_set_rois",
     "aptidx_compute_signatures", "aptidx_get_histograms", "aptidx_get_roi_atoms",
     "aptidx_set_reference", "aptidx_build_lut", "aptidx_get_lut", "aptidx_match", "aptidx_match_topk", "aptidx_match_phase", "aptidx_compute_signatures_multi", "aptidx_refine_roi_grid", "aptidx_compute_fsp", "aptidx_refine_loss", "aptidx_refine",
-    "band_for_spacing", "aptidx_band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile", "aptidx_probe_l2",
+    "band_for_spacing", "aptidx_band_for_spacing", "aptidx_path_supported", "aptidx_set_profiling", "aptidx_get_profile", "aptidx_probe_l2", "aptidx_probe_smem_atomics",
     "tc_available", "PHASES", "aptidx_signatures_noalloc",
     "APTIDX_MEM_HOST", "APTIDX_MEM_DEVICE", "APTIDX_PATH_PLAIN_FP32", "APTIDX_PATH_TC_FP16",
     "APTIDX_NORMALISE_MAX", "APTIDX_AUTOTUNE", "APTIDX_GRAPH", "APTIDX_DIRECT", "aptidx_get_tuning",
@@ -94,6 +94,7 @@ _SIGS = {
     "aptidx_set_profiling": (C.c_int, [_vp, C.c_int]),
     "aptidx_get_profile": (C.c_int, [_vp, _vp, _vp, _vp]),
     "aptidx_probe_l2": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp]),
+    "aptidx_probe_smem_atomics": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
     "aptidx_signatures_noalloc": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, C.c_int, _i32, _i32, _vp, _vp, _vp]),
 }
 
@@ -461,6 +462,14 @@ def aptidx_probe_l2(ctx, nbytes: int = 32 << 20, iters: int = 200) -> float:
     g = np.zeros(1, np.float64)
     _check(ctx, load().aptidx_probe_l2(ctx, int(nbytes), int(iters), g.ctypes.data))
     return float(g[0])
+
+
+def aptidx_probe_smem_atomics(ctx, threads: int = 512, iters: int = 4096):
+    """Shared-memory atomic add throughput: (lane increments per second over
+    the device, 32-lane atomic instructions per SM and SM cycle)."""
+    g = np.zeros(2, np.float64)
+    _check(ctx, load().aptidx_probe_smem_atomics(ctx, int(threads), int(iters), g.ctypes.data, g.ctypes.data + 8))
+    return float(g[0]), float(g[1])
 
 
 def aptidx_set_profiling(ctx, enable: bool):

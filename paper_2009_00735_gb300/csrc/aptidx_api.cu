@@ -887,6 +887,54 @@ __global__ void __launch_bounds__(256) k_l2_read(const uint4* __restrict__ buf, 
     }
     if (acc == 0x9E3779B9u) *sink = acc;
 }
+
+// Every lane adds 1 to words of its own bank (lane l: word l of a 128-byte
+// row) of a 1024-row shared array, as the signature histograms do; the rows
+// are drawn once per lane (16 of them, from a 32-bit mixing hash) and XORed
+// with the step number, so consecutive increments of a lane land in
+// different rows.  Block b writes the sum of its array (which must equal
+// threads x iters x 16) to sums[b] and its clock64 cycles to cycles[b].
+__global__ void __launch_bounds__(1024) k_smem_red(int iters, uint32_t* sums, long long* cycles) {
+    extern __shared__ __align__(16) uint32_t sh[];   // [1024][32]
+    for (int i = threadIdx.x; i < 1024 * 32; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(sh) + 4u * (threadIdx.x & 31u);
+    uint32_t a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        uint32_t h = (blockIdx.x * blockDim.x + threadIdx.x) * 16u + (uint32_t)u + 0x9E3779B9u;
+        h ^= h >> 16;
+        h *= 0x7FEB352Du;
+        h ^= h >> 15;
+        h *= 0x846CA68Bu;
+        h ^= h >> 16;
+        a[u] = base + (h >> 22) * 128u;
+    }
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+        const uint32_t x = ((uint32_t)it & 1023u) * 128u;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const uint32_t ad = (a[u] - base) ^ x;
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + ad), "r"(1u) : "memory");
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    uint32_t part = 0;
+    for (int i = threadIdx.x; i < 1024 * 32; i += blockDim.x) part += sh[i];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        sums[blockIdx.x] = tot;
+        cycles[blockIdx.x] = t1 - t0;
+    }
+}
 }  // namespace
 }  // namespace aptidx
 
@@ -922,6 +970,58 @@ int aptidx_probe_l2(aptidx_ctx* ctx, int64_t bytes, int32_t iters, double* gbs) 
     if (e != cudaSuccess) return cuda_check(c, e, "probe_l2");
     c->launches += 2;
     *gbs = (double)bytes * iters / (ms * 1e-3) / 1e9;
+    return APTIDX_OK;
+}
+
+int aptidx_probe_smem_atomics(aptidx_ctx* ctx, int32_t threads, int32_t iters, double* incr_per_s,
+                              double* reds_per_sm_cycle) {
+    CTX_OR_FAIL(ctx);
+    if (threads < 32 || threads > 1024 || threads % 32 != 0 || iters < 1 || iters > 1000000 || !incr_per_s)
+        return set_error(c, APTIDX_E_INVALID_ARG,
+                         "probe_smem_atomics: threads a multiple of 32 in [32, 1024], iters in [1, 1e6]");
+    const int nb = c->sm_count;
+    void* buf = nullptr;
+    int rc = dev_alloc(c, &buf, (size_t)nb * 12 + 64);
+    if (rc) return rc;
+    long long* cyc = static_cast<long long*>(buf);
+    uint32_t* sums = reinterpret_cast<uint32_t*>(cyc + nb);
+    const size_t smem = 1024 * 128;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaFuncSetAttribute(k_smem_red, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        k_smem_red<<<nb, threads, smem, c->stream>>>(1, sums, cyc);   // warm-up
+        e = cudaEventRecord(e0, c->stream);
+    }
+    if (e == cudaSuccess) {
+        k_smem_red<<<nb, threads, smem, c->stream>>>(iters, sums, cyc);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    std::vector<long long> hc(nb);
+    std::vector<uint32_t> hs(nb);
+    if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, (size_t)nb * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), sums, (size_t)nb * 4, cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(buf);
+    if (e != cudaSuccess) return cuda_check(c, e, "probe_smem_atomics");
+    c->launches += 2;
+    const uint32_t want = (uint32_t)((uint64_t)threads * (uint64_t)iters * 16u);
+    double cyc_mean = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        if (hs[b] != want)
+            return set_error(c, APTIDX_E_CUDA, "probe_smem_atomics: block %d counted %u increments, expected %u", b,
+                             hs[b], want);
+        cyc_mean += (double)hc[b] / nb;
+    }
+    const double incr = (double)nb * threads * (double)iters * 16.0;
+    *incr_per_s = incr / (ms * 1e-3);
+    if (reds_per_sm_cycle) *reds_per_sm_cycle = (double)threads / 32.0 * iters * 16.0 / cyc_mean;
     return APTIDX_OK;
 }
 

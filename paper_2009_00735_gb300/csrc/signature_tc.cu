@@ -565,22 +565,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                         float best[kNB];
                         int bk[kNB];
                         band_init_t<kNB>(p.bands, klo, best, bk);
+                        // the band maximum on |X|^2 (its root is the maximum
+                        // amplitude); the second half's factor w^(f h) is (-1)^f for
+                        // one chunk (a branch outside the frequency loop, so that the
+                        // loop carries no predicated sincos)
+                        const int f0 = p.kbase + 4 * fg0;
+                        if (nchunk == 1) {
+                            const float sg0 = (f0 & 1) ? -1.f : 1.f;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int f = p.kbase + 4 * fg0 + q;
-                            float xr, xi;
-                            if (nchunk == 1) {
-                                const float sg = (f & 1) ? -1.f : 1.f;
-                                xr = lo[2 * q] + sg * hv[2 * q];
-                                xi = lo[2 * q + 1] + sg * hv[2 * q + 1];
-                            } else {
+                            for (int q = 0; q < 4; ++q) {
+                                const float sg = (q & 1) ? -sg0 : sg0;
+                                const float xr = lo[2 * q] + sg * hv[2 * q], xi = lo[2 * q + 1] + sg * hv[2 * q + 1];
+                                band_update_t<kNB>(p.bands, klo, khi, f0 + q, xr * xr + xi * xi, best, bk);
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int f = f0 + q;
                                 float fs, fc;   // w^(f h) = fc - i fs, h = 512
                                 sincospif((float)f * (float)NBc / (float)NB, &fs, &fc);
-                                xr = lo[2 * q] + fc * hv[2 * q] - fs * hv[2 * q + 1];
-                                xi = lo[2 * q + 1] + fs * hv[2 * q] + fc * hv[2 * q + 1];
+                                const float xr = lo[2 * q] + fc * hv[2 * q] - fs * hv[2 * q + 1];
+                                const float xi = lo[2 * q + 1] + fs * hv[2 * q] + fc * hv[2 * q + 1];
+                                band_update_t<kNB>(p.bands, klo, khi, f, xr * xr + xi * xi, best, bk);
                             }
-                            // the band maximum on |X|^2: its root is the maximum amplitude
-                            band_update_t<kNB>(p.bands, klo, khi, f, xr * xr + xi * xi, best, bk);
                         }
 #pragma unroll
                         for (int b = 0; b < kNB; ++b)

@@ -215,3 +215,19 @@ def test_probe_l2(torch_cuda):
             apt.aptidx_probe_l2(ctx.handle, nbytes, 10)
         assert ei.value.code == apt.APTIDX_E_INVALID_ARG
     ctx.close()
+
+
+def test_probe_smem_atomics(torch_cuda):
+    """The shared-memory atomic probe counts every increment (the kernel checks
+    its array's sum), returns a rate between 0.05 and 4 32-lane atomics per SM
+    and cycle, and refuses thread counts that are not a multiple of 32 in
+    [32, 1024]."""
+    ctx = apt.Context(0)
+    incr, per_cycle = apt.aptidx_probe_smem_atomics(ctx.handle, 512, 256)
+    assert 0.05 < per_cycle < 4.0, per_cycle
+    assert 1e10 < incr < 1e14, incr
+    for threads in (16, 1056, 100):
+        with pytest.raises(apt.AptidxError) as ei:
+            apt.aptidx_probe_smem_atomics(ctx.handle, threads, 10)
+        assert ei.value.code == apt.APTIDX_E_INVALID_ARG
+    ctx.close()
