@@ -128,7 +128,7 @@ def gather_rooflines(l2, match_ms, refine_ms, nroi, nv, ng, ng_pad, n_hat, lut_b
     peak.  Eq. 3 reads, per ROI, every look-up table entry (n_hat x n_g) from
     L2 plus the ROI's signature row; a refinement pass reads, per direction,
     the direction (16 B), the measured value (4 B) and four bilinear image
-    taps (16 B), the taps mostly from L1."""
+    taps (16 B, one bilinear cell), the cells partly from L1."""
     peak = l2["gbs"] if l2 else None
     mb = float(nroi) * (n_hat * ng_pad * lut_bytes + nv * 4)
     rb = float(nroi) * nv * passes * (16 + 4 + 16)
@@ -136,7 +136,7 @@ def gather_rooflines(l2, match_ms, refine_ms, nroi, nv, ng, ng_pad, n_hat, lut_b
     for name, b, ms, what in (("k_match", mb, match_ms, f"{n_hat} x {ng_pad} table entries of {lut_bytes} B + "
                                                           f"{nv} x 4 B signature row per ROI"),
                               ("k_refine_gn", rb, refine_ms, f"{passes} passes x {nv} directions x 36 B per ROI "
-                                                             "(direction 16 B, value 4 B, four taps 16 B)")):
+                                                             "(direction 16 B, value 4 B, one 16 B image cell of four taps)")):
         if not ms:
             continue
         gbs = b / (ms / 1e3) / 1e9

@@ -451,7 +451,7 @@ int aptidx_destroy(aptidx_ctx* ctx) {
         free_ptr(r.d_node_sig);
         free_ptr(r.d_top);
         free_ptr(r.d_top_val);
-        free_ptr(r.d_img);
+        free_ptr(r.d_img4);
         free_ptr(r.d_lut);
         free_ptr(r.d_quats);
     }
@@ -1200,7 +1200,7 @@ int check_ref(Ctx* c, int32_t cand, bool need_lut, bool need_img) {
     if (!r.d_node_sig || r.nv_at_set != c->nv)
         return set_error(c, APTIDX_E_STATE, "candidate %d: set the reference for the current directions first", cand);
     if (need_lut && (!r.d_lut || r.ng <= 0)) return set_error(c, APTIDX_E_STATE, "candidate %d: build the look-up table first", cand);
-    if (need_img && !r.d_img) return set_error(c, APTIDX_E_STATE, "candidate %d: no reference image", cand);
+    if (need_img && !r.d_img4) return set_error(c, APTIDX_E_STATE, "candidate %d: no reference image", cand);
     return APTIDX_OK;
 }
 
@@ -1226,7 +1226,7 @@ int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, i
     free_ptr(r.d_top_val);
     free_ptr(r.d_lut);
     free_ptr(r.d_quats);
-    free_ptr(r.d_img);
+    free_ptr(r.d_img4);
     r.ng = 0;
     r.nv_at_set = -1;
     if ((rc = dev_alloc(c, (void**)&r.d_node_sig, (size_t)c->nv * sizeof(float)))) return rc;
@@ -1239,8 +1239,20 @@ int aptidx_set_reference(aptidx_ctx* ctx, int32_t cand, const float* node_sig, i
         if ((rc = to_host(c, img, ni, mem, hi))) return rc;
         for (size_t i = 0; i < ni; ++i)
             if (!isfinite(hi[i])) return set_error(c, APTIDX_E_INVALID_ARG, "set_reference: image value %zu not finite", i);
-        if ((rc = dev_alloc(c, (void**)&r.d_img, ni * sizeof(float)))) return rc;
-        APTIDX_CUDA(c, cudaMemcpyAsync(r.d_img, hi.data(), ni * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        // the four taps of every bilinear cell side by side: one 16-byte read
+        // per sample
+        const size_t nc = (size_t)(kImgRows - 1) * kImgCols;
+        std::vector<float4> cells(nc);
+        for (int i = 0; i + 1 < kImgRows; ++i)
+            for (int j = 0; j < kImgCols; ++j) {
+                const int j1 = j + 1 == kImgCols ? 0 : j + 1;
+                cells[(size_t)i * kImgCols + j] =
+                    make_float4(hi[(size_t)i * kImgCols + j], hi[(size_t)i * kImgCols + j1],
+                                hi[(size_t)(i + 1) * kImgCols + j], hi[(size_t)(i + 1) * kImgCols + j1]);
+            }
+        if ((rc = dev_alloc(c, (void**)&r.d_img4, nc * sizeof(float4)))) return rc;
+        APTIDX_CUDA(c, cudaMemcpyAsync(r.d_img4, cells.data(), nc * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+        APTIDX_CUDA(c, cudaStreamSynchronize(c->stream));   // `cells` is released on return
     }
     r.n_hat = n_hat;
     {

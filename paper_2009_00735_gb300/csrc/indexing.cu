@@ -432,7 +432,7 @@ struct DirTerm {
 // = -R (grad_c I x c); kCrystalJ returns grad_c I x c instead.
 template <bool kCrystalJ = false>
 __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy, float uz, float s,
-                                            const float* __restrict__ img, bool want_j) {
+                                            const float4* __restrict__ img4, bool want_j) {
     DirTerm t;
     const float cx = Rf[0] * ux + Rf[3] * uy + Rf[6] * uz;
     const float cy = Rf[1] * ux + Rf[4] * uy + Rf[7] * uz;
@@ -454,9 +454,10 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
     int j0 = (int)fj0;
     j0 = j0 >= kImgCols ? j0 - kImgCols : j0;
     j0 = min(max(j0, 0), kImgCols - 1);
-    const int j1 = j0 + 1 == kImgCols ? 0 : j0 + 1;
-    const float I00 = __ldg(img + i0 * kImgCols + j0), I01 = __ldg(img + i0 * kImgCols + j1);
-    const float I10 = __ldg(img + (i0 + 1) * kImgCols + j0), I11 = __ldg(img + (i0 + 1) * kImgCols + j1);
+    // the cell's four taps (I[i0][j0], I[i0][j0 + 1], I[i0 + 1][j0], I[i0 + 1][j0 + 1],
+    // the column index mod 360) in one read
+    const float4 cell = __ldg(img4 + i0 * kImgCols + j0);
+    const float I00 = cell.x, I01 = cell.y, I10 = cell.z, I11 = cell.w;
     const float v = (1.f - ti) * ((1.f - tj) * I00 + tj * I01) + ti * ((1.f - tj) * I10 + tj * I11);
     t.r = s - v;
     if (want_j) {
@@ -490,8 +491,9 @@ __device__ __forceinline__ DirTerm dir_term(const float* Rf, float ux, float uy,
     return t;
 }
 
-// direction and signature reads stream past L1 so that the reference image
-// (181 x 360 floats) stays resident there for the bilinear gathers
+// direction and signature reads stream past L1 so that L1 holds the reference
+// image cells (180 x 360 x 16 B, reused by neighbouring directions and ROIs)
+// for the bilinear gathers
 __device__ __forceinline__ float4 ld_stream4(const float4* p) {
     float4 v;
     asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
@@ -562,7 +564,7 @@ __device__ __forceinline__ void matrix_f32(const double* q, float* Rf) {
 // R(q0)): dL/domega = J_l(omega)^T dL/ddelta, J_l the left Jacobian of SO(3).
 template <bool kGrad>
 __global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __restrict__ S, const float4* __restrict__ dirs,
-                                                             int32_t nv, const float* __restrict__ img,
+                                                             int32_t nv, const float4* __restrict__ img,
                                                              const double* __restrict__ q0, const double* __restrict__ omega,
                                                              int64_t nroi, float* loss, float* grad) {
     __shared__ double scratch[4 * 32];
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(kRefThreads) k_refine_eval(const float* __rest
 constexpr int kGnThreads = 256;
 
 __global__ void __launch_bounds__(kGnThreads) k_refine_gn(const float* __restrict__ S, const float4* __restrict__ dsort,
-                                                          int32_t nv, const float* __restrict__ img,
+                                                          int32_t nv, const float4* __restrict__ img,
                                                           const double* __restrict__ q0,
                                                           const int32_t* __restrict__ best,
                                                           const double* __restrict__ quats, int64_t nroi, int iters,
@@ -844,10 +846,10 @@ cudaError_t launch_refine_eval(Ctx* c, Reference* r, const float* S, const doubl
                                int64_t nroi, float* loss, float* grad) {
     const int64_t grid = std::min<int64_t>((int64_t)c->sm_count * 8, nroi);
     if (grad)
-        k_refine_eval<true><<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, omega,
+        k_refine_eval<true><<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img4, q0, omega,
                                                                           nroi, loss, grad);
     else
-        k_refine_eval<false><<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img, q0, omega,
+        k_refine_eval<false><<<(unsigned)grid, kRefThreads, 0, c->stream>>>(S, c->d_dirs, c->nv, r->d_img4, q0, omega,
                                                                            nroi, loss, nullptr);
     return cudaGetLastError();
 }
@@ -865,7 +867,7 @@ cudaError_t launch_refine_gn(Ctx* c, Reference* r, const float* S, const double*
         if (dev_alloc(c, (void**)&c->d_gn_scratch, need)) return cudaErrorMemoryAllocation;
         c->gn_scratch_bytes = need;
     }
-    k_refine_gn<<<(unsigned)grid, kGnThreads, 0, c->stream>>>(S, c->d_dirs_sorted, c->nv, r->d_img, q0, best,
+    k_refine_gn<<<(unsigned)grid, kGnThreads, 0, c->stream>>>(S, c->d_dirs_sorted, c->nv, r->d_img4, q0, best,
                                                               r->d_quats, nroi, iters, c->d_gn_scratch, q_out, loss);
     return cudaGetLastError();
 }

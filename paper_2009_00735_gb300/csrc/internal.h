@@ -36,7 +36,9 @@ struct Reference {
     int32_t* d_top = nullptr;      // [n_hat] strongest nodes, strongest first
     float* d_top_val = nullptr;    // [n_hat] their values
     int32_t n_hat = 0;
-    float* d_img = nullptr;        // [181 x 360] or null
+    // reference image as bilinear cells, [180 x 360] or null: cell (i, j) holds
+    // (I[i][j], I[i][j'], I[i+1][j], I[i+1][j']) with j' = (j + 1) mod 360
+    float4* d_img4 = nullptr;
     void* d_lut = nullptr;         // [n_hat x ng_pad] (k-major), uint16 node indices when nv <= 65536, else int32
     int lut_bytes = 4;             // bytes per table entry (2 or 4)
     double* d_quats = nullptr;     // [ng x 4] test orientations of the table
