@@ -790,7 +790,11 @@ def main():
         print_secondary(args, measure_polycrystal, args.warmup, args.steps)
     elif args.workload == "wideband":
         import synth
-        print_secondary(args, measure_wideband, synth.single_crystal_bcc(), args.warmup, args.steps)
+        w = synth.single_crystal_bcc()
+        if args.rois > 0:   # a smaller case of the same workload (profiler captures)
+            w.centres = np.ascontiguousarray(w.centres[: args.rois])
+            w.radii = np.ascontiguousarray(w.radii[: args.rois])
+        print_secondary(args, measure_wideband, w, args.warmup, args.steps)
     elif args.workload == "large":
         import synth
         print_secondary(args, measure_large_rois, synth.single_crystal_bcc(), args.warmup, args.steps)
