@@ -170,7 +170,9 @@ int aptidx_band_for_spacing(double d_min, double d_max, double R, int m, int32_t
  * with the environment variable APTIDX_TUNE_CACHE naming a file, choices
  * persist across processes); APTIDX_GRAPH (the launches of the call are
  * captured in a CUDA graph on first use for these output pointers and sizes
- * and replayed on later calls; input changes discard the graphs);
+ * and replayed on later calls; input changes discard the graphs; the
+ * profiler of aptidx_set_profiling then books the whole replay, gather and
+ * ROI order included, as the signature phase);
  * APTIDX_DIRECT (no antipodal pairing: every direction is projected).
  * Outputs (in `mem`; NULL to skip): S nroi x nv FP32; argk nroi x nv u16 (the
  * lowest frequency bin attaining the maximum; not written when normalising

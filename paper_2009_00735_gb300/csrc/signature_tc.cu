@@ -112,10 +112,6 @@ __device__ __forceinline__ void hist_export_add(const uint32_t* H, int nbc, int 
     }
 }
 
-// ---- the kernel ----------------------------------------------------------------
-
-// kNB: band slots of the epilogue (1: the ROI's own band; APTIDX_MAX_BANDS:
-// the pass's BandSet, aptidx_compute_signatures_multi)
 // v += (-i)^(R0 + q) u for the n complex pairs (re, im) of v and u, where a
 // pair (r, i) stands for r - i i: multiplying by -i maps it to (-i, r), by -1
 // to (-r, -i), by i to (i, -r)
@@ -132,7 +128,13 @@ __device__ __forceinline__ void quarter_rot(float* v, const float* u, int n) {
     }
 }
 
-template <int kNB>
+// ---- the kernel ----------------------------------------------------------------
+
+// kNB: band slots of the epilogue (1: the ROI's own band; APTIDX_MAX_BANDS:
+// the pass's BandSet, aptidx_compute_signatures_multi); kWide: the instance
+// that streams the twiddles of bands wider than one B batch (the narrow-band
+// instance is compiled without that code)
+template <int kNB, bool kWide>
 __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled operands; offset arithmetic on the
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     // so a stage's bytes feed twice the tensor work of the bin-half
                     // split alone.  Thread 0 issues the MMAs as stages land; thread 32
                     // refills a stage once its MMAs are done, three stages ahead.
-                    const bool wide = nbatch > 1;
+                    const bool wide = kWide && nbatch > 1;
                     const int n_iss = wide ? 1 : p.n_iss;
                     const uint32_t sbo_b = (uint32_t)KB * 1024u;
                     const bool issuer = lane == 0 && warp < n_iss;
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     }
                 };
                 const bool quad = nbatch == 1 && p.n_iss == kIssuers && fg1 == fg0;
-                const int zw0 = (quad || nbatch > 1) ? 8 : 4;   // first zeroing warp
+                const int zw0 = (quad || (kWide && nbatch > 1)) ? 8 : 4;   // first zeroing warp
                 if (warp >= zw0) {
                     for (int i = tid - zw0 * 32; i < NBc * 8; i += kThreads - zw0 * 32)
                         reinterpret_cast<uint4*>(H)[i] = make_uint4(0, 0, 0, 0);
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                             if (best[b] >= 0.f) best[b] = sqrtf(best[b]) * 16777216.0f;
                         write_out(best, bk, dir);
                     }
-                } else if (nbatch > 1) {
+                } else if (kWide && nbatch > 1) {
                     // Wide bands, warps 0-7: the 64 directions form two groups
                     // (32 p .. 32 p + 31, p = warp & 1); a group's first-half rows are
                     // lane quadrant p (warps p, p + 4), its second-half rows quadrant
@@ -941,7 +943,10 @@ cudaError_t launch_signatures_tc(Ctx* c, float* S, uint16_t* argk, uint16_t* his
     if (cap < 256) return cudaErrorInvalidConfiguration;
     const size_t smem = tc_smem_bytes(c->m, cap, bt_bytes);
     const bool multi = !hist_out && c->multi.n > 0;
-    auto kern = multi ? k_sig_tc<APTIDX_MAX_BANDS> : k_sig_tc<1>;
+    // the wide-band stream lives in its own instances, so that the narrow-band
+    // kernel compiles without it
+    auto kern = multi ? (c->tc_wide ? k_sig_tc<APTIDX_MAX_BANDS, true> : k_sig_tc<APTIDX_MAX_BANDS, false>)
+                      : (c->tc_wide ? k_sig_tc<1, true> : k_sig_tc<1, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     // antipodal pairs (one projection per pair) unless switched off or exporting
