@@ -317,7 +317,7 @@ static int autotune(Ctx* c, int path, float* dS, uint16_t* dA) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int tpis[] = {4, 8, 16, 32};
+    const int tpis[] = {4, 8, 16, 32, 64};
     const int isss[] = {2, 4};
     Ctx::TuneCfg best{c->tune_tpi[pi], c->tune_iss, 1e30f};
     for (int tpi : tpis) {

@@ -347,22 +347,14 @@ __device__ __forceinline__ int hist_tile_pairs2(uint32_t* H, const float4* A, in
     int j = warp;
     auto ld_xy = [&](int i) { return *reinterpret_cast<const ulonglong2*>(A + 2 * i); };
     auto ld_z = [&](int i) { return *reinterpret_cast<const uint64_t*>(A + 2 * i + 1); };
-    if (j + W < np) {
-        ulonglong2 xa = ld_xy(j), xb = ld_xy(j + W);
-        uint64_t za = ld_z(j), zb = ld_z(j + W);
-        for (; j + 3 * W < np; j += 2 * W) {
-            const ulonglong2 nxa = ld_xy(j + 2 * W), nxb = ld_xy(j + 3 * W);
-            const uint64_t nza = ld_z(j + 2 * W), nzb = ld_z(j + 3 * W);
-            hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1, zp);
-            hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1, zp);
-            xa = nxa;
-            xb = nxb;
-            za = nza;
-            zb = nzb;
-        }
-        hist_add_pair2<kCount, kChunked>(hb, xa, za, q, bc, cmask, c0, c1, zp);
-        hist_add_pair2<kCount, kChunked>(hb, xb, zb, q, bc, cmask, c0, c1, zp);
-        j += 2 * W;
+    // four independent atom pairs per step (their loads first)
+    for (; j + 3 * W < np; j += 4 * W) {
+        const ulonglong2 x0 = ld_xy(j), x1 = ld_xy(j + W), x2 = ld_xy(j + 2 * W), x3 = ld_xy(j + 3 * W);
+        const uint64_t z0 = ld_z(j), z1 = ld_z(j + W), z2 = ld_z(j + 2 * W), z3 = ld_z(j + 3 * W);
+        hist_add_pair2<kCount, kChunked>(hb, x0, z0, q, bc, cmask, c0, c1, zp);
+        hist_add_pair2<kCount, kChunked>(hb, x1, z1, q, bc, cmask, c0, c1, zp);
+        hist_add_pair2<kCount, kChunked>(hb, x2, z2, q, bc, cmask, c0, c1, zp);
+        hist_add_pair2<kCount, kChunked>(hb, x3, z3, q, bc, cmask, c0, c1, zp);
     }
     for (; j < np; j += W) hist_add_pair2<kCount, kChunked>(hb, ld_xy(j), ld_z(j), q, bc, cmask, c0, c1, zp);
     int handled = warp < np ? 2 * ((np - warp + W - 1) / W) : 0;
