@@ -29,16 +29,32 @@ int cuda_check(Ctx* c, cudaError_t e, const char* what) {
     return set_error(c, code, "%s: %s", what, cudaGetErrorString(e));
 }
 
+constexpr size_t kSpareBytes = (size_t)4 << 30;
+
 int dev_alloc(Ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    for (size_t i = c->spare.size(); i-- > 0;) {
+        if (c->spare[i].second == bytes) {
+            *p = c->spare[i].first;
+            c->spare_bytes -= bytes;
+            c->spare.erase(c->spare.begin() + (ptrdiff_t)i);
+            return APTIDX_OK;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation && !c->spare.empty()) {
+        cudaGetLastError();
+        release_spare(c);
+        e = cudaMalloc(p, bytes);
+    }
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return set_error(c, e == cudaErrorMemoryAllocation ? APTIDX_E_OOM : APTIDX_E_CUDA,
                          "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
+    c->block_bytes[*p] = bytes;
     return APTIDX_OK;
 }
 
@@ -46,9 +62,32 @@ void dev_free(void* p) {
     if (p) cudaFree(p);
 }
 
+void dev_recycle(Ctx* c, void* p) {
+    if (!p) return;
+    auto it = c->block_bytes.find(p);
+    if (it == c->block_bytes.end() || c->spare_bytes + it->second > kSpareBytes) {
+        cudaFree(p);
+        return;
+    }
+    c->spare.emplace_back(p, it->second);
+    c->spare_bytes += it->second;
+}
+
+void release_spare(Ctx* c) {
+    for (auto& b : c->spare) cudaFree(b.first);
+    c->spare.clear();
+    c->spare_bytes = 0;
+}
+
 template <typename T>
 static void free_ptr(T*& p) {
     dev_free((void*)p);
+    p = nullptr;
+}
+
+template <typename T>
+static void recycle_ptr(Ctx* c, T*& p) {
+    dev_recycle(c, (void*)p);
     p = nullptr;
 }
 
@@ -129,24 +168,24 @@ static void clear_graphs(Ctx* c);
 
 static void free_rois(Ctx* c) {
     clear_graphs(c);
-    free_ptr(c->d_centres);
-    free_ptr(c->d_radii);
-    free_ptr(c->d_scale);
-    free_ptr(c->d_band);
-    free_ptr(c->d_nw);
-    free_ptr(c->d_nw64);
-    free_ptr(c->d_off);
-    free_ptr(c->d_atoms);
-    free_ptr(c->d_order);
-    free_ptr(c->d_scan_tmp);
+    recycle_ptr(c, c->d_centres);
+    recycle_ptr(c, c->d_radii);
+    recycle_ptr(c, c->d_scale);
+    recycle_ptr(c, c->d_band);
+    recycle_ptr(c, c->d_nw);
+    recycle_ptr(c, c->d_nw64);
+    recycle_ptr(c, c->d_off);
+    recycle_ptr(c, c->d_atoms);
+    recycle_ptr(c, c->d_order);
+    recycle_ptr(c, c->d_scan_tmp);
     c->nroi = 0;
     c->atoms_cap = c->atoms_total = 0;
     c->scan_tmp_elems = 0;
 }
 
 static void free_grid(Ctx* c) {
-    free_ptr(c->d_cell_start);
-    free_ptr(c->d_cell_pos);
+    recycle_ptr(c, c->d_cell_start);
+    recycle_ptr(c, c->d_cell_pos);
     c->cell_h = 0.0;
     c->n_cells = 0;
 }
@@ -198,13 +237,14 @@ static int build_grid(Ctx* c, double h) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) rc = cuda_check(c, e, "cell grid build");
     }
-    dev_free(cell_of);
-    dev_free(k2);
-    dev_free(idx);
-    dev_free(v2);
-    dev_free(counts);
-    dev_free(hist);
-    dev_free(offs);
+    // the stream is synchronised above: the temporaries are idle
+    dev_recycle(c, cell_of);
+    dev_recycle(c, k2);
+    dev_recycle(c, idx);
+    dev_recycle(c, v2);
+    dev_recycle(c, counts);
+    dev_recycle(c, hist);
+    dev_recycle(c, offs);
     if (rc) free_grid(c);
     return rc;
 }
@@ -437,6 +477,7 @@ int aptidx_destroy(aptidx_ctx* ctx) {
     c->d_twb = nullptr;
     free_ptr(c->d_status);
     free_ptr(c->d_counter);
+    release_spare(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_ptr(c->d_sort_hist);
     for (auto& pr : c->ev_pending) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -155,6 +156,13 @@ struct Ctx {
 
     // CUDA graphs of compute_signatures calls, keyed by their arguments
     std::map<std::string, cudaGraphExec_t> graphs;
+    // device blocks of the ROI set, the cell grid and its build released by a
+    // reload, kept by exact size (at most kSpareBytes) for the next set of
+    // equal sizes: a reload per step then allocates and frees nothing.  Every
+    // reuse is ordered on `stream`, where the blocks were last used.
+    std::vector<std::pair<void*, size_t>> spare;
+    size_t spare_bytes = 0;
+    std::unordered_map<void*, size_t> block_bytes;   // sizes of the blocks dev_alloc returned
     cudaStream_t cap_stream = nullptr;
 
     Reference ref[kMaxCandidates];
@@ -185,6 +193,9 @@ int cuda_check(Ctx* c, cudaError_t e, const char* what);
     } while (0)
 
 int dev_alloc(Ctx* c, void** p, size_t bytes);
+// hand a block from dev_alloc back for reuse by the same context (see Ctx::spare)
+void dev_recycle(Ctx* c, void* p);
+void release_spare(Ctx* c);
 void dev_free(void* p);
 
 // launches (all async on c->stream) -----------------------------------------
