@@ -231,3 +231,42 @@ def test_probe_smem_atomics(torch_cuda):
             apt.aptidx_probe_smem_atomics(ctx.handle, threads, 10)
         assert ei.value.code == apt.APTIDX_E_INVALID_ARG
     ctx.close()
+
+
+@pytest.mark.parametrize("path", [PLAIN, TC])
+def test_reload_reuses_blocks(torch_cuda, tiny, path):
+    """A reload keeps the ROI and cell-grid blocks it releases for the next set
+    of the same sizes.  Loading set A, then a set B of other sizes (half the
+    atoms, every other ROI), then A again gives A's signatures, argmax bins and
+    atom counts bit for bit, and B's match a context that only ever saw B."""
+    torch = torch_cuda
+    ctx, band, m, d = make_ctx(torch, tiny)
+    h = ctx.handle
+    nv = d.shape[0]
+    nroi = tiny.centres.shape[0]
+    S1, A1, N1 = gpu_signatures(torch, ctx, nroi, nv, path=path)
+    xyz_b = np.ascontiguousarray(tiny.xyz[::2])
+    cen_b = np.ascontiguousarray(tiny.centres[::2])
+    rad_b = np.ascontiguousarray(tiny.radii[::2])
+    for _ in range(2):
+        apt.aptidx_load_positions(h, torch.from_numpy(xyz_b).cuda())
+        apt.aptidx_set_rois(h, torch.from_numpy(cen_b).cuda(), torch.from_numpy(rad_b).cuda())
+        Sb, Ab, Nb = gpu_signatures(torch, ctx, cen_b.shape[0], nv, path=path)
+        apt.aptidx_load_positions(h, torch.from_numpy(tiny.xyz).cuda())
+        apt.aptidx_set_rois(h, torch.from_numpy(tiny.centres).cuda(), torch.from_numpy(tiny.radii).cuda())
+        S2, A2, N2 = gpu_signatures(torch, ctx, nroi, nv, path=path)
+        assert np.array_equal(N1, N2)
+        assert np.array_equal(A1, A2)
+        assert np.array_equal(S1.view(np.uint32), S2.view(np.uint32))
+    ctx.close()
+    fresh = apt.Context(0)
+    hf = fresh.handle
+    apt.aptidx_load_positions(hf, torch.from_numpy(xyz_b).cuda())
+    apt.aptidx_set_directions(hf, torch.from_numpy(np.ascontiguousarray(d)).cuda())
+    apt.aptidx_set_binning(hf, m, band[0], band[1])
+    apt.aptidx_set_rois(hf, torch.from_numpy(cen_b).cuda(), torch.from_numpy(rad_b).cuda())
+    Sf, Af, Nf = gpu_signatures(torch, fresh, cen_b.shape[0], nv, path=path)
+    assert np.array_equal(Nb, Nf)
+    assert np.array_equal(Ab, Af)
+    assert np.array_equal(Sb.view(np.uint32), Sf.view(np.uint32))
+    fresh.close()
