@@ -792,12 +792,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_sig_tc(TcParams p) {
                     if (warp < 2) write_out(best, bk, dir);
                 }
                 tc_fence_before();
-                __syncthreads();   // H is zero and the accumulators are read before the next pass
+                // the next tile's directions have landed (this thread's copies;
+                // the barrier publishes them), H is zero and the accumulators
+                // are read before the next pass or tile
+                cp_async_wait_all();
+                __syncthreads();
                 tc_fence_after();
             }
-            cp_async_wait_all();   // the next tile's directions have landed
-            tc_fence_before();
-            __syncthreads();
         }
         if (failed) break;
     }
