@@ -7,7 +7,9 @@
 
 #include <algorithm>
 #include <functional>
+#include <mutex>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -30,6 +32,11 @@ int cuda_check(Ctx* c, cudaError_t e, const char* what) {
 }
 
 constexpr size_t kSpareBytes = (size_t)4 << 30;
+
+// sizes of the live blocks dev_alloc returned (all contexts; dev_free and
+// release_spare drop them)
+static std::mutex g_blk_mu;
+static std::unordered_map<void*, size_t> g_blk_bytes;
 
 int dev_alloc(Ctx* c, void** p, size_t bytes) {
     *p = nullptr;
@@ -54,27 +61,40 @@ int dev_alloc(Ctx* c, void** p, size_t bytes) {
         return set_error(c, e == cudaErrorMemoryAllocation ? APTIDX_E_OOM : APTIDX_E_CUDA,
                          "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
-    c->block_bytes[*p] = bytes;
+    {
+        std::lock_guard<std::mutex> lk(g_blk_mu);
+        g_blk_bytes[*p] = bytes;
+    }
     return APTIDX_OK;
 }
 
 void dev_free(void* p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_blk_mu);
+        g_blk_bytes.erase(p);
+    }
+    cudaFree(p);
 }
 
 void dev_recycle(Ctx* c, void* p) {
     if (!p) return;
-    auto it = c->block_bytes.find(p);
-    if (it == c->block_bytes.end() || c->spare_bytes + it->second > kSpareBytes) {
-        cudaFree(p);
+    size_t bytes = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_blk_mu);
+        auto it = g_blk_bytes.find(p);
+        if (it != g_blk_bytes.end()) bytes = it->second;
+    }
+    if (bytes == 0 || c->spare_bytes + bytes > kSpareBytes) {
+        dev_free(p);
         return;
     }
-    c->spare.emplace_back(p, it->second);
-    c->spare_bytes += it->second;
+    c->spare.emplace_back(p, bytes);
+    c->spare_bytes += bytes;
 }
 
 void release_spare(Ctx* c) {
-    for (auto& b : c->spare) cudaFree(b.first);
+    for (auto& b : c->spare) dev_free(b.first);
     c->spare.clear();
     c->spare_bytes = 0;
 }

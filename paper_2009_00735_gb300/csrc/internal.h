@@ -5,7 +5,6 @@
 #include <stdint.h>
 
 #include <map>
-#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -162,7 +161,6 @@ struct Ctx {
     // reuse is ordered on `stream`, where the blocks were last used.
     std::vector<std::pair<void*, size_t>> spare;
     size_t spare_bytes = 0;
-    std::unordered_map<void*, size_t> block_bytes;   // sizes of the blocks dev_alloc returned
     cudaStream_t cap_stream = nullptr;
 
     Reference ref[kMaxCandidates];
