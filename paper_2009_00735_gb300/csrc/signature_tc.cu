@@ -20,9 +20,15 @@
 // -u gets the same signature value and frequency bin (its histogram is the
 // mirror image of u's, whose spectrum has the same amplitudes), provided no
 // atom's bin product along u is an exact integer, which the histogram pass
-// counts exactly (common.cuh).  A tile with such an atom runs a second pass
+// checks exactly (common.cuh).  A tile with such an atom runs a second pass
 // over the negated directions and writes their signatures from their own
 // histograms.
+//
+// Wide bands (more frequency groups than one B batch holds) run in their own
+// kernel instance (kWide): the chunk's bins split into quarters, only the
+// first quarter's twiddles stream from L2 through four shared-memory stages,
+// and each stage feeds two M = 128 MMAs per K step (bin quarters 0 | 2 and
+// 1 | 3); the epilogue applies the quarter factor w^(k NBc / 4).
 //
 // Per 64-direction tile of a ROI and (block, chunk) pass:
 //   1. histograms by shared-memory atomics (bank-private columns, as in the
@@ -35,9 +41,10 @@
 //      (M = 128, K = 16, N = 16 per group of 4 frequencies: 8 hi columns, then
 //      8 lo columns, where T = T_hi + T_lo with both parts fp16) into FP32
 //      accumulators in TMEM;
-//   4. after the last pass, four warps read the accumulators (tcgen05.ld), add
-//      hi and lo parts and the two bin halves, scale by 2^24 and keep the band
-//      maximum of |X(k)|.
+//   4. after the last pass, warps 0-7 read the accumulators (tcgen05.ld), add
+//      the partials, hi and lo parts and the two bin halves (one exchange in
+//      shared memory), scale by 2^24 and keep the band maximum of |X(k)|,
+//      while warps 8-15 zero the histogram for the next pass.
 #include <cuda_fp16.h>
 
 #include "tcgen05.cuh"
