@@ -69,6 +69,23 @@ def test_committed_traffic_figure():
         assert t8 is None and t1 is None
 
 
+def test_traffic_figure_follows_the_fingerprint(tmp_path, monkeypatch):
+    """A traffic record taken on other sources (one flipped fingerprint digit)
+    gives null; the same record with the current fingerprint gives the
+    captured bytes scaled by the ROI count."""
+    with open(bench.TRAFFIC_JSON) as fh:
+        t = json.load(fh)
+    good = bench.kernel_sources_sha16(t["sources"])
+    stale = dict(t, sources_sha256_16=("0" if good[0] != "0" else "1") + good[1:])
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(stale))
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(f))
+    assert bench.tc_traffic_per_launch(8192) is None
+    f.write_text(json.dumps(dict(t, sources_sha256_16=good)))
+    got = bench.tc_traffic_per_launch(2 * t["captured_rois"])
+    assert got is not None and np.isclose(got, 2 * t["dram_bytes_per_launch_captured"])
+
+
 def test_reference_arm_json_line():
     env = dict(os.environ, OMP_NUM_THREADS="2")
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
